@@ -1,0 +1,72 @@
+"""Brute-force enumerators used to pin the oracle (pure Python, tiny sizes).
+
+They share nothing with the oracle's code: Split is solved by listing every
+set of cut points of the giant tour, reinsertion by simulating every one of
+the 2^T delivery sequences forward in time.
+"""
+import itertools
+import math
+
+
+def euclid(coords, a, b):
+    dx = float(coords[a][0]) - float(coords[b][0])
+    dy = float(coords[a][1]) - float(coords[b][1])
+    return math.sqrt(dx * dx + dy * dy)
+
+
+def split_brute(tour, q_by_customer, Q, cost):
+    """Min over all partitions of the tour into consecutive routes whose load
+    is <= Q of the summed route costs (depot -> customers in tour order ->
+    depot).  cost(a, b) gives the travel cost between nodes (0 = depot).
+    Returns (best cost, list of optimal partitions as lists of routes)."""
+    n = len(tour)
+    if n == 0:
+        return 0.0, [[]]
+    best, arg = math.inf, []
+    for mask in range(1 << (n - 1)):
+        cuts = [k for k in range(1, n) if mask >> (k - 1) & 1]
+        bounds = [0] + cuts + [n]
+        total, ok = 0.0, True
+        routes = []
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            seg = tour[a:b]
+            if sum(q_by_customer[c - 1] for c in seg) > Q:
+                ok = False
+                break
+            r = cost(0, seg[0]) + cost(seg[-1], 0)
+            for x, y in zip(seg[:-1], seg[1:]):
+                r += cost(x, y)
+            total += r
+            routes.append(list(seg))
+        if not ok:
+            continue
+        tol = 1e-12 * max(1.0, abs(total))
+        if best == math.inf or total < best - tol:
+            best, arg = total, [routes]
+        elif abs(total - best) <= tol:
+            arg.append(routes)
+    return best, arg
+
+
+def reinsert_brute(T, U, I0, h, p, unit_cost, fixed, cons, H=None):
+    """Min over all 2^T delivery sequences of the simulated total cost.
+    Returns (best value, list of optimal 0/1 sequences)."""
+    best, arg = math.inf, []
+    for seq in itertools.product((0, 1), repeat=T):
+        I, total = I0, 0.0
+        for t, a in enumerate(seq):
+            q = (U - I) if a else 0
+            if q > 0:
+                total += float(fixed[t]) + unit_cost * q
+            x = I + q - int(cons[t])
+            if H is not None:
+                total += H[max(0, x)]
+            else:
+                total += h * x if x >= 0 else p * (-x)
+            I = max(0, x)
+        tol = 1e-12 * max(1.0, abs(total))
+        if best == math.inf or total < best - tol:
+            best, arg = total, [seq]
+        elif abs(total - best) <= tol:
+            arg.append(seq)
+    return best, arg
