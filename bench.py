@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Throughput of the scenario-batched Split Bellman update on GB300.
+
+Workload (one step = one pass of the whole Split path over one batch):
+  giant tour n=500, coords uniform fp32 in [0,100)^2 (depot (50,50)), Q=200,
+  S=10^6 demand scenarios per GPU, demands iid U{1..30} int32 (seed 1),
+  through sdp_split_eval: tour prep -> DEQUE DP kernel (+ plain fallback, a
+  no-op here) writing fp32 costs and uint16 predecessors -> FP64 mean.
+Metric: Bellman arc relaxations/s (capacity-feasible arcs (p,i) of Eq. eqdpA,
+  counted exactly on the device once, outside the timed region) and
+  scenarios/s, whole job over all ranks.
+  Inputs (2.0 GB per GPU) are larger than L2 (129 MB): no flush is needed.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N>1 (torchrun, one process per GPU): rank r evaluates scenarios
+[r*S, (r+1)*S) of one N*S-scenario set (weak scaling); the global FP64 mean
+is the one exchange step (an all-reduce of the per-rank sum).
+--impl reference times the FP64 CPU oracle (the paper's method as plain C)
+on bounded samples of the same workload on rank 0's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Bellman arc relaxations/s (Split, n=500, S=1e6 per GPU)"
+UNIT = "arcs/s"
+WORKLOAD = "split_n500_Q200_S1e6_U1-30"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+
+    def summary(self, t0, t1):
+        rows = []
+        for ts, ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((ts, parts))
+        inside = [r for ts, r in rows if t0 <= ts <= t1] or [r for _, r in rows]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in inside if num(r[1]) is not None]
+        smax = [num(r[2]) for r in inside if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in inside for k in range(4)
+                          if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(inside)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_sample(spec, rows, nthreads):
+    """Time the FP64 oracle on demand rows [rows] of the workload."""
+    import oracle
+    from paper_2602_05179_gb300 import workloads as wl
+    tour, xy, _ = wl.split_tour(spec)
+    q = wl.split_demands(spec, 0, rows)
+    oracle.split(tour, spec.Q, q[:8], coords=xy, nthreads=nthreads)  # build + warm
+    t0 = time.perf_counter()
+    r = oracle.split(tour, spec.Q, q, coords=xy, want_pred=True, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return int(r["arcs"].sum()), dt
+
+
+def cpu_baseline(spec, budget_s=12.0):
+    import oracle
+    cores = min(host_cores(), oracle.max_threads())
+    arcs, dt = oracle_sample(spec, 2000, cores)
+    rows = int(min(spec.S, max(2000, 2000 * budget_s / max(dt, 1e-3))))
+    arcs, dt = oracle_sample(spec, rows, cores)
+    return {"value": arcs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {rows} of the 10^6 scenarios ({arcs} arcs, {dt:.2f} s), "
+                      f"FP64 C oracle, OpenMP over scenarios",
+            "scenarios_per_s": rows / dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2602_05179_gb300 import workloads as wl
+    spec = wl.SPLIT_C2
+    cores = min(host_cores(), oracle.max_threads())
+    # per-step sample sized so the whole run stays within ~90 s
+    _, dt = oracle_sample(spec, 512, cores)
+    per_scen = dt / 512
+    rows = int(max(32, min(20000, 90.0 / max(1, args.steps + args.warmup) / per_scen)))
+    tour, xy, _ = wl.split_tour(spec)
+    total_arcs, total_t = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        s0 = (k * rows) % (spec.S - rows)
+        q = wl.split_demands(spec, s0, s0 + rows)
+        t0 = time.perf_counter()
+        r = oracle.split(tour, spec.Q, q, coords=xy, want_pred=True, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            total_arcs += int(r["arcs"].sum())
+            total_t += dt
+    value = total_arcs / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": spec.n, "Q": spec.Q,
+                       "scenarios_per_step": rows, "sample": "bounded"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} scenarios per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="deque", choices=["deque", "plain"])
+    ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--scenarios", type=int, default=0,
+                    help="override S per GPU (small cases for ncu captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_05179_gb300 import api
+    from paper_2602_05179_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    spec = wl.SPLIT_C2
+    if args.scenarios > 0:
+        import dataclasses
+        spec = dataclasses.replace(spec, S=args.scenarios)
+    S = spec.S
+    tour, xy, _ = wl.split_tour(spec)
+    t_d = torch.from_numpy(tour).to(dev)
+    c_d = torch.from_numpy(xy).to(dev)
+    q_d = wl.split_demands_device(spec, dev, rank * S, (rank + 1) * S) if world > 1 else \
+        wl.split_demands_device(spec, dev)
+    _, total = api.split_count_arcs(t_d, spec.Q, q_d, coords=c_d, per_scenario=False)
+    torch.cuda.synchronize()
+    arcs_rank = int(total)
+
+    def step(algo=args.algo):
+        return api.split_eval(t_d, spec.Q, q_d, coords=c_d, preds="u16", algo=algo)
+
+    # ---- device-resident timed region
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for ev in ks + ke:  # create the CUDA events before the timed region
+        ev.record()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    e0.record()
+    for k in range(args.steps):
+        api.set_profile_events(ks[k], ke[k])
+        r = step()
+    e1.record()
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if world > 1:
+        dist.barrier()
+    clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ks, ke))
+    flags = api.status()
+    t = torch.tensor([ms_total, kern_ms], dtype=torch.float64, device=dev)
+    cnt = torch.tensor([float(arcs_rank), float(r["cost"].double().sum())],
+                       dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    ms_total, kern_ms = float(t[0]), float(t[1])
+    arcs_all = cnt[0].item()
+    ms_step = ms_total / args.steps
+    value = arcs_all * args.steps / (ms_total / 1e3)
+    scen_s = S * world * args.steps / (ms_total / 1e3)
+
+    # ---- plain-kernel comparison (same call, algo=plain)
+    plain = None
+    if args.plain_steps > 0:
+        for _ in range(3):
+            step("plain")
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record()
+        for _ in range(args.plain_steps):
+            step("plain")
+        p1.record()
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / args.plain_steps
+        plain = {"value": arcs_rank * world / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                 "speedup_of_deque": (pms / ms_step)}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = e2e_run(args, api, spec, t_d, c_d, q_d, arcs_all, world, dist, dev)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    return report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plain,
+                  e2e, flags, clocks, t_wall0, t_wall1, dist)
+
+
+def e2e_run(args, api, spec, t_d, c_d, q_d, arcs_all, world, dist, dev):
+    import torch
+    q_host = torch.empty(q_d.shape, dtype=torch.int32, pin_memory=True)
+    q_host.copy_(q_d)
+    q_e2e = torch.empty_like(q_d)
+    h2d = q_host.numel() * 4
+    for _ in range(3):
+        q_e2e.copy_(q_host, non_blocking=True)
+        api.split_eval(t_d, spec.Q, q_e2e, coords=c_d, preds="u16", algo=args.algo)["mean"].item()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    w0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        q_e2e.copy_(q_host, non_blocking=True)
+        m = api.split_eval(t_d, spec.Q, q_e2e, coords=c_d, preds="u16", algo=args.algo)["mean"]
+        m.item()
+    w1 = time.perf_counter()
+    et = torch.tensor([w1 - w0], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    return {"value": arcs_all * args.e2e_steps / float(et[0]), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8, "steps": args.e2e_steps}
+
+
+def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plain, e2e,
+           flags, clocks, t_wall0, t_wall1, dist):
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peaks, peak_src = measured_peaks()
+    n = spec.n
+    alg_bytes = S * n * 4 + S * 4 + S * n * 2  # demands in, fp32 cost + uint16 preds out
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "split_deque_traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            tj = json.load(f)
+        if tj.get("kernel_rev") == kernel_rev():
+            traffic = tj.get("dram_bytes_per_launch")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "kernel": "split_deque_kernel", "kernel_ms": kern_ms,
+            "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_src} hbm_gbs (copy)"}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    p_alu = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if S == 1_000_000 else f"split_n500_Q200_S{S}_U1-30",
+                   "n": n, "Q": spec.Q, "S_per_gpu": S,
+                   "demand": "iid U{1..30} int32, seed 1", "coords": "U[0,100)^2 fp32",
+                   "algo": args.algo, "preds": "u16", "parallelism": f"scenario-sharded x{world}",
+                   "l2": "inputs larger than L2 (2.0 GB demands per step), no flush",
+                   "arcs_per_step": arcs_all},
+        "scenarios_per_s": scen_s,
+        "roofline": roof,
+        "alu_roofline": {"ops_per_arc": 2, "peak_ops_per_s": p_alu,
+                         "frac": 2 * arcs_all / world / (kern_ms / 1e3) / p_alu},
+        "vs_plain": plain,
+        "e2e": e2e,
+        "gpu_launches": 5 * args.steps,
+        "device_flags": flags,
+        "clocks": clocks.summary(t_wall0, t_wall1),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_rev():
+    """Hash of the DP kernel source, to tell whether stored ncu counters still
+    describe the kernel being timed."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2602_05179_gb300", "csrc", "split_deque.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

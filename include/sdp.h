@@ -1,0 +1,246 @@
+/*
+ * sdp.h -- C ABI of libsdp: scenario-batched Bellman (min-plus) kernels for
+ * GB300 (sm_103a), after arXiv 2602.05179, "From Sequential to Parallel:
+ * Reformulating Dynamic Programming as GPU Kernels for Large-Scale Stochastic
+ * Combinatorial Optimization".
+ *
+ * Operators
+ *   Split (Sec. 2 "Instantiation A", Eq. eqdpA; Algorithms "GPU Splitting"
+ *   and "2D Kernel for Splitting"): for a giant tour s_1..s_n, capacity Q and
+ *   S demand scenarios, per scenario
+ *       J(0) = 0,  J(i) = min_{p<i, load(s_{p+1..i}) <= Q} J(p) + W(p,i),
+ *       W(p,i) = c(0,s_{p+1}) + sum_{k=p+1}^{i-1} c(s_k,s_{k+1}) + c(s_i,0),
+ *   returning cost J(n), the predecessor array and the FP64 scenario mean.
+ *   Reinsertion (Sec. 2 "Instantiation B", Eq. eqdp2; Algorithm
+ *   "SolveBatchDP"): one customer, order-up-to level U, horizon T, per
+ *   scenario the backward DP over inventory states 0..U with the two actions
+ *   "no delivery" and "deliver up to U", returning the value from I0, the
+ *   optimal policy and the FP64 scenario mean.
+ *
+ * Conventions (every entry point)
+ *   - Array arguments are DEVICE pointers owned by the caller unless a field
+ *     says "host".  The library never frees them and never keeps them after
+ *     the call returns (plans keep the pointers given at creation).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).  Outputs are valid once the stream
+ *     has reached the call.  Argument checks that need no device data happen
+ *     before anything is launched; on error nothing is launched.
+ *   - The return value is a status code (SDP_OK, SDP_WARN_*, SDP_ERR_*).
+ *     sdp_last_error() gives a thread-local message for the last failure.
+ *   - Conditions found by the kernels (a demand above Q, a negative demand or
+ *     consumption) are raised in a per-device status word read with
+ *     sdp_device_status() (which synchronises the device).
+ *   - Eager calls never allocate device memory: scratch comes from the
+ *     caller's `workspace` (size from the matching *_workspace_bytes query).
+ *     Plans own device memory from sdp_split_plan_create until
+ *     sdp_plan_destroy.
+ *   - Calls on distinct streams are thread-safe; a plan must not be run
+ *     concurrently with itself.
+ */
+#ifndef SDP_H_
+#define SDP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SDP_VERSION 1
+
+/* status codes */
+#define SDP_OK 0
+#define SDP_WARN_INFEASIBLE 1     /* some scenario is infeasible (cost +inf) */
+#define SDP_ERR_INVALID_ARG (-1)  /* bad size, null or host pointer, ... */
+#define SDP_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define SDP_ERR_OOM (-3)          /* plan allocation failed */
+#define SDP_ERR_WORKSPACE (-4)    /* workspace missing or too small */
+#define SDP_ERR_UNSUPPORTED (-5)  /* valid but not supported (see field docs) */
+#define SDP_ERR_DEVICE_CHECK (-6) /* a kernel's own bounds check fired */
+
+/* device status word bits (sdp_device_status) */
+#define SDP_FLAG_INFEASIBLE 1u     /* a Split scenario had a demand > Q */
+#define SDP_FLAG_NEG_INPUT 2u      /* a negative demand / consumption was read */
+#define SDP_FLAG_DEVICE_CHECK 4u   /* an internal bounds check fired */
+#define SDP_FLAG_FALLBACK 8u       /* a scenario took the per-scenario path */
+
+/* Split algorithms */
+#define SDP_ALGO_AUTO 0   /* DEQUE when supported, else PLAIN */
+#define SDP_ALGO_PLAIN 1  /* one thread per scenario, demands read straight
+                             from HBM, every feasible arc (p,i) relaxed in
+                             turn: the min-plus column product of Eq. eqdpA */
+#define SDP_ALGO_DEQUE 2  /* warp tile of 32 scenarios staged in shared
+                             memory; the window minimum is kept in a monotone
+                             deque (the linear split of Algorithm "2D Kernel
+                             for Splitting"); needs Q <= 32767 */
+
+/* predecessor dtypes */
+#define SDP_PRED_U16 1    /* uint16, requires n < 65535 */
+#define SDP_PRED_I32 2    /* int32 */
+
+int sdp_version(void);
+const char* sdp_last_error(void);
+
+/* Measurement hook.  start/stop are cudaEvent_t handles (as void*) created
+ * by the caller; the calling thread's NEXT operator call records `start` on
+ * its stream just before launching its dominant kernel (the DP kernel) and
+ * `stop` just after it, then forgets them.  NULL, NULL disables.  Errors:
+ * SDP_ERR_INVALID_ARG if exactly one is NULL. */
+int sdp_set_profile_events(void* start, void* stop);
+
+/* Reads (and with clear != 0 resets) the status word of the current device.
+ * Synchronises the device.  *flags_out receives SDP_FLAG_* bits. */
+int sdp_device_status(int clear, uint32_t* flags_out);
+
+/* ------------------------------------------------------------------ Split */
+/* One giant tour, S scenarios.
+ * Exactly one of coords / dist is non-NULL:
+ *   coords [(n+1)*2] fp32, (x,y) per node, node 0 = depot: c(a,b) is the fp32
+ *          Euclidean distance (IEEE sqrt, no contraction);
+ *   dist   [(n+1)*(n+1)] fp32 row-major, c(a,b) = dist[a*(n+1)+b].
+ * The destination depot n+1 is the same node as the depot 0.
+ * demands [S*n] int32, demands[s*n + c-1] = demand of customer c in scenario
+ *   s (indexed by customer id; the tour permutes them).  A demand above Q
+ *   makes the scenario infeasible: cost +inf, predecessors -1 (0xFFFF for
+ *   uint16), SDP_FLAG_INFEASIBLE raised.  Negative demands raise
+ *   SDP_FLAG_NEG_INPUT and are read as 0.
+ * Route costs are FP32 (computed as the DP of K(i) = J(i) - D(i), D the
+ *   prefix tour length, which keeps every FP32 operand small); the tour
+ *   length D(n) is accumulated in FP64; the mean is FP64.
+ */
+typedef struct sdp_split_args {
+  int32_t n;              /* customers, n >= 0 (DEQUE: n <= 65534) */
+  int32_t Q;              /* capacity, Q > 0 */
+  int64_t S;              /* scenarios, S >= 0 */
+  const int32_t* tour;    /* [n], permutation of 1..n (not checked) */
+  const float* coords;    /* [(n+1)*2] or NULL */
+  const float* dist;      /* [(n+1)*(n+1)] or NULL */
+  const int32_t* demands; /* [S*n] */
+  float* cost_out;        /* [S], required: J_s(n) */
+  void* pred_out;         /* [S*n] or NULL: pred[s*n+i-1] = argmin p of J(i),
+                             the smallest p on exact ties */
+  int32_t pred_dtype;     /* SDP_PRED_U16 or SDP_PRED_I32 (ignored if no preds) */
+  int32_t algo;           /* SDP_ALGO_* */
+  double* mean_out;       /* [1] or NULL: (1/S) sum_s cost[s], +inf if any
+                             scenario is infeasible */
+  void* workspace;        /* device scratch, >= sdp_split_workspace_bytes */
+  size_t workspace_bytes;
+  int32_t warps_per_cta;  /* DEQUE tuning: 0 = default, else 1..16 */
+  int32_t ring;           /* DEQUE tuning: deque ring entries per scenario,
+                             0 = default, else 8, 16 or 32 */
+} sdp_split_args;
+
+size_t sdp_split_args_size(void);
+size_t sdp_split_workspace_bytes(const sdp_split_args* a);
+int sdp_split_eval(const sdp_split_args* a, void* stream);
+
+/* Number of capacity-feasible arcs (p,i), p < i, load(s_{p+1..i}) <= Q, per
+ * scenario -- the relaxations of Eq. eqdpA, the throughput unit.
+ * arcs_out [S] int64 or NULL; total_out [1] uint64 (device) or NULL. */
+int sdp_split_count_arcs(const sdp_split_args* a, int64_t* arcs_out,
+                         uint64_t* total_out, void* stream);
+
+/* Adjoint of the scenario mean of Split with respect to the travel-cost
+ * matrix (dist mode only).  The optimal cost is piecewise linear in dist, so
+ * at a point where each scenario's optimum is unique
+ *     d mean / d dist[a][b] = (1/S) * #uses of arc (a,b) in the optimal routes.
+ * fwd: the forward arguments (dist != NULL; cost_out / pred_out / mean_out
+ *      are not written).  pred: the forward's predecessors ([S*n], dtype
+ *      fwd->pred_dtype) to backtrack, or NULL to recompute them in a fused
+ *      forward + backtrack pass that keeps them on chip.
+ * grad_mean: [1] device scalar (upstream gradient);
+ * grad_dist: [(n+1)*(n+1)] fp32, overwritten with
+ *      (count(a,b) / S) * (*grad_mean).
+ * route_hist_out: [2n] int64 or NULL: route starts per tour position then
+ *      route ends per tour position, summed over feasible scenarios.
+ * Infeasible scenarios contribute no arc (the mean is +inf there). */
+size_t sdp_split_backward_workspace_bytes(const sdp_split_args* fwd);
+int sdp_split_backward(const sdp_split_args* fwd, const void* pred,
+                       const float* grad_mean, float* grad_dist,
+                       int64_t* route_hist_out, void* stream);
+
+/* -------------------------------------------------------- batched Split */
+/* B giant tours of uneven length, S scenarios each, run as one persistent
+ * launch (work queue over (tour, 32-scenario tile) items, longest tours
+ * first) captured in a CUDA graph.  Offsets are HOST arrays read at plan
+ * creation; the device arrays must stay valid while the plan is used. */
+typedef struct sdp_split_batch_desc {
+  int32_t B;                    /* tours, B >= 1 */
+  int32_t Q;                    /* capacity, 1 <= Q <= 32767 */
+  int64_t S;                    /* scenarios per tour, S >= 1 */
+  const int32_t* n_host;        /* host [B], 1 <= n_b <= 65534 */
+  const int64_t* tour_off_host; /* host [B]: tour b = tours[tour_off[b] ..+n_b) */
+  const int32_t* tours;         /* device, permutations of 1..n_b */
+  const int64_t* coord_off_host;/* host [B]: coords of tour b start at
+                                   coords[2*coord_off[b]], (n_b+1) nodes */
+  const float* coords;          /* device */
+  const int64_t* dem_off_host;  /* host [B]: demands of tour b = [S, n_b]
+                                   row-major at demands[dem_off[b]] */
+  const int32_t* demands;       /* device */
+  float* costs_out;             /* device [B*S], costs_out[b*S + s] */
+  double* means_out;            /* device [B] or NULL */
+} sdp_split_batch_desc;
+
+typedef struct sdp_plan sdp_plan;
+/* Allocates the plan's device memory (offsets, tour records, work counter,
+ * fallback list and scratch); SDP_ERR_OOM if that fails.  Uses the current
+ * device; every later call on the plan must run with that device current. */
+int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out);
+/* Times the candidate launch shapes (warps per CTA x deque ring entries) on
+ * `stream` -- each runs the whole plan, so outputs are overwritten -- and
+ * keeps the fastest.  cache_path (optional, host string) is a text file of
+ * earlier choices keyed by the device and the plan's shape: a hit skips the
+ * timing, a miss appends the new choice. */
+int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path);
+/* Enqueues one evaluation of the whole batch on `stream`: tour preparation,
+ * the persistent kernel, the fallback for flagged scenarios and the per-tour
+ * FP64 means.  The first call captures these launches into a CUDA graph;
+ * later calls replay it (a new launch shape from autotune re-captures). */
+int sdp_plan_run(sdp_plan* p, void* stream);
+/* Device time of the persistent kernel in the most recent sdp_plan_run
+ * (waits for it). */
+int sdp_plan_kernel_ms(sdp_plan* p, float* ms);
+/* Launch shape in use and the number of (tour, 32-scenario tile) items. */
+int sdp_plan_info(const sdp_plan* p, int32_t* warps_per_cta, int32_t* ring,
+                  int32_t* ctas, int64_t* items);
+/* Total feasible arcs of the whole batch (synchronous on `stream`). */
+int sdp_plan_count_arcs(sdp_plan* p, void* stream, uint64_t* total_host);
+void sdp_plan_destroy(sdp_plan* p);
+
+/* ------------------------------------------------------------ Reinsertion */
+/* One customer, order-up-to level U, days t = 0..T-1, S scenarios.
+ * State: start-of-day inventory I in 0..U.  Actions q in {0, U-I}; delivery
+ * arrives before consumption; unmet demand is lost:
+ *     I' = max(0, I + q - d_t).
+ * Stage cost F_t(q) + e(I + q - d_t) with F_t(q) = fixed[t] + unit_cost*q for
+ * q > 0 and 0 for q = 0; e(x) = h*x for x >= 0 and p*(-x) for x < 0, or, if
+ * end_cost_table != NULL, e(x) = end_cost_table[max(0,x)].  Terminal cost 0.
+ * Backward DP C_T = 0, C_t(I) = min(no delivery, delivery), ties to no
+ * delivery; value = C_0(I0); policy = decisions along the optimal path. */
+typedef struct sdp_reinsert_args {
+  int32_t T;                  /* 1 <= T <= 4096 */
+  int32_t U;                  /* 0 <= U <= 1023 */
+  int32_t I0;                 /* 0 <= I0 <= U */
+  int32_t algo;               /* 0 = default */
+  float h, p, unit_cost;
+  int64_t S;                  /* scenarios, S >= 0 */
+  const float* fixed;         /* [T] per-day routing/insertion cost f_t */
+  const float* end_cost_table;/* [U+1] or NULL */
+  const int32_t* consumption; /* [S*T], consumption[s*T + t] */
+  float* value_out;           /* [S], required */
+  uint8_t* policy_out;        /* [S*T] or NULL: 1 = deliver up to U on day t */
+  float* value0_out;          /* [S*(U+1)] or NULL: C_0(I) for every I */
+  double* mean_out;           /* [1] or NULL */
+  void* workspace;
+  size_t workspace_bytes;
+} sdp_reinsert_args;
+
+size_t sdp_reinsert_args_size(void);
+size_t sdp_reinsert_workspace_bytes(const sdp_reinsert_args* a);
+int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDP_H_ */

@@ -1,0 +1,452 @@
+// sdp_api.cu -- the C ABI of libsdp (include/sdp.h): argument checks,
+// workspace carving, kernel dispatch and the per-device status word.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "sdp_internal.cuh"
+
+namespace sdp {
+
+// Per-device status word: kernels OR SDP_FLAG_* bits into it.
+__device__ uint32_t g_status_word;
+
+namespace {
+
+thread_local char g_err[512] = "";
+// Optional CUDA events recorded around the dominant kernel of the calling
+// thread's next operator call (sdp_set_profile_events).
+thread_local cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
+
+void prof_begin(cudaStream_t st) {
+  if (g_prof_start) cudaEventRecord(g_prof_start, st);
+}
+void prof_end(cudaStream_t st) {
+  if (g_prof_stop) cudaEventRecord(g_prof_stop, st);
+  g_prof_start = g_prof_stop = nullptr;
+}
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SDP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int kMaxDev = 64;
+std::mutex g_mu;
+uint32_t* g_status_ptr[kMaxDev] = {};
+int g_sms[kMaxDev] = {};
+
+int current_device(int* dev) {
+  cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (*dev < 0 || *dev >= kMaxDev) return fail(SDP_ERR_UNSUPPORTED, "device id %d", *dev);
+  return SDP_OK;
+}
+
+int status_ptr(uint32_t** out) {
+  int dev;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_status_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_status_word);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
+    g_status_ptr[dev] = static_cast<uint32_t*>(p);
+  }
+  *out = g_status_ptr[dev];
+  return SDP_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// workspace carving (every block 256-byte aligned)
+struct Carver {
+  unsigned char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off = align_up(off + count * sizeof(T), 256);
+    return p;
+  }
+};
+
+constexpr int64_t kPlainSlots = 262144;   // PLAIN: threads in flight (grid-stride)
+constexpr int64_t kFallbackSlots = 4096;  // DEQUE fallback path
+
+struct SplitWs {
+  TourPrep prep;
+  double* mean_partial;
+  uint32_t* fb_count;
+  uint32_t* fb_list;
+  float* kscratch;
+  int32_t* pscratch;
+  int64_t nslots;
+  unsigned long long* hist;
+  size_t bytes;
+};
+
+int resolve_algo(const sdp_split_args* a) {
+  int algo = a->algo;
+  if (algo == SDP_ALGO_AUTO) algo = deque_supported(a->n, a->Q) ? SDP_ALGO_DEQUE : SDP_ALGO_PLAIN;
+  return algo;
+}
+
+SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
+  SplitWs w{};
+  Carver c{static_cast<unsigned char*>(base)};
+  const int n = a->n;
+  const int algo = resolve_algo(a);
+  w.prep.rec = c.take<StepRec>((size_t)n);
+  w.prep.cols = c.take<uint16_t>((size_t)n);
+  w.prep.Dn = c.take<double>(1);
+  w.mean_partial = c.take<double>(kMeanBlocks);
+  w.fb_count = c.take<uint32_t>(1);
+  if (algo == SDP_ALGO_DEQUE) {
+    w.fb_list = c.take<uint32_t>((size_t)a->S);
+    w.nslots = a->S < kFallbackSlots ? a->S : kFallbackSlots;
+  } else {
+    w.fb_list = nullptr;
+    w.nslots = a->S < kPlainSlots ? a->S : kPlainSlots;
+  }
+  if (w.nslots < 1) w.nslots = 1;
+  w.kscratch = c.take<float>((size_t)(n + 1) * w.nslots);
+  w.pscratch = backward ? c.take<int32_t>((size_t)n * w.nslots) : nullptr;
+  w.hist = backward ? c.take<unsigned long long>(2 * (size_t)n + 1) : nullptr;
+  w.bytes = c.off;
+  return w;
+}
+
+int check_split(const sdp_split_args* a, bool need_cost) {
+  if (!a) return fail(SDP_ERR_INVALID_ARG, "args is NULL");
+  if (a->n < 0) return fail(SDP_ERR_INVALID_ARG, "n = %d < 0", a->n);
+  if (a->Q <= 0) return fail(SDP_ERR_INVALID_ARG, "Q = %d <= 0", a->Q);
+  if (a->S < 0) return fail(SDP_ERR_INVALID_ARG, "S = %lld < 0", (long long)a->S);
+  if (a->S > (int64_t)0xFFFFFFFFll) return fail(SDP_ERR_UNSUPPORTED, "S above 2^32-1");
+  if (a->algo < SDP_ALGO_AUTO || a->algo > SDP_ALGO_DEQUE)
+    return fail(SDP_ERR_INVALID_ARG, "unknown algo %d", a->algo);
+  if (a->algo == SDP_ALGO_DEQUE && !deque_supported(a->n, a->Q))
+    return fail(SDP_ERR_UNSUPPORTED, "DEQUE needs 1 <= n <= 65534 and Q <= 32767");
+  if (need_cost && a->S > 0 && !is_device_ptr(a->cost_out))
+    return fail(SDP_ERR_INVALID_ARG, "cost_out must be a device pointer");
+  if (a->n > 0 && a->S > 0) {
+    if ((a->coords == nullptr) == (a->dist == nullptr))
+      return fail(SDP_ERR_INVALID_ARG, "exactly one of coords / dist must be set");
+    if (!is_device_ptr(a->tour)) return fail(SDP_ERR_INVALID_ARG, "tour must be a device pointer");
+    if (a->coords && !is_device_ptr(a->coords))
+      return fail(SDP_ERR_INVALID_ARG, "coords must be a device pointer");
+    if (a->dist && !is_device_ptr(a->dist))
+      return fail(SDP_ERR_INVALID_ARG, "dist must be a device pointer");
+    if (!is_device_ptr(a->demands)) return fail(SDP_ERR_INVALID_ARG, "demands must be a device pointer");
+  }
+  if (a->pred_out) {
+    if (a->pred_dtype != SDP_PRED_U16 && a->pred_dtype != SDP_PRED_I32)
+      return fail(SDP_ERR_INVALID_ARG, "pred_dtype must be SDP_PRED_U16 or SDP_PRED_I32");
+    if (a->pred_dtype == SDP_PRED_U16 && a->n >= 65535)
+      return fail(SDP_ERR_UNSUPPORTED, "uint16 predecessors need n < 65535");
+    if (a->S > 0 && a->n > 0 && !is_device_ptr(a->pred_out))
+      return fail(SDP_ERR_INVALID_ARG, "pred_out must be a device pointer");
+  }
+  if (a->mean_out && !is_device_ptr(a->mean_out))
+    return fail(SDP_ERR_INVALID_ARG, "mean_out must be a device pointer");
+  if (a->warps_per_cta < 0 || a->warps_per_cta > 16)
+    return fail(SDP_ERR_INVALID_ARG, "warps_per_cta must be 0..16");
+  if (a->ring != 0 && a->ring != 8 && a->ring != 16 && a->ring != 32)
+    return fail(SDP_ERR_INVALID_ARG, "ring must be 0, 8, 16 or 32");
+  return SDP_OK;
+}
+
+int check_ws(void* ws, size_t have, size_t need) {
+  if (need == 0) return SDP_OK;
+  if (!ws || have < need)
+    return fail(SDP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, have);
+  if (!is_device_ptr(ws)) return fail(SDP_ERR_INVALID_ARG, "workspace must be a device pointer");
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(SDP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  return SDP_OK;
+}
+
+// Runs the DEQUE kernel (+ plain fallback) or the PLAIN kernel over all S.
+int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
+                   unsigned long long* hist, cudaStream_t st) {
+  const int algo = resolve_algo(a);
+  const int sms = num_sms();
+  float* cost = hist ? nullptr : a->cost_out;
+  void* pred = hist ? nullptr : a->pred_out;
+  if (algo == SDP_ALGO_DEQUE) {
+    const int warps = a->warps_per_cta > 0 ? a->warps_per_cta : 4;
+    const int ring = a->ring > 0 ? a->ring : 16;
+    DequeConfig cfg = deque_config(a->n, a->Q, warps, ring, hist != nullptr);
+    if (cfg.smem > 227 * 1024)
+      return fail(SDP_ERR_UNSUPPORTED, "DEQUE tile needs %zu B of shared memory; lower warps_per_cta", cfg.smem);
+    int occ = 0;
+    int e = deque_max_ctas_per_sm(cfg, hist != nullptr, a->pred_dtype, pred != nullptr, &occ);
+    if (e) return cuda_fail((cudaError_t)e, "deque occupancy");
+    if (occ < 1) return fail(SDP_ERR_UNSUPPORTED, "DEQUE configuration does not fit on an SM");
+    const int64_t tiles = (a->S + 31) / 32;
+    const int64_t ctas_needed = (tiles + warps - 1) / warps;
+    const int grid = (int)(ctas_needed < (int64_t)occ * sms ? ctas_needed : (int64_t)occ * sms);
+    SplitDequeArgs d{};
+    d.n = a->n; d.Q = a->Q; d.S = a->S;
+    d.rec = w.prep.rec; d.cols = w.prep.cols; d.Dn = w.prep.Dn;
+    d.demands = a->demands; d.cost = cost; d.pred = pred; d.pred_dtype = a->pred_dtype;
+    d.hist = hist; d.fb_list = w.fb_list; d.fb_count = w.fb_count; d.status = status;
+    prof_begin(st);
+    e = launch_split_deque(d, cfg, grid, st);
+    prof_end(st);
+    if (e) return cuda_fail((cudaError_t)e, "split_deque launch");
+  }
+  SplitPlainArgs p{};
+  p.n = a->n; p.Q = a->Q; p.S = a->S;
+  p.rec = w.prep.rec; p.Dn = w.prep.Dn; p.demands = a->demands;
+  p.cost = cost; p.pred = pred; p.pred_dtype = a->pred_dtype;
+  p.kscratch = w.kscratch; p.pscratch = (hist && !pred) ? w.pscratch : nullptr;
+  p.nslots = w.nslots; p.hist = hist;
+  p.fb_list = algo == SDP_ALGO_DEQUE ? w.fb_list : nullptr;
+  p.fb_count = w.fb_count; p.status = status;
+  const int grid = (int)((w.nslots + 255) / 256);
+  if (algo != SDP_ALGO_DEQUE) prof_begin(st);
+  launch_split_plain(p, grid, st);
+  if (algo != SDP_ALGO_DEQUE) prof_end(st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "split_plain launch");
+  return SDP_OK;
+}
+
+}  // namespace
+
+int status_word(uint32_t** out) { return status_ptr(out); }
+
+int api_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
+int num_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+  if (!g_sms[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    g_sms[dev] = v > 0 ? v : 1;
+  }
+  return g_sms[dev];
+}
+
+}  // namespace sdp
+
+using namespace sdp;
+
+extern "C" {
+
+int sdp_version(void) { return SDP_VERSION; }
+
+const char* sdp_last_error(void) { return g_err; }
+
+size_t sdp_split_args_size(void) { return sizeof(sdp_split_args); }
+
+int sdp_set_profile_events(void* start, void* stop) {
+  if ((start == nullptr) != (stop == nullptr))
+    return fail(SDP_ERR_INVALID_ARG, "give both events or neither");
+  g_prof_start = static_cast<cudaEvent_t>(start);
+  g_prof_stop = static_cast<cudaEvent_t>(stop);
+  return SDP_OK;
+}
+size_t sdp_reinsert_args_size(void) { return sizeof(sdp_reinsert_args); }
+
+int sdp_device_status(int clear, uint32_t* flags_out) {
+  uint32_t* sp;
+  int rc = status_ptr(&sp);
+  if (rc) return rc;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  uint32_t v = 0;
+  e = cudaMemcpy(&v, sp, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status");
+  if (clear) {
+    e = cudaMemset(sp, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+  }
+  if (flags_out) *flags_out = v;
+  if (v & SDP_FLAG_DEVICE_CHECK) return fail(SDP_ERR_DEVICE_CHECK, "a kernel bounds check fired");
+  return (v & SDP_FLAG_INFEASIBLE) ? SDP_WARN_INFEASIBLE : SDP_OK;
+}
+
+size_t sdp_split_workspace_bytes(const sdp_split_args* a) {
+  if (!a || a->n < 0 || a->S < 0) return 0;
+  return carve_split(a, nullptr, false).bytes;
+}
+
+size_t sdp_split_backward_workspace_bytes(const sdp_split_args* a) {
+  if (!a || a->n < 0 || a->S < 0) return 0;
+  return carve_split(a, nullptr, true).bytes;
+}
+
+int sdp_split_eval(const sdp_split_args* a, void* stream) {
+  int rc = check_split(a, true);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SplitWs need = carve_split(a, nullptr, false);
+  rc = check_ws(a->workspace, a->workspace_bytes, need.bytes);
+  if (rc) return rc;
+  uint32_t* status;
+  rc = status_ptr(&status);
+  if (rc) return rc;
+  const SplitWs w = carve_split(a, a->workspace, false);
+  if (a->S > 0 && a->n == 0) {
+    cudaError_t e = cudaMemsetAsync(a->cost_out, 0, sizeof(float) * a->S, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset cost");
+  } else if (a->S > 0) {
+    launch_tour_prep(a->tour, a->n, a->coords, a->dist, w.prep, status, w.fb_count, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tour_prep launch");
+    rc = run_split_core(a, w, status, nullptr, st);
+    if (rc) return rc;
+  }
+  if (a->mean_out) {
+    launch_mean(a->cost_out, a->S, w.mean_partial, a->mean_out, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mean launch");
+  }
+  return SDP_OK;
+}
+
+int sdp_split_count_arcs(const sdp_split_args* a, int64_t* arcs_out, uint64_t* total_out,
+                         void* stream) {
+  int rc = check_split(a, false);
+  if (rc) return rc;
+  if (arcs_out && !is_device_ptr(arcs_out)) return fail(SDP_ERR_INVALID_ARG, "arcs_out must be a device pointer");
+  if (total_out && !is_device_ptr(total_out)) return fail(SDP_ERR_INVALID_ARG, "total_out must be a device pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SplitWs need = carve_split(a, nullptr, false);
+  rc = check_ws(a->workspace, a->workspace_bytes, need.bytes);
+  if (rc) return rc;
+  uint32_t* status;
+  rc = status_ptr(&status);
+  if (rc) return rc;
+  const SplitWs w = carve_split(a, a->workspace, false);
+  if (total_out) {
+    cudaError_t e = cudaMemsetAsync(total_out, 0, sizeof(uint64_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset total");
+  }
+  if (a->S == 0) return SDP_OK;
+  if (a->n == 0) {
+    if (arcs_out) {
+      cudaError_t e = cudaMemsetAsync(arcs_out, 0, sizeof(int64_t) * a->S, st);
+      if (e != cudaSuccess) return cuda_fail(e, "memset arcs");
+    }
+    return SDP_OK;
+  }
+  launch_tour_prep(a->tour, a->n, a->coords, a->dist, w.prep, status, w.fb_count, st);
+  launch_count_arcs(a->n, a->Q, a->S, w.prep.rec, a->demands, arcs_out,
+                    reinterpret_cast<unsigned long long*>(total_out), 4 * num_sms(), st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "count_arcs launch");
+  return SDP_OK;
+}
+
+int sdp_split_backward(const sdp_split_args* fwd, const void* pred, const float* grad_mean,
+                       float* grad_dist, int64_t* route_hist_out, void* stream) {
+  int rc = check_split(fwd, false);
+  if (rc) return rc;
+  if (!fwd->dist) return fail(SDP_ERR_UNSUPPORTED, "the adjoint is taken with respect to dist: set dist, not coords");
+  if (!is_device_ptr(grad_mean)) return fail(SDP_ERR_INVALID_ARG, "grad_mean must be a device pointer");
+  if (!is_device_ptr(grad_dist)) return fail(SDP_ERR_INVALID_ARG, "grad_dist must be a device pointer");
+  if (route_hist_out && !is_device_ptr(route_hist_out))
+    return fail(SDP_ERR_INVALID_ARG, "route_hist_out must be a device pointer");
+  if (pred && !is_device_ptr(pred)) return fail(SDP_ERR_INVALID_ARG, "pred must be a device pointer");
+  if (pred && fwd->pred_dtype != SDP_PRED_U16 && fwd->pred_dtype != SDP_PRED_I32)
+    return fail(SDP_ERR_INVALID_ARG, "pred_dtype must be SDP_PRED_U16 or SDP_PRED_I32");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SplitWs need = carve_split(fwd, nullptr, true);
+  rc = check_ws(fwd->workspace, fwd->workspace_bytes, need.bytes);
+  if (rc) return rc;
+  uint32_t* status;
+  rc = status_ptr(&status);
+  if (rc) return rc;
+  const SplitWs w = carve_split(fwd, fwd->workspace, true);
+  const int n = fwd->n;
+  cudaError_t e = cudaMemsetAsync(w.hist, 0, sizeof(unsigned long long) * (2 * (size_t)n + 1), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset hist");
+  if (n > 0 && fwd->S > 0) {
+    if (pred) {
+      launch_backtrack_hist(n, fwd->S, pred, fwd->pred_dtype, w.hist, status, st);
+    } else {
+      launch_tour_prep(fwd->tour, n, fwd->coords, fwd->dist, w.prep, status, w.fb_count, st);
+      rc = run_split_core(fwd, w, status, w.hist, st);
+      if (rc) return rc;
+    }
+  }
+  launch_grad_assemble(n, fwd->S, fwd->tour, w.hist, grad_mean, grad_dist, route_hist_out, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return SDP_OK;
+}
+
+size_t sdp_reinsert_workspace_bytes(const sdp_reinsert_args* a) {
+  if (!a || a->S < 0) return 0;
+  return (size_t)kMeanBlocks * sizeof(double);
+}
+
+int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
+  if (!a) return fail(SDP_ERR_INVALID_ARG, "args is NULL");
+  if (a->T < 1 || a->T > 4096) return fail(SDP_ERR_INVALID_ARG, "T = %d outside 1..4096", a->T);
+  if (a->U < 0 || a->U > 1023) return fail(SDP_ERR_INVALID_ARG, "U = %d outside 0..1023", a->U);
+  if (a->I0 < 0 || a->I0 > a->U) return fail(SDP_ERR_INVALID_ARG, "I0 = %d outside 0..U", a->I0);
+  if (a->S < 0) return fail(SDP_ERR_INVALID_ARG, "S < 0");
+  const int kc = a->U + 1 <= 256 ? (a->U + 1 + 31) / 32 : (a->U + 1 <= 512 ? 16 : 32);
+  if ((int64_t)a->T * kc > 2048)
+    return fail(SDP_ERR_UNSUPPORTED, "T * ceil((U+1)/32) = %lld above 2048 (decision bits kept on chip)",
+                (long long)a->T * kc);
+  if (a->S > 0) {
+    if (!is_device_ptr(a->fixed)) return fail(SDP_ERR_INVALID_ARG, "fixed must be a device pointer");
+    if (!is_device_ptr(a->consumption)) return fail(SDP_ERR_INVALID_ARG, "consumption must be a device pointer");
+    if (!is_device_ptr(a->value_out)) return fail(SDP_ERR_INVALID_ARG, "value_out must be a device pointer");
+    if (a->end_cost_table && !is_device_ptr(a->end_cost_table))
+      return fail(SDP_ERR_INVALID_ARG, "end_cost_table must be a device pointer");
+    if (a->policy_out && !is_device_ptr(a->policy_out))
+      return fail(SDP_ERR_INVALID_ARG, "policy_out must be a device pointer");
+    if (a->value0_out && !is_device_ptr(a->value0_out))
+      return fail(SDP_ERR_INVALID_ARG, "value0_out must be a device pointer");
+  }
+  if (a->mean_out && !is_device_ptr(a->mean_out)) return fail(SDP_ERR_INVALID_ARG, "mean_out must be a device pointer");
+  const size_t need = sdp_reinsert_workspace_bytes(a);
+  int rc = a->mean_out ? check_ws(a->workspace, a->workspace_bytes, need) : SDP_OK;
+  if (rc) return rc;
+  uint32_t* status;
+  rc = status_ptr(&status);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ReinsertArgs r{};
+  r.T = a->T; r.U = a->U; r.I0 = a->I0; r.h = a->h; r.p = a->p; r.c = a->unit_cost;
+  r.S = a->S; r.fixed = a->fixed; r.table = a->end_cost_table; r.cons = a->consumption;
+  r.value = a->value_out; r.policy = a->policy_out; r.value0 = a->value0_out; r.status = status;
+  prof_begin(st);
+  int e = launch_reinsert(r, st);
+  prof_end(st);
+  if (e) return cuda_fail((cudaError_t)e, "reinsert launch");
+  if (a->mean_out) {
+    launch_mean(a->value_out, a->S, static_cast<double*>(a->workspace), a->mean_out, st);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(ce, "mean launch");
+  }
+  return SDP_OK;
+}
+
+}  // extern "C"

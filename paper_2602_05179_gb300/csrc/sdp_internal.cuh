@@ -1,0 +1,186 @@
+// sdp_internal.cuh -- internal declarations shared by the libsdp translation
+// units (kernels + C-ABI layer).  Not part of the public ABI (include/sdp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sdp.h"
+
+namespace sdp {
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// ---------------------------------------------------------------- Split prep
+// Per tour position i = 1..n one 16-byte record, read by every scenario of
+// the tour (a warp-uniform broadcast load per DP step):
+//   col = s_i - 1            (column of customer s_i in a demand row)
+//   a   = c(0,s_i) - c(s_{i-1},s_i)   (0 for the second term when i = 1)
+//   ce  = c(s_i, 0)
+// With D(k) = sum_{m=1}^{k-1} c(s_m,s_{m+1}) and K(i) = J(i) - D(i), the
+// recursion of Eq. eqdpA becomes
+//   psi(p) = K(p) + a_{p+1},  K(i) = min_{p in window(i)} psi(p) + ce_i,
+//   J(n)   = K(n) + D(n),
+// so every FP32 operand stays at the scale of the depot legs rather than the
+// whole tour length; D(n) is accumulated in FP64 once per tour.
+struct __align__(16) StepRec {
+  uint32_t col;
+  float a;
+  float ce;
+  uint32_t pad;
+};
+
+struct TourPrep {
+  StepRec* rec;     // [n]
+  uint16_t* cols;   // [n] (col of each position, compact copy for copy-out)
+  double* Dn;       // [1] tour length D(n) in FP64
+};
+
+// ----------------------------------------------------------------- kernels
+// status bits are OR-ed into *status (a per-device __device__ word).
+
+// one CTA per tour; coords or dist mode
+void launch_tour_prep(const int32_t* tour, int n, const float* coords,
+                      const float* dist, TourPrep prep, uint32_t* status,
+                      uint32_t* reset_word, cudaStream_t st);
+
+struct SplitPlainArgs {
+  int n, Q;
+  int64_t S;
+  const StepRec* rec;
+  const double* Dn;
+  const int32_t* demands;
+  float* cost;
+  void* pred;           // nullable
+  int pred_dtype;
+  float* kscratch;      // [(n+1) * nslots], K(p) of the scenario in slot
+  int32_t* pscratch;    // [n * nslots] preds when pred == NULL and hist != NULL
+  int64_t nslots;
+  unsigned long long* hist;  // [2n] or NULL (route start / end counts)
+  const uint32_t* fb_list;   // NULL: all scenarios; else list of scenario ids
+  const uint32_t* fb_count;  // [1] number of entries in fb_list
+  uint32_t* status;
+};
+void launch_split_plain(const SplitPlainArgs& a, int grid, cudaStream_t st);
+int plain_grid(int device_sms);
+
+struct SplitDequeArgs {
+  int n, Q;
+  int64_t S;
+  const StepRec* rec;
+  const uint16_t* cols;
+  const double* Dn;
+  const int32_t* demands;
+  float* cost;          // nullable in the fused backward
+  void* pred;           // nullable
+  int pred_dtype;
+  unsigned long long* hist;  // [2n] or NULL: fused backtrack histograms
+  uint32_t* fb_list;    // [S] scenario ids that need the per-scenario path
+  uint32_t* fb_count;   // [1]
+  uint32_t* status;
+};
+struct DequeConfig {
+  int warps;     // warps per CTA
+  int ring;      // deque ring entries per scenario (8, 16, 32)
+  int qbytes;    // 1 (uint8 staging) or 2 (uint16 staging)
+  int row_stride;// bytes per staged demand row
+  size_t smem;   // dynamic shared memory per CTA
+};
+bool deque_supported(int n, int Q);
+DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist);
+// returns 0 or a cudaError_t
+int launch_split_deque(const SplitDequeArgs& a, const DequeConfig& c, int grid,
+                       cudaStream_t st);
+int deque_max_ctas_per_sm(const DequeConfig& c, bool hist, int pred_dtype,
+                          bool want_pred, int* out);
+
+// batched Split (persistent work queue over (tour, 32-scenario tile) items)
+struct BatchKernelArgs {
+  int B, Q, n_max;
+  int64_t S;
+  const int32_t* n;          // [B]
+  const int64_t* dem_off;    // [B] element offset of tour b's [S, n_b] block
+  const int64_t* rec_off;    // [B] offset of tour b's StepRecs
+  const int32_t* order;      // [B] tours by decreasing n
+  const StepRec* rec;
+  const double* Dn;          // [B]
+  const int32_t* demands;
+  float* costs;              // [B*S]
+  unsigned long long* counter;
+  unsigned long long* fb_list;  // [B*S] global scenario ids b*S+s
+  uint32_t* fb_count;
+  uint32_t* status;
+};
+size_t batch_smem(int n_max, int Q, int warps, int ring);
+struct BatchPrepArgs {
+  const int32_t* n;
+  const int64_t* tour_off;
+  const int64_t* coord_off;
+  const int64_t* rec_off;
+  const int32_t* tours;
+  const float* coords;
+  StepRec* rec;
+  double* Dn;
+  unsigned long long* counter;  // reset to 0 by the prep kernel
+  uint32_t* fb_count;           // reset to 0 by the prep kernel
+  uint32_t* status;
+};
+void launch_batch_prep(const BatchPrepArgs& a, int B, cudaStream_t st);
+void launch_batch_means(const float* costs, int B, int64_t S, double* means, cudaStream_t st);
+void launch_batch_count(const BatchPrepArgs& a, int B, int64_t S, int Q, const int64_t* dem_off,
+                        const int32_t* demands, unsigned long long* total, cudaStream_t st);
+struct BatchFallbackArgs {
+  int Q;
+  int64_t S;
+  const int32_t* n;
+  const int64_t* dem_off;
+  const int64_t* rec_off;
+  const StepRec* rec;
+  const double* Dn;
+  const int32_t* demands;
+  float* costs;
+  const unsigned long long* fb_list;
+  const uint32_t* fb_count;
+  float* kscratch;   // [(n_max+1) * nslots]
+  int64_t nslots;
+};
+void launch_batch_fallback(const BatchFallbackArgs& a, cudaStream_t st);
+int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int grid,
+                       cudaStream_t st, int* occ_out);
+
+// arc counting (capacity-feasible (p,i) pairs)
+void launch_count_arcs(int n, int Q, int64_t S, const StepRec* rec,
+                       const int32_t* demands, int64_t* arcs,
+                       unsigned long long* total, int grid, cudaStream_t st);
+
+// FP64 mean of a float array, deterministic (fixed blocking and order)
+constexpr int kMeanBlocks = 512;
+void launch_mean(const float* x, int64_t count, double* partial /*[kMeanBlocks]*/,
+                 double* out, cudaStream_t st);
+
+// adjoint assembly: grad[(n+1)^2] = counts / S * (*grad_mean)
+void launch_grad_assemble(int n, int64_t S, const int32_t* tour,
+                          const unsigned long long* hist, const float* grad_mean,
+                          float* grad, int64_t* hist_out, cudaStream_t st);
+void launch_backtrack_hist(int n, int64_t S, const void* pred, int pred_dtype,
+                           unsigned long long* hist, uint32_t* status,
+                           cudaStream_t st);
+
+// reinsertion
+struct ReinsertArgs {
+  int T, U, I0;
+  float h, p, c;
+  int64_t S;
+  const float* fixed;
+  const float* table;
+  const int32_t* cons;
+  float* value;
+  uint8_t* policy;
+  float* value0;
+  uint32_t* status;
+};
+int launch_reinsert(const ReinsertArgs& a, cudaStream_t st);
+
+int num_sms();
+
+}  // namespace sdp

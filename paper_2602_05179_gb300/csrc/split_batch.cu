@@ -1,0 +1,370 @@
+// split_batch.cu -- plans for batched Split: thousands of giant tours of
+// uneven length (first-stage candidates) times S scenarios each, evaluated by
+// one persistent launch replayed from a CUDA graph.
+//
+// A plan owns: per-tour metadata on the device (n_b, offsets, the order of
+// tours by decreasing n_b), the concatenated tour records, the per-tour D(n)
+// in FP64, the work-queue counter, the fallback list and its scratch.  One
+// run = [tour prep for every tour (also resets the counter) -> persistent
+// DEQUE kernel over (tour, 32-scenario tile) items -> plain fallback for
+// flagged scenarios -> per-tour FP64 means], captured once in a CUDA graph
+// and replayed.  sdp_plan_autotune times the launch shapes (warps per CTA x
+// deque ring size) and keeps the fastest; choices can be cached in a text
+// file keyed by the device and the plan's shape.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sdp_internal.cuh"
+
+struct sdp_plan {
+  int device = 0;
+  int B = 0, Q = 0, n_max = 0;
+  int64_t S = 0, sum_n = 0;
+  // device arrays owned by the plan
+  int32_t* d_n = nullptr;
+  int64_t* d_tour_off = nullptr;
+  int64_t* d_coord_off = nullptr;
+  int64_t* d_dem_off = nullptr;
+  int64_t* d_rec_off = nullptr;
+  int32_t* d_order = nullptr;
+  sdp::StepRec* d_rec = nullptr;
+  double* d_Dn = nullptr;
+  unsigned long long* d_counter = nullptr;
+  uint32_t* d_fb_count = nullptr;
+  unsigned long long* d_fb_list = nullptr;
+  float* d_kscratch = nullptr;
+  int64_t nslots = 0;
+  unsigned long long* d_total = nullptr;
+  // caller's arrays
+  const int32_t* tours = nullptr;
+  const float* coords = nullptr;
+  const int32_t* demands = nullptr;
+  float* costs = nullptr;
+  double* means = nullptr;
+  // launch shape
+  int warps = 4, ring = 16, grid = 0;
+  // graph
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent kernel
+  int64_t total_arcs = -1;
+};
+
+namespace sdp {
+int status_word(uint32_t** out);               // sdp_api.cu
+int api_fail(int code, const char* msg);       // sdp_api.cu
+namespace {
+
+int pfail(int code, const char* msg) { return api_fail(code, msg); }
+
+int pcuda(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  return api_fail(SDP_ERR_CUDA, buf);
+}
+
+template <typename T>
+cudaError_t alloc_copy(T** dst, const T* src, size_t count) {
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) return e;
+  if (src && count) e = cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+  return e;
+}
+
+BatchPrepArgs prep_args(const sdp_plan* p, uint32_t* status) {
+  BatchPrepArgs a{};
+  a.n = p->d_n;
+  a.tour_off = p->d_tour_off;
+  a.coord_off = p->d_coord_off;
+  a.rec_off = p->d_rec_off;
+  a.tours = p->tours;
+  a.coords = p->coords;
+  a.rec = p->d_rec;
+  a.Dn = p->d_Dn;
+  a.counter = p->d_counter;
+  a.fb_count = p->d_fb_count;
+  a.status = status;
+  return a;
+}
+
+int configure(sdp_plan* p, int warps, int ring) {
+  if (batch_smem(p->n_max, p->Q, warps, ring) > 227 * 1024) return SDP_ERR_UNSUPPORTED;
+  BatchKernelArgs k{};
+  k.n_max = p->n_max;
+  k.Q = p->Q;
+  int occ = 0;
+  int e = launch_split_batch(k, warps, ring, 0, nullptr, &occ);
+  if (e) return pcuda((cudaError_t)e, "batch occupancy");
+  if (occ < 1) return SDP_ERR_UNSUPPORTED;
+  const int64_t items = (int64_t)p->B * ((p->S + 31) / 32);
+  const int64_t want = (items + warps - 1) / warps;
+  p->warps = warps;
+  p->ring = ring;
+  p->grid = (int)std::min<int64_t>(want, (int64_t)occ * num_sms());
+  return SDP_OK;
+}
+
+int enqueue(sdp_plan* p, cudaStream_t st, uint32_t* status, bool with_events) {
+  launch_batch_prep(prep_args(p, status), p->B, st);
+  BatchKernelArgs k{};
+  k.B = p->B; k.Q = p->Q; k.n_max = p->n_max; k.S = p->S;
+  k.n = p->d_n; k.dem_off = p->d_dem_off; k.rec_off = p->d_rec_off; k.order = p->d_order;
+  k.rec = p->d_rec; k.Dn = p->d_Dn; k.demands = p->demands; k.costs = p->costs;
+  k.counter = p->d_counter; k.fb_list = p->d_fb_list; k.fb_count = p->d_fb_count;
+  k.status = status;
+  if (with_events) cudaEventRecord(p->ev0, st);
+  int e = launch_split_batch(k, p->warps, p->ring, p->grid, st, nullptr);
+  if (with_events) cudaEventRecord(p->ev1, st);
+  if (e) return pcuda((cudaError_t)e, "batch kernel");
+  BatchFallbackArgs f{};
+  f.Q = p->Q; f.S = p->S; f.n = p->d_n; f.dem_off = p->d_dem_off; f.rec_off = p->d_rec_off;
+  f.rec = p->d_rec; f.Dn = p->d_Dn; f.demands = p->demands; f.costs = p->costs;
+  f.fb_list = p->d_fb_list; f.fb_count = p->d_fb_count; f.kscratch = p->d_kscratch;
+  f.nslots = p->nslots;
+  launch_batch_fallback(f, st);
+  if (p->means) launch_batch_means(p->costs, p->B, p->S, p->means, st);
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return pcuda(ce, "batch enqueue");
+  return SDP_OK;
+}
+
+void drop_graph(sdp_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  p->exec = nullptr;
+}
+
+std::string cache_key(const sdp_plan* p) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, p->device);
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|sm%d|B%d|S%lld|Q%d|nmax%d|sumn%lld", prop.name,
+           prop.multiProcessorCount, p->B, (long long)p->S, p->Q, p->n_max,
+           (long long)p->sum_n);
+  std::string k(buf);
+  for (char& c : k)
+    if (c == ' ') c = '_';
+  return k;
+}
+
+}  // namespace
+}  // namespace sdp
+
+using namespace sdp;
+
+extern "C" {
+
+void sdp_plan_destroy(sdp_plan* p) {
+  if (!p) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  drop_graph(p);
+  cudaFree(p->d_n); cudaFree(p->d_tour_off); cudaFree(p->d_coord_off);
+  cudaFree(p->d_dem_off); cudaFree(p->d_rec_off); cudaFree(p->d_order);
+  cudaFree(p->d_rec); cudaFree(p->d_Dn); cudaFree(p->d_counter); cudaFree(p->d_fb_count);
+  cudaFree(p->d_fb_list); cudaFree(p->d_kscratch); cudaFree(p->d_total);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  cudaSetDevice(prev);
+  delete p;
+}
+
+int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out) {
+  if (!d || !out) return pfail(SDP_ERR_INVALID_ARG, "desc / out is NULL");
+  *out = nullptr;
+  if (d->B < 1) return pfail(SDP_ERR_INVALID_ARG, "B < 1");
+  if (d->Q < 1 || d->Q > 32767) return pfail(SDP_ERR_UNSUPPORTED, "batched Split needs 1 <= Q <= 32767");
+  if (d->S < 1) return pfail(SDP_ERR_INVALID_ARG, "S < 1");
+  if ((double)d->B * (double)d->S > 1.8e19) return pfail(SDP_ERR_UNSUPPORTED, "B*S too large");
+  if (!d->n_host || !d->tour_off_host || !d->coord_off_host || !d->dem_off_host)
+    return pfail(SDP_ERR_INVALID_ARG, "host offset arrays must be set");
+  if (!d->tours || !d->coords || !d->demands || !d->costs_out)
+    return pfail(SDP_ERR_INVALID_ARG, "tours / coords / demands / costs_out must be set");
+  auto* p = new sdp_plan();
+  cudaGetDevice(&p->device);
+  p->B = d->B; p->Q = d->Q; p->S = d->S;
+  p->tours = d->tours; p->coords = d->coords; p->demands = d->demands;
+  p->costs = d->costs_out; p->means = d->means_out;
+  std::vector<int64_t> rec_off(d->B);
+  for (int b = 0; b < d->B; ++b) {
+    const int n = d->n_host[b];
+    if (n < 1 || n > 65534) { sdp_plan_destroy(p); return pfail(SDP_ERR_UNSUPPORTED, "n_b outside 1..65534"); }
+    if (d->tour_off_host[b] < 0 || d->coord_off_host[b] < 0 || d->dem_off_host[b] < 0) {
+      sdp_plan_destroy(p);
+      return pfail(SDP_ERR_INVALID_ARG, "negative offset");
+    }
+    rec_off[b] = p->sum_n;
+    p->sum_n += n;
+    p->n_max = std::max(p->n_max, n);
+  }
+  std::vector<int32_t> order(d->B);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return d->n_host[a] > d->n_host[b]; });
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chk(alloc_copy(&p->d_n, d->n_host, d->B));
+  chk(alloc_copy(&p->d_tour_off, d->tour_off_host, d->B));
+  chk(alloc_copy(&p->d_coord_off, d->coord_off_host, d->B));
+  chk(alloc_copy(&p->d_dem_off, d->dem_off_host, d->B));
+  chk(alloc_copy(&p->d_rec_off, rec_off.data(), d->B));
+  chk(alloc_copy(&p->d_order, order.data(), d->B));
+  chk(alloc_copy<StepRec>(&p->d_rec, nullptr, p->sum_n));
+  chk(alloc_copy<double>(&p->d_Dn, nullptr, d->B));
+  chk(alloc_copy<unsigned long long>(&p->d_counter, nullptr, 1));
+  chk(alloc_copy<uint32_t>(&p->d_fb_count, nullptr, 1));
+  chk(alloc_copy<unsigned long long>(&p->d_fb_list, nullptr, (size_t)d->B * d->S));
+  p->nslots = std::min<int64_t>((int64_t)d->B * d->S, 4096);
+  chk(alloc_copy<float>(&p->d_kscratch, nullptr, (size_t)(p->n_max + 1) * p->nslots));
+  chk(alloc_copy<unsigned long long>(&p->d_total, nullptr, 1));
+  if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    sdp_plan_destroy(p);
+    return e == cudaErrorMemoryAllocation ? pfail(SDP_ERR_OOM, "plan allocation failed")
+                                          : pcuda(e, "plan create");
+  }
+  int rc = configure(p, 4, 16);
+  if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 1, 8);
+  if (rc) {
+    sdp_plan_destroy(p);
+    return pfail(rc, "no launch shape of the batched kernel fits this plan");
+  }
+  *out = p;
+  return SDP_OK;
+}
+
+int sdp_plan_run(sdp_plan* p, void* stream) {
+  if (!p) return pfail(SDP_ERR_INVALID_ARG, "plan is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* status;
+  int rc = status_word(&status);
+  if (rc) return rc;
+  if (!p->exec) {
+    // capture on a private stream so the caller's stream may be the legacy one
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return pcuda(e, "capture stream");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); return pcuda(e, "begin capture"); }
+    rc = enqueue(p, cs, status, true);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return pcuda(e, "end capture");
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { p->exec = nullptr; return pcuda(e, "graph instantiate"); }
+  }
+  cudaError_t e = cudaGraphLaunch(p->exec, st);
+  if (e != cudaSuccess) return pcuda(e, "graph launch");
+  return SDP_OK;
+}
+
+int sdp_plan_kernel_ms(sdp_plan* p, float* ms) {
+  if (!p || !ms) return pfail(SDP_ERR_INVALID_ARG, "NULL argument");
+  cudaError_t e = cudaEventSynchronize(p->ev1);
+  if (e != cudaSuccess) return pcuda(e, "event sync");
+  e = cudaEventElapsedTime(ms, p->ev0, p->ev1);
+  if (e != cudaSuccess) return pcuda(e, "elapsed");
+  return SDP_OK;
+}
+
+int sdp_plan_info(const sdp_plan* p, int32_t* warps_per_cta, int32_t* ring, int32_t* ctas,
+                  int64_t* items) {
+  if (!p) return pfail(SDP_ERR_INVALID_ARG, "plan is NULL");
+  if (warps_per_cta) *warps_per_cta = p->warps;
+  if (ring) *ring = p->ring;
+  if (ctas) *ctas = p->grid;
+  if (items) *items = (int64_t)p->B * ((p->S + 31) / 32);
+  return SDP_OK;
+}
+
+int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
+  if (!p) return pfail(SDP_ERR_INVALID_ARG, "plan is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const std::string key = cache_key(p);
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "r");
+    if (f) {
+      char line[512];
+      while (fgets(line, sizeof(line), f)) {
+        char k[400];
+        int w = 0, r = 0;
+        if (sscanf(line, "%399s %d %d", k, &w, &r) == 3 && key == k) {
+          fclose(f);
+          drop_graph(p);
+          int rc = configure(p, w, r);
+          return rc ? configure(p, 4, 16) : SDP_OK;
+        }
+      }
+      fclose(f);
+    }
+  }
+  uint32_t* status;
+  int rc = status_word(&status);
+  if (rc) return rc;
+  const int warps_c[] = {1, 2, 4, 8};
+  const int ring_c[] = {8, 16};
+  float best = 1e30f;
+  int bw = p->warps, br = p->ring;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (int w : warps_c)
+    for (int r : ring_c) {
+      if (configure(p, w, r)) continue;
+      float tsum = 0.f;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        cudaEventRecord(a, st);
+        ok = enqueue(p, st, status, false) == SDP_OK;
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) tsum += ms;  // first rep warms up
+      }
+      if (ok && tsum < best) { best = tsum; bw = w; br = r; }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  drop_graph(p);
+  rc = configure(p, bw, br);
+  if (rc) return rc;
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "a");
+    if (f) {
+      fprintf(f, "%s %d %d\n", key.c_str(), bw, br);
+      fclose(f);
+    }
+  }
+  return SDP_OK;
+}
+
+int sdp_plan_count_arcs(sdp_plan* p, void* stream, uint64_t* total_host) {
+  if (!p || !total_host) return pfail(SDP_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* status;
+  int rc = status_word(&status);
+  if (rc) return rc;
+  cudaMemsetAsync(p->d_total, 0, sizeof(unsigned long long), st);
+  launch_batch_prep(prep_args(p, status), p->B, st);
+  launch_batch_count(prep_args(p, status), p->B, p->S, p->Q, p->d_dem_off, p->demands,
+                     p->d_total, st);
+  unsigned long long t = 0;
+  cudaError_t e = cudaMemcpyAsync(&t, p->d_total, sizeof(t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return pcuda(e, "count arcs");
+  *total_host = t;
+  p->total_arcs = (int64_t)t;
+  return SDP_OK;
+}
+
+}  // extern "C"

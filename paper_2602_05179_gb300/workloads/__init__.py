@@ -247,3 +247,77 @@ def batch_demands(spec: BatchSpec, b: int, n_b: int, s0: int = 0, s1: int | None
     st = ST_BATCH0 + 4 * b + 2
     q = poisson_clip(spec.seed, st, s0 * n_b, (s1 - s0) * n_b, spec.lam, 1, spec.Q)
     return q.reshape(s1 - s0, n_b)
+
+
+# --------------------------------------------------------------------------
+# Device twin (gen.cu, libsdpgen.so): the same counter-mode draws written
+# straight into CUDA tensors, for inputs too large to build on the host.
+_GEN = None
+
+
+def _gen():
+    global _GEN
+    if _GEN is None:
+        import ctypes
+        import os
+        path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "libsdpgen.so")
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        u64, i64, i32, P = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+        lib.sdpgen_uniform_int.argtypes = [u64, u64, i64, i64, i32, i32, P, P]
+        lib.sdpgen_uniform_int.restype = ctypes.c_int
+        lib.sdpgen_poisson_clip.argtypes = [u64, u64, i64, i64, P, ctypes.c_int, i32, i32, P, P]
+        lib.sdpgen_poisson_clip.restype = ctypes.c_int
+        _GEN = lib
+    return _GEN
+
+
+def _dev_out(out):
+    import torch
+    assert out.is_cuda and out.dtype == torch.int32 and out.is_contiguous()
+    return out.data_ptr(), torch.cuda.current_stream().cuda_stream
+
+
+def device_uniform_int(out, seed, stream, k0, lo, hi):
+    ptr, st = _dev_out(out)
+    rc = _gen().sdpgen_uniform_int(seed, stream, k0, out.numel(), lo, hi, ptr, st)
+    if rc != 0:
+        raise RuntimeError(f"sdpgen_uniform_int failed: {rc}")
+    return out
+
+
+def device_poisson_clip(out, seed, stream, k0, lam, lo, hi):
+    import torch
+    cdf = torch.from_numpy(poisson_cdf(lam)).to(out.device)
+    ptr, st = _dev_out(out)
+    rc = _gen().sdpgen_poisson_clip(seed, stream, k0, out.numel(), cdf.data_ptr(),
+                                    int(cdf.numel()), lo, hi, ptr, st)
+    if rc != 0:
+        raise RuntimeError(f"sdpgen_poisson_clip failed: {rc}")
+    torch.cuda.current_stream().synchronize()  # keep cdf alive until the kernel ran
+    return out
+
+
+def split_demands_device(spec: SplitSpec, device="cuda", s0=0, s1=None):
+    """Rows s0..s1-1 of the demand matrix generated on the device."""
+    import torch
+    s1 = spec.S if s1 is None else s1
+    out = torch.empty((s1 - s0, spec.n), dtype=torch.int32, device=device)
+    if spec.demand == "uniform":
+        return device_uniform_int(out, spec.seed, ST_DEMAND, s0 * spec.n, spec.lo, spec.hi)
+    return device_poisson_clip(out, spec.seed, ST_DEMAND, s0 * spec.n, spec.lam, spec.lo, spec.hi)
+
+
+def reinsert_consumption_device(spec: ReinsertSpec, device="cuda", s0=0, s1=None):
+    import torch
+    s1 = spec.S if s1 is None else s1
+    out = torch.empty((s1 - s0, spec.T), dtype=torch.int32, device=device)
+    return device_poisson_clip(out, spec.seed, ST_CONS, s0 * spec.T, spec.lam, 0, 1 << 30)
+
+
+def batch_demands_device(spec: BatchSpec, b: int, n_b: int, out):
+    """Fill out (int32 [S, n_b] CUDA view) with tour b's demands."""
+    st = ST_BATCH0 + 4 * b + 2
+    return device_poisson_clip(out, spec.seed, st, 0, spec.lam, 1, spec.Q)

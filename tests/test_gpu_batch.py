@@ -1,0 +1,139 @@
+"""GPU parity of the batched Split plan (persistent kernel + CUDA graph +
+autotuned launch shape) against the FP64 oracle and the eager kernels."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_05179_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def api():
+    from paper_2602_05179_gb300 import api as a
+    return a
+
+
+def _batch(seed, B, S, Q, nlo, nhi, qhi):
+    rng = np.random.default_rng(seed)
+    n = rng.integers(nlo, nhi + 1, size=B).astype(np.int32)
+    tours, coords, dem = [], [], []
+    for b in range(B):
+        tours.append((rng.permutation(n[b]) + 1).astype(np.int32))
+        xy = np.empty((n[b] + 1, 2), np.float32)
+        xy[0] = (50, 50)
+        xy[1:] = rng.uniform(0, 100, (n[b], 2)).astype(np.float32)
+        coords.append(xy)
+        dem.append(rng.integers(1, qhi + 1, size=(S, n[b])).astype(np.int32))
+    return n, tours, coords, dem
+
+
+def _plan(n, tours, coords, dem, Q, S):
+    t = torch.from_numpy(np.concatenate(tours)).cuda()
+    c = torch.from_numpy(np.concatenate(coords)).cuda()
+    d = torch.from_numpy(np.concatenate([x.reshape(-1) for x in dem])).cuda()
+    return api().SplitPlan(n, t, c, d, Q, S), (t, c, d)
+
+
+@pytest.mark.parametrize("Q,qhi", [(150, 40), (400, 90)])
+def test_batch_small_vs_oracle_and_eager(Q, qhi, tmp_path):
+    B, S = 37, 100
+    n, tours, coords, dem = _batch(11 + Q, B, S, Q, 1, 300, qhi)
+    plan, keep = _plan(n, tours, coords, dem, Q, S)
+    costs, means = plan.run()
+    torch.cuda.synchronize()
+    c1 = costs.clone()
+    for b in range(B):
+        o = oracle.split(tours[b], Q, dem[b], coords=coords[b])
+        g = costs[b].cpu().double().numpy()
+        rel = np.abs(g - o["cost"]) / o["cost"]
+        assert rel.max() <= 1e-5, (b, rel.max())
+        assert abs(float(means[b]) - o["mean"]) <= 1e-5 * o["mean"]
+        # same bits as the eager single-tour call
+        r = api().split_eval(torch.from_numpy(tours[b]).cuda(), Q,
+                             torch.from_numpy(dem[b]).cuda(),
+                             coords=torch.from_numpy(coords[b]).cuda(), algo="deque")
+        assert torch.equal(r["cost"], costs[b])
+    # graph replay, then autotune (+ cache) give the same bits
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(costs, c1)
+    cache = str(tmp_path / "tune.txt")
+    info = plan.autotune(cache)
+    assert info["warps_per_cta"] in (1, 2, 4, 8) and info["ring"] in (8, 16)
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(costs, c1)
+    assert os.path.exists(cache)
+    assert plan.autotune(cache) == info   # cache hit
+    arcs = plan.count_arcs()
+    assert arcs == sum(int(oracle.split(tours[b], Q, dem[b], coords=coords[b])["arcs"].sum())
+                       for b in range(B))
+    assert plan.kernel_ms() > 0
+    assert api().status() & api().FLAG_INFEASIBLE == 0
+    plan.close()
+
+
+def test_batch_infeasible_and_fallback():
+    """Scenarios with a demand above Q and with zero-cost ties (deque ring
+    overflow -> plain fallback) inside a batch."""
+    B, S, Q = 5, 70, 12
+    rng = np.random.default_rng(3)
+    n = np.array([40, 7, 33, 1, 20], np.int32)
+    tours = [(rng.permutation(k) + 1).astype(np.int32) for k in n]
+    coords = [np.full((k + 1, 2), 50.0, np.float32) if b % 2 == 0 else
+              np.concatenate([[[50, 50]], rng.uniform(0, 100, (k, 2))]).astype(np.float32)
+              for b, k in enumerate(n)]
+    dem = [rng.integers(0, 3, size=(S, k)).astype(np.int32) for k in n]
+    dem[1][5, 3] = Q + 1
+    plan, keep = _plan(n, tours, coords, dem, Q, S)
+    costs, means = plan.run()
+    torch.cuda.synchronize()
+    for b in range(B):
+        o = oracle.split(tours[b], Q, dem[b], coords=coords[b])
+        g = costs[b].cpu().double().numpy()
+        assert np.array_equal(np.isinf(g), np.isinf(o["cost"]))
+        f = np.isfinite(g)
+        assert np.all(np.abs(g[f] - o["cost"][f]) <= 1e-5 * np.maximum(o["cost"][f], 1e-30))
+    assert np.isinf(float(means[1]))
+    fl = api().status()
+    assert fl & api().FLAG_INFEASIBLE and fl & api().FLAG_FALLBACK
+    plan.close()
+
+
+def test_batch_c4_full_size_sampled():
+    """4096 tours, n_b ~ U{20..1000}, S=4096 each (34 GB of demands generated
+    on the device), sampled (tour, scenario) pairs checked against the
+    oracle and every per-tour mean against the FP32 costs."""
+    spec = wl.BATCH_C4
+    nb = wl.batch_sizes(spec)
+    tours, coords = zip(*(wl.batch_tour(spec, b, int(nb[b])) for b in range(spec.B)))
+    dem_off = np.zeros(spec.B, np.int64)
+    dem_off[1:] = np.cumsum(nb[:-1].astype(np.int64) * spec.S)
+    total = int(dem_off[-1] + nb[-1] * spec.S)
+    d = torch.empty(total, dtype=torch.int32, device="cuda")
+    for b in range(spec.B):
+        seg = d[dem_off[b]:dem_off[b] + nb[b] * spec.S].view(spec.S, int(nb[b]))
+        wl.batch_demands_device(spec, b, int(nb[b]), seg)
+    t = torch.from_numpy(np.concatenate(tours)).cuda()
+    c = torch.from_numpy(np.concatenate(coords)).cuda()
+    plan = api().SplitPlan(nb, t, c, d, spec.Q, spec.S, dem_off=dem_off)
+    costs, means = plan.run()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    for b in rng.choice(spec.B, 48, replace=False):
+        rows = np.sort(rng.choice(spec.S, 8, replace=False))
+        q = np.concatenate([wl.batch_demands(spec, int(b), int(nb[b]), int(s), int(s) + 1)
+                            for s in rows])
+        np.testing.assert_array_equal(
+            q, d[dem_off[b]:dem_off[b] + nb[b] * spec.S].view(spec.S, -1)[rows].cpu().numpy())
+        o = oracle.split(tours[b], spec.Q, q, coords=coords[b])
+        g = costs[int(b)][rows].cpu().double().numpy()
+        assert (np.abs(g - o["cost"]) / o["cost"]).max() <= 1e-5
+    host_means = costs.double().mean(1)
+    assert torch.allclose(means, host_means, rtol=1e-12, atol=0)
+    assert api().status() & (api().FLAG_INFEASIBLE | api().FLAG_FALLBACK) == 0
+    plan.close()

@@ -1,0 +1,172 @@
+"""GPU parity of the Split kernels (PLAIN and DEQUE) against the FP64 oracle,
+through the C ABI (paper_2602_05179_gb300.api -> libsdp.so)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_05179_gb300 import workloads as wl
+from tests.golden_io import arr, load
+from tests.gpu_util import check_split, preds_to_i64
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def sdp():
+    from paper_2602_05179_gb300 import api
+    return api
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+ALGOS = ["plain", "deque"]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_split_paper_toy(algo):
+    g = load("split_toy.json")
+    dist = np.asarray(g["cost_matrix"], np.float32)
+    tour = arr(g["tour"], np.int32)
+    q = arr(g["demand_by_customer"], np.int32)[None, :]
+    r = sdp().split_eval(_cuda(tour), g["Q"], _cuda(q), dist=_cuda(dist), preds="i32",
+                         algo=algo)
+    torch.cuda.synchronize()
+    assert float(r["cost"][0]) == g["V"][-1]
+    assert preds_to_i64(r["pred"])[0].tolist() == g["pred"]
+    assert float(r["mean"]) == g["V"][-1]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("preds", ["u16", "i32"])
+def test_split_c1_full(algo, preds):
+    """n=50, S=1000 (ragged: 1000 = 31 tiles of 32 + 8; 50 % 4 = 2)."""
+    spec = wl.SPLIT_C1
+    tour, xy, _ = wl.split_tour(spec)
+    q = wl.split_demands(spec)
+    orc = oracle.split(tour, spec.Q, q, coords=xy, want_margin=True)
+    r = sdp().split_eval(_cuda(tour), spec.Q, _cuda(q), coords=_cuda(xy), preds=preds,
+                         algo=algo)
+    torch.cuda.synchronize()
+    check_split(r["cost"], r["pred"], orc)
+    assert abs(float(r["mean"]) - orc["mean"]) <= 1e-5 * orc["mean"]
+    assert sdp().status() & (sdp().FLAG_INFEASIBLE | sdp().FLAG_DEVICE_CHECK) == 0
+
+
+def _random_case(seed, n, S, Q, qlo, qhi, dist_mode=False):
+    rng = np.random.default_rng(seed)
+    xy = np.empty((n + 1, 2), np.float32)
+    xy[0] = (50, 50)
+    xy[1:] = rng.uniform(0, 100, (n, 2)).astype(np.float32)
+    tour = (rng.permutation(n) + 1).astype(np.int32)
+    q = rng.integers(qlo, qhi + 1, size=(S, n)).astype(np.int32)
+    dist = wl.dist_matrix_f32(xy) if dist_mode else None
+    return tour, xy, dist, q
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("case", [
+    # (seed, n, S, Q, qlo, qhi, dist)
+    (1, 1, 33, 10, 1, 10, False),       # n = 1
+    (2, 3, 70, 10, 1, 12, False),       # n < 4: scalar ingest; some infeasible
+    (3, 7, 65, 15, 0, 9, True),         # zero demands, dist mode
+    (4, 37, 200, 40, 1, 45, False),     # infeasible scenarios (demand > Q)
+    (5, 64, 97, 255, 1, 60, False),     # uint16 staging (Q >= 255)
+    (6, 129, 64, 300, 0, 3, False),     # long windows: > 255 customers per route
+    (7, 250, 131, 30000, 1, 500, False),  # uint16, large Q, long routes
+])
+def test_split_edge_cases(algo, case):
+    seed, n, S, Q, qlo, qhi, dm = case
+    tour, xy, dist, q = _random_case(seed, n, S, Q, qlo, qhi, dm)
+    kw = {"dist": dist} if dm else {"coords": xy}
+    orc = oracle.split(tour, Q, q, want_margin=True, **kw)
+    r = sdp().split_eval(_cuda(tour), Q, _cuda(q), preds="i32", algo=algo,
+                         **{k: _cuda(v) for k, v in kw.items()})
+    torch.cuda.synchronize()
+    check_split(r["cost"], r["pred"], orc, min_checked=0.0)
+    if np.isinf(orc["cost"]).any():
+        assert np.isinf(float(r["mean"]))
+        assert sdp().status() & sdp().FLAG_INFEASIBLE
+    else:
+        assert abs(float(r["mean"]) - orc["mean"]) <= 1e-5 * abs(orc["mean"])
+        sdp().status()
+
+
+@pytest.mark.parametrize("ring", [8, 16, 32])
+@pytest.mark.parametrize("warps", [1, 3, 8])
+def test_split_deque_tilings_bit_identical(ring, warps):
+    """Every launch shape gives the same bits as the plain kernel."""
+    spec = wl.SPLIT_C1
+    tour, xy, _ = wl.split_tour(spec)
+    q = wl.split_demands(spec)
+    args = (_cuda(tour), spec.Q, _cuda(q))
+    ref = sdp().split_eval(*args, coords=_cuda(xy), preds="i32", algo="plain")
+    r = sdp().split_eval(*args, coords=_cuda(xy), preds="i32", algo="deque", warps=warps,
+                         ring=ring)
+    torch.cuda.synchronize()
+    assert torch.equal(r["cost"], ref["cost"])
+    assert torch.equal(r["pred"], ref["pred"])
+    assert float(r["mean"]) == float(ref["mean"])
+
+
+def test_split_deque_ring_overflow_fallback():
+    """All travel costs zero: every candidate ties, the deque keeps them all
+    (equal psi is never popped), so windows longer than the ring overflow and
+    those scenarios are recomputed by the plain kernel."""
+    n, S, Q = 40, 70, 12
+    rng = np.random.default_rng(9)
+    tour = (rng.permutation(n) + 1).astype(np.int32)
+    q = rng.integers(0, 3, size=(S, n)).astype(np.int32)
+    xy = np.full((n + 1, 2), 50.0, np.float32)
+    orc = oracle.split(tour, Q, q, coords=xy, want_margin=True)
+    r = sdp().split_eval(_cuda(tour), Q, _cuda(q), coords=_cuda(xy), preds="i32",
+                         algo="deque", ring=8)
+    torch.cuda.synchronize()
+    assert sdp().status() & sdp().FLAG_FALLBACK
+    # exact ties everywhere: both sides keep the smallest p
+    np.testing.assert_array_equal(preds_to_i64(r["pred"]), orc["pred"])
+    np.testing.assert_array_equal(r["cost"].cpu().numpy(), 0.0)
+
+
+def test_split_count_arcs_matches_oracle():
+    spec = wl.SPLIT_C1
+    tour, xy, _ = wl.split_tour(spec)
+    q = wl.split_demands(spec)
+    orc = oracle.split(tour, spec.Q, q, coords=xy)
+    arcs, total = sdp().split_count_arcs(_cuda(tour), spec.Q, _cuda(q), coords=_cuda(xy))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(arcs.cpu().numpy(), orc["arcs"])
+    assert int(total) == int(orc["arcs"].sum())
+
+
+def test_split_c2_full_size_sampled():
+    """n=500, S=10^6 generated on the device, in the launch configuration the
+    benchmark times (DEQUE, uint16 predecessors); sampled scenarios checked
+    one by one against the oracle, all scenarios against the plain kernel."""
+    spec = wl.SPLIT_C2
+    tour, xy, _ = wl.split_tour(spec)
+    qd = wl.split_demands_device(spec)
+    # device generator == host definition on a slice
+    np.testing.assert_array_equal(qd[123_456:123_456 + 40].cpu().numpy(),
+                                  wl.split_demands(spec, 123_456, 123_496))
+    t, c = _cuda(tour), _cuda(xy)
+    r = sdp().split_eval(t, spec.Q, qd, coords=c, preds="u16", algo="deque")
+    ref = sdp().split_eval(t, spec.Q, qd, coords=c, preds="u16", algo="plain")
+    torch.cuda.synchronize()
+    assert torch.equal(r["cost"], ref["cost"])
+    assert torch.equal(r["pred"], ref["pred"])
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(spec.S, 1500, replace=False))
+    rows = np.concatenate([rows, [0, 31, 32, spec.S - 1]])
+    qs = np.concatenate([wl.split_demands(spec, int(s), int(s) + 1) for s in rows])
+    orc = oracle.split(tour, spec.Q, qs, coords=xy, want_margin=True)
+    # J(i) ~ 2.6e4 here, so a 1e-4 relative gap is 2.6 distance units: about a
+    # third of the positions qualify; the 10x stricter 1e-5 gap covers more.
+    check_split(r["cost"], r["pred"], orc, rows=rows, min_checked=0.25)
+    frac = check_split(r["cost"], r["pred"], orc, rows=rows, margin=1e-5, min_checked=0.7)
+    assert frac > 0.7
+    # the mean over all 10^6 against the FP32 costs summed in FP64 on the host
+    host_mean = r["cost"].double().mean().item()
+    assert abs(float(r["mean"]) - host_mean) <= 1e-12 * host_mean
+    assert sdp().status() & (sdp().FLAG_INFEASIBLE | sdp().FLAG_FALLBACK) == 0
