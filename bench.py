@@ -195,6 +195,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-operators", action="store_true",
+                    help="skip the reinsertion / batched / adjoint operator lines")
     ap.add_argument("--scenarios", type=int, default=0,
                     help="override S per GPU (small cases for ncu captures)")
     args = ap.parse_args()
@@ -225,8 +227,9 @@ def main():
     tour, xy, _ = wl.split_tour(spec)
     t_d = torch.from_numpy(tour).to(dev)
     c_d = torch.from_numpy(xy).to(dev)
-    q_d = wl.split_demands_device(spec, dev, rank * S, (rank + 1) * S) if world > 1 else \
-        wl.split_demands_device(spec, dev)
+    from paper_2602_05179_gb300 import shard
+    s0, s1 = shard.scenario_range(rank, world, S)
+    q_d = wl.split_demands_device(spec, dev, s0, s1)
     _, total = api.split_count_arcs(t_d, spec.Q, q_d, coords=c_d, per_scenario=False)
     torch.cuda.synchronize()
     arcs_rank = int(total)
@@ -302,8 +305,13 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return 0
+    ops = None
+    if not args.no_operators and world == 1:
+        del q_d, r
+        torch.cuda.empty_cache()
+        ops = operators(api, wl, dev)
     return report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plain,
-                  e2e, flags, clocks, t_wall0, t_wall1, dist)
+                  e2e, flags, clocks, t_wall0, t_wall1, dist, ops)
 
 
 def e2e_run(args, api, spec, t_d, c_d, q_d, arcs_all, world, dist, dev):
@@ -331,8 +339,109 @@ def e2e_run(args, api, spec, t_d, c_d, q_d, arcs_all, world, dist, dev):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8, "steps": args.e2e_steps}
 
 
+def _timed(fn, steps, warmup=3, events=True):
+    """(ms per call, mean kernel ms via the profile hook) on the current stream."""
+    import torch
+    from paper_2602_05179_gb300 import api
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ks = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for ev in ks + ke:
+        ev.record()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for k in range(steps):
+        if events:
+            api.set_profile_events(ks[k], ke[k])
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    kern = statistics.mean(x.elapsed_time(y) for x, y in zip(ks, ke)) if events else None
+    return a.elapsed_time(b) / steps, kern
+
+
+def operators(api, wl, dev):
+    """The other hot-path operators at their workload sizes (few steps each)."""
+    import torch
+    peaks, src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    p_alu = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    hbm = peaks["hbm_gbs"]
+    out = {}
+    # ---- reinsertion T=60, U=200, S=10^6 (ALU bound)
+    rs = wl.REINSERT_C3
+    cons = wl.reinsert_consumption_device(rs, dev)
+    fixed = torch.from_numpy(wl.reinsert_fixed(rs)).to(dev)
+    fn = lambda: api.reinsert_eval(rs.T, rs.U, rs.I0, rs.h, rs.p, rs.unit_cost, fixed, cons)
+    ms, kms = _timed(fn, 10)
+    rel = 2.0 * (rs.U + 1) * rs.T * rs.S
+    out[rs.name] = {"value": rel / (ms / 1e3), "unit": "relaxations/s",
+                    "scenarios_per_s": rs.S / (ms / 1e3), "ms_per_step": ms, "kernel_ms": kms,
+                    "roofline": {"bound": "alu", "achieved": 2 * rel / (kms / 1e3),
+                                 "peak": p_alu, "unit": "ops/s",
+                                 "frac": 2 * rel / (kms / 1e3) / p_alu,
+                                 "peak_source": f"{sms} SMs x 128 lanes x sm_max_mhz ({src})"}}
+    del cons
+    # ---- adjoint n=300, S=10^5 (fused forward + on-chip backtrack)
+    ad = wl.ADJOINT_C5
+    tour, xy, distm = wl.split_tour(ad)
+    t = torch.from_numpy(tour).to(dev)
+    dm = torch.from_numpy(distm).to(dev)
+    q = wl.split_demands_device(ad, dev)
+    _, tot = api.split_count_arcs(t, ad.Q, q, dist=dm, per_scenario=False)
+    arcs = int(tot)
+    g = torch.ones((), dtype=torch.float32, device=dev)
+    fn = lambda: api.split_backward(t, ad.Q, q, dm, g)
+    ms, kms = _timed(fn, 20)
+    byts = ad.S * ad.n * 4
+    out[ad.name] = {"value": arcs / (ms / 1e3), "unit": "arcs/s (forward+backtrack)",
+                    "ms_per_step": ms, "kernel_ms": kms,
+                    "roofline": {"bound": "hbm", "achieved": byts / (kms / 1e3) / 1e9,
+                                 "peak": hbm, "unit": "GB/s",
+                                 "frac": byts / (kms / 1e3) / 1e9 / hbm},
+                    "alu_frac": 2 * arcs / (kms / 1e3) / p_alu}
+    fn2 = lambda: api.split_eval(t, ad.Q, q, dist=dm, algo="plain")
+    pms, _ = _timed(fn2, 5, events=False)
+    out[ad.name]["plain_forward_ms"] = pms
+    del q
+    # ---- batched: 4096 tours, n ~ U{20..1000}, S=4096 (persistent + graph)
+    bs = wl.BATCH_C4
+    nb = wl.batch_sizes(bs)
+    tours, coords = zip(*(wl.batch_tour(bs, b, int(nb[b])) for b in range(bs.B)))
+    dem_off = np.zeros(bs.B, np.int64)
+    dem_off[1:] = np.cumsum(nb[:-1].astype(np.int64) * bs.S)
+    total = int(dem_off[-1] + nb[-1] * bs.S)
+    d = torch.empty(total, dtype=torch.int32, device=dev)
+    for b in range(bs.B):
+        seg = d[dem_off[b]:dem_off[b] + nb[b] * bs.S].view(bs.S, int(nb[b]))
+        wl.batch_demands_device(bs, b, int(nb[b]), seg)
+    tt = torch.from_numpy(np.concatenate(tours)).to(dev)
+    cc = torch.from_numpy(np.concatenate(coords)).to(dev)
+    plan = api.SplitPlan(nb, tt, cc, d, bs.Q, bs.S, dem_off=dem_off)
+    arcs = plan.count_arcs()
+    import tempfile
+    tune = plan.autotune(os.path.join(tempfile.gettempdir(), "sdp_autotune_cache.txt"))
+    ms, _ = _timed(plan.run, 10, events=False)
+    kms = plan.kernel_ms()
+    byts = total * 4 + bs.B * bs.S * 4
+    out[bs.name] = {"value": arcs / (ms / 1e3), "unit": UNIT,
+                    "scenarios_per_s": bs.B * bs.S / (ms / 1e3), "ms_per_step": ms,
+                    "kernel_ms_last_replay": kms, "arcs_per_step": arcs, "launch": tune,
+                    "roofline": {"bound": "hbm", "achieved": byts / (kms / 1e3) / 1e9,
+                                 "peak": hbm, "unit": "GB/s",
+                                 "frac": byts / (kms / 1e3) / 1e9 / hbm},
+                    "alu_frac": 2 * arcs / (kms / 1e3) / p_alu}
+    plan.close()
+    del d
+    return out
+
+
 def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plain, e2e,
-           flags, clocks, t_wall0, t_wall1, dist):
+           flags, clocks, t_wall0, t_wall1, dist, ops=None):
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     peaks, peak_src = measured_peaks()
@@ -371,6 +480,7 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,
         "device_flags": flags,
+        "operators": ops,
         "clocks": clocks.summary(t_wall0, t_wall1),
     }
     if not args.no_cpu_baseline:

@@ -126,7 +126,11 @@ typedef struct sdp_split_args {
                              scenario is infeasible */
   void* workspace;        /* device scratch, >= sdp_split_workspace_bytes */
   size_t workspace_bytes;
-  int32_t warps_per_cta;  /* DEQUE tuning: 0 = default, else 1..16 */
+  int32_t warps_per_cta;  /* DEQUE tuning: 0 = default (demand rows staged in
+                             tensor memory when a row fits 512 bytes, 16
+                             warps per SM; else shared memory, 4 warps per
+                             CTA); 1..8 = shared-memory staging with that
+                             many warps per CTA */
   int32_t ring;           /* DEQUE tuning: deque ring entries per scenario,
                              0 = default, else 8, 16 or 32 */
 } sdp_split_args;

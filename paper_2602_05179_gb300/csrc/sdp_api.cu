@@ -169,8 +169,8 @@ int check_split(const sdp_split_args* a, bool need_cost) {
   }
   if (a->mean_out && !is_device_ptr(a->mean_out))
     return fail(SDP_ERR_INVALID_ARG, "mean_out must be a device pointer");
-  if (a->warps_per_cta < 0 || a->warps_per_cta > 16)
-    return fail(SDP_ERR_INVALID_ARG, "warps_per_cta must be 0..16");
+  if (a->warps_per_cta < 0 || a->warps_per_cta > 8)
+    return fail(SDP_ERR_INVALID_ARG, "warps_per_cta must be 0..8");
   if (a->ring != 0 && a->ring != 8 && a->ring != 16 && a->ring != 32)
     return fail(SDP_ERR_INVALID_ARG, "ring must be 0, 8, 16 or 32");
   return SDP_OK;
@@ -193,9 +193,13 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
   float* cost = hist ? nullptr : a->cost_out;
   void* pred = hist ? nullptr : a->pred_out;
   if (algo == SDP_ALGO_DEQUE) {
-    const int warps = a->warps_per_cta > 0 ? a->warps_per_cta : 4;
     const int ring = a->ring > 0 ? a->ring : 16;
-    DequeConfig cfg = deque_config(a->n, a->Q, warps, ring, hist != nullptr);
+    const int pbytes = pred ? (a->pred_dtype == SDP_PRED_U16 ? 2 : 4) : 0;
+    // warps_per_cta == 0: default launch, TMEM staging when the rows fit;
+    // an explicit warp count selects shared-memory staging with that shape.
+    DequeConfig cfg = deque_config(a->n, a->Q, a->warps_per_cta, ring, hist != nullptr, pbytes,
+                                   a->warps_per_cta == 0);
+    const int warps = cfg.warps;
     if (cfg.smem > 227 * 1024)
       return fail(SDP_ERR_UNSUPPORTED, "DEQUE tile needs %zu B of shared memory; lower warps_per_cta", cfg.smem);
     int occ = 0;

@@ -80,14 +80,19 @@ struct SplitDequeArgs {
   uint32_t* status;
 };
 struct DequeConfig {
-  int warps;     // warps per CTA
-  int ring;      // deque ring entries per scenario (8, 16, 32)
-  int qbytes;    // 1 (uint8 staging) or 2 (uint16 staging)
-  int row_stride;// bytes per staged demand row
-  size_t smem;   // dynamic shared memory per CTA
+  int warps;        // warps per CTA
+  int ring;         // deque ring entries per scenario (8, 16, 32)
+  int qbytes;       // 1 (uint8 staging) or 2 (uint16 staging)
+  int row_stride;   // bytes per staged demand row (shared-memory staging)
+  bool rec_in_smem; // tour records copied to shared memory (n <= 4096)
+  bool tmem;        // demand rows staged in tensor memory (16 warps, 1 CTA/SM)
+  size_t smem;      // dynamic shared memory per CTA
 };
 bool deque_supported(int n, int Q);
-DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist);
+// pred_bytes: size of one output predecessor (0 when none are written);
+// allow_tmem: stage demands in TMEM when a row fits 128 columns.
+DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_bytes,
+                         bool allow_tmem);
 // returns 0 or a cudaError_t
 int launch_split_deque(const SplitDequeArgs& a, const DequeConfig& c, int grid,
                        cudaStream_t st);

@@ -116,9 +116,11 @@ int enqueue(sdp_plan* p, cudaStream_t st, uint32_t* status, bool with_events) {
   k.rec = p->d_rec; k.Dn = p->d_Dn; k.demands = p->demands; k.costs = p->costs;
   k.counter = p->d_counter; k.fb_list = p->d_fb_list; k.fb_count = p->d_fb_count;
   k.status = status;
-  if (with_events) cudaEventRecord(p->ev0, st);
+  // External records become event-record nodes of the captured graph (a plain
+  // record inside a capture only orders streams and never fires).
+  if (with_events) cudaEventRecordWithFlags(p->ev0, st, cudaEventRecordExternal);
   int e = launch_split_batch(k, p->warps, p->ring, p->grid, st, nullptr);
-  if (with_events) cudaEventRecord(p->ev1, st);
+  if (with_events) cudaEventRecordWithFlags(p->ev1, st, cudaEventRecordExternal);
   if (e) return pcuda((cudaError_t)e, "batch kernel");
   BatchFallbackArgs f{};
   f.Q = p->Q; f.S = p->S; f.n = p->d_n; f.dem_off = p->d_dem_off; f.rec_off = p->d_rec_off;

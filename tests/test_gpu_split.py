@@ -65,7 +65,7 @@ def _random_case(seed, n, S, Q, qlo, qhi, dist_mode=False):
     return tour, xy, dist, q
 
 
-@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("algo,warps", [("plain", 0), ("deque", 0), ("deque", 4)])
 @pytest.mark.parametrize("case", [
     # (seed, n, S, Q, qlo, qhi, dist)
     (1, 1, 33, 10, 1, 10, False),       # n = 1
@@ -75,13 +75,16 @@ def _random_case(seed, n, S, Q, qlo, qhi, dist_mode=False):
     (5, 64, 97, 255, 1, 60, False),     # uint16 staging (Q >= 255)
     (6, 129, 64, 300, 0, 3, False),     # long windows: > 255 customers per route
     (7, 250, 131, 30000, 1, 500, False),  # uint16, large Q, long routes
+    (8, 600, 70, 200, 1, 30, False),      # row too long for tensor memory
 ])
-def test_split_edge_cases(algo, case):
+def test_split_edge_cases(algo, warps, case):
+    """warps=0: default launch (tensor-memory staging when rows fit 512 B);
+    warps=4: shared-memory staging."""
     seed, n, S, Q, qlo, qhi, dm = case
     tour, xy, dist, q = _random_case(seed, n, S, Q, qlo, qhi, dm)
     kw = {"dist": dist} if dm else {"coords": xy}
     orc = oracle.split(tour, Q, q, want_margin=True, **kw)
-    r = sdp().split_eval(_cuda(tour), Q, _cuda(q), preds="i32", algo=algo,
+    r = sdp().split_eval(_cuda(tour), Q, _cuda(q), preds="i32", algo=algo, warps=warps,
                          **{k: _cuda(v) for k, v in kw.items()})
     torch.cuda.synchronize()
     check_split(r["cost"], r["pred"], orc, min_checked=0.0)
@@ -153,9 +156,11 @@ def test_split_c2_full_size_sampled():
     t, c = _cuda(tour), _cuda(xy)
     r = sdp().split_eval(t, spec.Q, qd, coords=c, preds="u16", algo="deque")
     ref = sdp().split_eval(t, spec.Q, qd, coords=c, preds="u16", algo="plain")
+    sm = sdp().split_eval(t, spec.Q, qd, coords=c, preds="u16", algo="deque", warps=4)
     torch.cuda.synchronize()
     assert torch.equal(r["cost"], ref["cost"])
     assert torch.equal(r["pred"], ref["pred"])
+    assert torch.equal(sm["cost"], ref["cost"]) and torch.equal(sm["pred"], ref["pred"])
     rng = np.random.default_rng(0)
     rows = np.sort(rng.choice(spec.S, 1500, replace=False))
     rows = np.concatenate([rows, [0, 31, 32, spec.S - 1]])
