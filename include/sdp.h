@@ -139,6 +139,30 @@ size_t sdp_split_args_size(void);
 size_t sdp_split_workspace_bytes(const sdp_split_args* a);
 int sdp_split_eval(const sdp_split_args* a, void* stream);
 
+/* Split evaluation that allocates nothing, for callers that cannot hand the
+ * library device memory beyond their inputs and outputs: host programs that
+ * own every device allocation and pass a solver only the buffers it reads and
+ * writes (plugins, embedded solvers), or latency-critical loops where a
+ * cudaMalloc / cudaFree would synchronize the device.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Same arguments, results and errors as sdp_split_eval, except that
+ * a->workspace / a->workspace_bytes are ignored: the scratch is a fixed
+ * device array of SDP_NOALLOC_SCRATCH_BYTES inside the library, which every
+ * device that loads the library holds until the process exits.
+ *   - Calls whose workspace (sdp_split_workspace_bytes) exceeds that size are
+ *     rejected with SDP_ERR_UNSUPPORTED and nothing is launched (at n = 500,
+ *     algo DEQUE, about 2 million scenarios fit; algo PLAIN needs more).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     each call resets what must start at zero (the fallback counter).  Calls
+ *     that overlap on the GPU (other streams, other host threads) race on it:
+ *     serialise them. */
+#define SDP_NOALLOC_SCRATCH_BYTES (16u << 20)
+int sdp_split_eval_noalloc(const sdp_split_args* a, void* stream);
+
 /* Number of capacity-feasible arcs (p,i), p < i, load(s_{p+1..i}) <= Q, per
  * scenario -- the relaxations of Eq. eqdpA, the throughput unit.
  * arcs_out [S] int64 or NULL; total_out [1] uint64 (device) or NULL. */

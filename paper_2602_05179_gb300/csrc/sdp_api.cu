@@ -331,6 +331,56 @@ int sdp_split_eval(const sdp_split_args* a, void* stream) {
   return SDP_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------ no-allocation
+// Fixed device scratch for sdp_split_eval_noalloc.  Every device that loads
+// this library holds these SDP_NOALLOC_SCRATCH_BYTES until the process exits.
+// In host code the symbol is only a host-side handle: kernels receive the
+// device address obtained below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SDP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+void* g_noalloc_ptr[kMaxDev] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (with that device current) and cached.
+int noalloc_scratch(void** out) {
+  int dev;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SDP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int sdp_split_eval_noalloc(const sdp_split_args* a, void* stream) {
+  if (!a) return fail(SDP_ERR_INVALID_ARG, "args is NULL");
+  if (a->n < 0 || a->S < 0) return fail(SDP_ERR_INVALID_ARG, "n and S must be >= 0");
+  const size_t need = sdp_split_workspace_bytes(a);
+  if (need > (size_t)SDP_NOALLOC_SCRATCH_BYTES)
+    return fail(SDP_ERR_UNSUPPORTED,
+                "this call needs %zu bytes of scratch; the no-allocation scratch holds %zu "
+                "(use sdp_split_eval with a caller workspace)",
+                need, (size_t)SDP_NOALLOC_SCRATCH_BYTES);
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  sdp_split_args b = *a;
+  b.workspace = scratch;
+  b.workspace_bytes = SDP_NOALLOC_SCRATCH_BYTES;
+  return sdp_split_eval(&b, stream);
+}
+
 int sdp_split_count_arcs(const sdp_split_args* a, int64_t* arcs_out, uint64_t* total_out,
                          void* stream) {
   int rc = check_split(a, false);
