@@ -195,6 +195,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--only", default="", choices=["", "reinsert", "batch", "adjoint"],
+                    help="run one operator line alone (profiling)")
+    ap.add_argument("--preds", default="u16", choices=["u16", "i32", "none"])
     ap.add_argument("--no-operators", action="store_true",
                     help="skip the reinsertion / batched / adjoint operator lines")
     ap.add_argument("--scenarios", type=int, default=0,
@@ -216,6 +219,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only:
+        print(json.dumps(operators(api, wl, dev, only=args.only, steps=args.steps)))
+        return 0
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
@@ -234,8 +240,10 @@ def main():
     torch.cuda.synchronize()
     arcs_rank = int(total)
 
+    preds = None if args.preds == "none" else args.preds
+
     def step(algo=args.algo):
-        return api.split_eval(t_d, spec.Q, q_d, coords=c_d, preds="u16", algo=algo)
+        return api.split_eval(t_d, spec.Q, q_d, coords=c_d, preds=preds, algo=algo)
 
     # ---- device-resident timed region
     for _ in range(args.warmup):
@@ -320,16 +328,17 @@ def e2e_run(args, api, spec, t_d, c_d, q_d, arcs_all, world, dist, dev):
     q_host.copy_(q_d)
     q_e2e = torch.empty_like(q_d)
     h2d = q_host.numel() * 4
+    preds = None if args.preds == "none" else args.preds
     for _ in range(3):
         q_e2e.copy_(q_host, non_blocking=True)
-        api.split_eval(t_d, spec.Q, q_e2e, coords=c_d, preds="u16", algo=args.algo)["mean"].item()
+        api.split_eval(t_d, spec.Q, q_e2e, coords=c_d, preds=preds, algo=args.algo)["mean"].item()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     w0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         q_e2e.copy_(q_host, non_blocking=True)
-        m = api.split_eval(t_d, spec.Q, q_e2e, coords=c_d, preds="u16", algo=args.algo)["mean"]
+        m = api.split_eval(t_d, spec.Q, q_e2e, coords=c_d, preds=preds, algo=args.algo)["mean"]
         m.item()
     w1 = time.perf_counter()
     et = torch.tensor([w1 - w0], dtype=torch.float64, device=dev)
@@ -364,7 +373,7 @@ def _timed(fn, steps, warmup=3, events=True):
     return a.elapsed_time(b) / steps, kern
 
 
-def operators(api, wl, dev):
+def operators(api, wl, dev, only="", steps=0):
     """The other hot-path operators at their workload sizes (few steps each)."""
     import torch
     peaks, src = measured_peaks()
@@ -372,12 +381,14 @@ def operators(api, wl, dev):
     p_alu = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
     hbm = peaks["hbm_gbs"]
     out = {}
+    if only and only != "reinsert":
+        return _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm)
     # ---- reinsertion T=60, U=200, S=10^6 (ALU bound)
     rs = wl.REINSERT_C3
     cons = wl.reinsert_consumption_device(rs, dev)
     fixed = torch.from_numpy(wl.reinsert_fixed(rs)).to(dev)
     fn = lambda: api.reinsert_eval(rs.T, rs.U, rs.I0, rs.h, rs.p, rs.unit_cost, fixed, cons)
-    ms, kms = _timed(fn, 10)
+    ms, kms = _timed(fn, steps or 10)
     rel = 2.0 * (rs.U + 1) * rs.T * rs.S
     out[rs.name] = {"value": rel / (ms / 1e3), "unit": "relaxations/s",
                     "scenarios_per_s": rs.S / (ms / 1e3), "ms_per_step": ms, "kernel_ms": kms,
@@ -386,6 +397,15 @@ def operators(api, wl, dev):
                                  "frac": 2 * rel / (kms / 1e3) / p_alu,
                                  "peak_source": f"{sms} SMs x 128 lanes x sm_max_mhz ({src})"}}
     del cons
+    if only:
+        return out
+    return _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm)
+
+
+def _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm):
+    import torch
+    if only and only != "adjoint":
+        return _operator_batch(api, wl, dev, steps, out, p_alu, hbm)
     # ---- adjoint n=300, S=10^5 (fused forward + on-chip backtrack)
     ad = wl.ADJOINT_C5
     tour, xy, distm = wl.split_tour(ad)
@@ -396,7 +416,7 @@ def operators(api, wl, dev):
     arcs = int(tot)
     g = torch.ones((), dtype=torch.float32, device=dev)
     fn = lambda: api.split_backward(t, ad.Q, q, dm, g)
-    ms, kms = _timed(fn, 20)
+    ms, kms = _timed(fn, steps or 20)
     byts = ad.S * ad.n * 4
     out[ad.name] = {"value": arcs / (ms / 1e3), "unit": "arcs/s (forward+backtrack)",
                     "ms_per_step": ms, "kernel_ms": kms,
@@ -408,6 +428,14 @@ def operators(api, wl, dev):
     pms, _ = _timed(fn2, 5, events=False)
     out[ad.name]["plain_forward_ms"] = pms
     del q
+    if only:
+        return out
+    return _operator_batch(api, wl, dev, steps, out, p_alu, hbm)
+
+
+def _operator_batch(api, wl, dev, steps, out, p_alu, hbm):
+    import tempfile
+    import torch
     # ---- batched: 4096 tours, n ~ U{20..1000}, S=4096 (persistent + graph)
     bs = wl.BATCH_C4
     nb = wl.batch_sizes(bs)
@@ -423,9 +451,8 @@ def operators(api, wl, dev):
     cc = torch.from_numpy(np.concatenate(coords)).to(dev)
     plan = api.SplitPlan(nb, tt, cc, d, bs.Q, bs.S, dem_off=dem_off)
     arcs = plan.count_arcs()
-    import tempfile
     tune = plan.autotune(os.path.join(tempfile.gettempdir(), "sdp_autotune_cache.txt"))
-    ms, _ = _timed(plan.run, 10, events=False)
+    ms, _ = _timed(plan.run, steps or 10, events=False)
     kms = plan.kernel_ms()
     byts = total * 4 + bs.B * bs.S * 4
     out[bs.name] = {"value": arcs / (ms / 1e3), "unit": UNIT,
@@ -446,7 +473,8 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
     dev = torch.device("cuda", torch.cuda.current_device())
     peaks, peak_src = measured_peaks()
     n = spec.n
-    alg_bytes = S * n * 4 + S * 4 + S * n * 2  # demands in, fp32 cost + uint16 preds out
+    pbytes = {"u16": 2, "i32": 4, "none": 0}[args.preds]
+    alg_bytes = S * n * 4 + S * 4 + S * n * pbytes  # demands in, fp32 cost + preds out
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     traffic = None
     tp = os.path.join(ROOT, "profiles", "split_deque_traffic.json")
@@ -457,7 +485,8 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
             traffic = tj.get("dram_bytes_per_launch")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": "split_deque_kernel", "kernel_ms": kern_ms,
+            "kernel": "split_tmem_kernel" if args.algo == "deque" else "split_plain_kernel",
+            "kernel_ms": kern_ms,
             "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_src} hbm_gbs (copy)"}
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     p_alu = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
@@ -469,7 +498,8 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
         "config": {"workload": WORKLOAD if S == 1_000_000 else f"split_n500_Q200_S{S}_U1-30",
                    "n": n, "Q": spec.Q, "S_per_gpu": S,
                    "demand": "iid U{1..30} int32, seed 1", "coords": "U[0,100)^2 fp32",
-                   "algo": args.algo, "preds": "u16", "parallelism": f"scenario-sharded x{world}",
+                   "algo": args.algo, "preds": args.preds,
+                   "parallelism": f"scenario-sharded x{world}",
                    "l2": "inputs larger than L2 (2.0 GB demands per step), no flush",
                    "arcs_per_step": arcs_all},
         "scenarios_per_s": scen_s,

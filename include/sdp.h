@@ -247,7 +247,10 @@ void sdp_plan_destroy(sdp_plan* p);
  * Backward DP C_T = 0, C_t(I) = min(no delivery, delivery), ties to no
  * delivery; value = C_0(I0); policy = decisions along the optimal path. */
 typedef struct sdp_reinsert_args {
-  int32_t T;                  /* 1 <= T <= 4096 */
+  int32_t T;                  /* 1 <= T; T * W <= 4096 where W = 8 for
+                                 U < 256, 16 for U < 512, 32 for U < 1024
+                                 (decision bits stay on chip), else
+                                 SDP_ERR_UNSUPPORTED */
   int32_t U;                  /* 0 <= U <= 1023 */
   int32_t I0;                 /* 0 <= I0 <= U */
   int32_t algo;               /* 0 = default */

@@ -22,30 +22,45 @@ namespace sdp {
 
 constexpr int kPad = 32;
 
-template <int KC, bool TABLE>
+// Decision words of one stage: KC ballots, padded to 8 words so that lane 0
+// stores them with two 16-byte shared stores.
+__host__ __device__ constexpr int bits_stride(int kc) { return (kc + 7) & ~7; }
+
+template <int KC, bool TABLE, bool UNIT>
 __global__ void __launch_bounds__(512) reinsert_kernel(ReinsertArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int T = a.T, U = a.U;
-  const int GW = kPad + 32 * KC;
-  const size_t per_warp = ((size_t)2 * GW + (size_t)T * KC + (size_t)T) * 4;
-  unsigned char* wb = smem + per_warp * warp;
+  constexpr int GW = kPad + 32 * KC;
+  constexpr int BS = bits_stride(KC);
+  // CTA-shared per-day routing cost, then per warp: G double buffer,
+  // decision words, consumption of the current scenario
+  float* fixed_sm = reinterpret_cast<float*>(smem);
+  const size_t fixed_bytes = ((size_t)T * 4 + 15) & ~(size_t)15;
+  // 16-byte multiple: lane 0 stores decision words with 16-byte stores
+  const size_t per_warp = (((size_t)2 * GW + (size_t)T * BS + (size_t)T) * 4 + 15) & ~(size_t)15;
+  unsigned char* wb = smem + fixed_bytes + per_warp * warp;
   float* G0 = reinterpret_cast<float*>(wb);
   float* G1 = G0 + GW;
   uint32_t* bits = reinterpret_cast<uint32_t*>(G1 + GW);
-  int32_t* dsm = reinterpret_cast<int32_t*>(bits + (size_t)T * KC);
+  int32_t* dsm = reinterpret_cast<int32_t*>(bits + (size_t)T * BS);
+  for (int t = threadIdx.x; t < T; t += blockDim.x) fixed_sm[t] = __ldg(a.fixed + t);
+  __syncthreads();
 
   const float h = a.h, p = a.p, c = a.c;
-  // per-slot constants: e(I) for I >= 0, the delivery's unit part c (U - I)
+  // per-slot constants: e(I) for I >= 0; the delivery's extra cost over the
+  // stage base, c (U - I) for I < U and +inf at I >= U (q = 0 there)
   float eI[KC], cq[KC];
 #pragma unroll
   for (int k = 0; k < KC; ++k) {
     const int I = lane + 32 * k;
     const int Ic = min(I, U);
     eI[k] = TABLE ? __ldg(a.table + Ic) : __fmul_rn(h, (float)Ic);
-    cq[k] = I < U ? __fmul_rn(c, (float)(U - I)) : CUDART_INF_F;
+    cq[k] = I < U ? (UNIT ? __fmul_rn(c, (float)(U - I)) : 0.f) : CUDART_INF_F;
   }
   const float e0 = TABLE ? __ldg(a.table) : 0.f;
+  // e(j) for the negative region j = lane - P of the G buffer, without C
+  const float eneg = TABLE ? e0 : __fmul_rn(p, (float)(kPad - lane));
   bool neg = false;
 
   for (int64_t s = (int64_t)blockIdx.x * nw + warp; s < a.S; s += (int64_t)gridDim.x * nw) {
@@ -59,7 +74,7 @@ __global__ void __launch_bounds__(512) reinsert_kernel(ReinsertArgs a) {
     float* Gc = G1;
 #pragma unroll
     for (int k = 0; k < KC; ++k) Gn[kPad + lane + 32 * k] = eI[k];
-    Gn[lane] = TABLE ? e0 : __fmul_rn(p, (float)(kPad - lane));  // j = lane - P < 0
+    Gn[lane] = eneg;
     __syncwarp();
     float C[KC];
 #pragma unroll
@@ -67,41 +82,62 @@ __global__ void __launch_bounds__(512) reinsert_kernel(ReinsertArgs a) {
 
     for (int t = T - 1; t >= 0; --t) {
       const int d = dsm[t];
-      const float C0n = Gn[kPad] - (TABLE ? e0 : 0.f);  // C_{t+1}(0) = G_{t+1}(0) - e(0)
+      const float C0n = Gn[kPad] - e0;  // C_{t+1}(0); exact (e0 = 0 in linear mode)
       // G_{t+1}(j) for any j <= U
       auto gat = [&](int j) -> float {
         if (j >= -kPad) return Gn[j + kPad];
         return TABLE ? Gn[kPad] : __fadd_rn(C0n, __fmul_rn(p, (float)(-j)));
       };
-      const float base = __fadd_rn(__ldg(a.fixed + t), gat(U - d));
-      if (d <= kPad) {
+      const float ft = fixed_sm[t];
+      const float base = __fadd_rn(ft, gat(U - d));
+      uint32_t w[KC];
+      if (!UNIT && d <= kPad && ft >= 0.f) {
+        // no unit cost and f_t >= 0: the delivery cost is `base` for every I,
+        // and at I = U (where delivering means q = 0) base = f_t + nd >= nd,
+        // so the comparison alone already keeps "no delivery" there
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-          const int I = lane + 32 * k;
-          const float nd = Gn[I - d + kPad];
+          const float nd = Gn[lane + 32 * k - d + kPad];
+          const bool dec = base < nd;
+          C[k] = dec ? base : nd;
+          w[k] = __ballot_sync(0xffffffffu, dec);
+        }
+      } else if (d <= kPad) {
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+          const float nd = Gn[lane + 32 * k - d + kPad];
           const float dv = __fadd_rn(base, cq[k]);
           const bool dec = dv < nd;
           C[k] = dec ? dv : nd;
-          const uint32_t w = __ballot_sync(0xffffffffu, dec && I <= U);
-          if (lane == 0) bits[t * KC + k] = w;
+          w[k] = __ballot_sync(0xffffffffu, dec);
         }
       } else {
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-          const int I = lane + 32 * k;
-          const float nd = gat(I - d);
+          const float nd = gat(lane + 32 * k - d);
           const float dv = __fadd_rn(base, cq[k]);
           const bool dec = dv < nd;
           C[k] = dec ? dv : nd;
-          const uint32_t w = __ballot_sync(0xffffffffu, dec && I <= U);
-          if (lane == 0) bits[t * KC + k] = w;
+          w[k] = __ballot_sync(0xffffffffu, dec);
+        }
+      }
+      if (lane == 0) {
+        uint32_t* row = bits + t * BS;
+#pragma unroll
+        for (int k0 = 0; k0 < BS; k0 += 4) {
+          uint4 v;
+          v.x = k0 + 0 < KC ? w[k0 + 0] : 0u;
+          v.y = k0 + 1 < KC ? w[k0 + 1] : 0u;
+          v.z = k0 + 2 < KC ? w[k0 + 2] : 0u;
+          v.w = k0 + 3 < KC ? w[k0 + 3] : 0u;
+          *reinterpret_cast<uint4*>(row + k0) = v;
         }
       }
       // G_t for the next (earlier) stage
       const float C0 = __shfl_sync(0xffffffffu, C[0], 0);
 #pragma unroll
       for (int k = 0; k < KC; ++k) Gc[kPad + lane + 32 * k] = __fadd_rn(eI[k], C[k]);
-      Gc[lane] = TABLE ? __fadd_rn(e0, C0) : __fadd_rn(C0, __fmul_rn(p, (float)(kPad - lane)));
+      Gc[lane] = TABLE ? __fadd_rn(e0, C0) : __fadd_rn(C0, eneg);
       __syncwarp();
       float* tmp = Gn; Gn = Gc; Gc = tmp;
     }
@@ -120,15 +156,15 @@ __global__ void __launch_bounds__(512) reinsert_kernel(ReinsertArgs a) {
         if (I <= U) a.value0[s * (U + 1) + I] = C[k];
       }
     }
-    // backtrack (every lane walks the same path; lane t%32 writes day t)
+    // backtrack (every lane walks the same path; lane t%32 writes day t):
+    // deliver -> max(0, U - d_t), else max(0, I - d_t)
     if (a.policy) {
       int I = a.I0;
       for (int t = 0; t < T; ++t) {
-        const uint32_t w = bits[t * KC + (I >> 5)];
-        const int dec = (w >> (I & 31)) & 1;
+        const uint32_t wd = bits[t * BS + (I >> 5)];
+        const int dec = (wd >> (I & 31)) & 1;
         if ((t & 31) == lane) a.policy[s * T + t] = (uint8_t)dec;
-        const int x = I + (dec ? U - I : 0) - dsm[t];
-        I = max(x, 0);
+        I = max((dec ? U : I) - dsm[t], 0);
       }
     }
     __syncwarp();
@@ -137,14 +173,16 @@ __global__ void __launch_bounds__(512) reinsert_kernel(ReinsertArgs a) {
 }
 
 namespace {
-template <int KC, bool TABLE>
+template <int KC, bool TABLE, bool UNIT>
 int launch_kc(const ReinsertArgs& a, cudaStream_t st) {
-  auto k = reinsert_kernel<KC, TABLE>;
-  const int GW = kPad + 32 * KC;
-  const size_t per_warp = ((size_t)2 * GW + (size_t)a.T * KC + (size_t)a.T) * 4;
+  auto k = reinsert_kernel<KC, TABLE, UNIT>;
+  constexpr int GW = kPad + 32 * KC;
+  const size_t per_warp =
+      (((size_t)2 * GW + (size_t)a.T * bits_stride(KC) + (size_t)a.T) * 4 + 15) & ~(size_t)15;
+  const size_t fixed_bytes = ((size_t)a.T * 4 + 15) & ~(size_t)15;
   int warps = 16;
-  while (warps > 1 && per_warp * warps > 100 * 1024) warps >>= 1;
-  const size_t smem = per_warp * warps;
+  while (warps > 1 && fixed_bytes + per_warp * warps > 100 * 1024) warps >>= 1;
+  const size_t smem = fixed_bytes + per_warp * warps;
   if (smem > 200 * 1024) return (int)cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -159,28 +197,30 @@ int launch_kc(const ReinsertArgs& a, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
-template <bool TABLE>
+template <bool TABLE, bool UNIT>
 int by_kc(const ReinsertArgs& a, cudaStream_t st) {
   const int kc = (a.U + 1 + 31) / 32;
   switch (kc) {
-    case 1: return launch_kc<1, TABLE>(a, st);
-    case 2: return launch_kc<2, TABLE>(a, st);
-    case 3: return launch_kc<3, TABLE>(a, st);
-    case 4: return launch_kc<4, TABLE>(a, st);
-    case 5: return launch_kc<5, TABLE>(a, st);
-    case 6: return launch_kc<6, TABLE>(a, st);
-    case 7: return launch_kc<7, TABLE>(a, st);
-    case 8: return launch_kc<8, TABLE>(a, st);
+    case 1: return launch_kc<1, TABLE, UNIT>(a, st);
+    case 2: return launch_kc<2, TABLE, UNIT>(a, st);
+    case 3: return launch_kc<3, TABLE, UNIT>(a, st);
+    case 4: return launch_kc<4, TABLE, UNIT>(a, st);
+    case 5: return launch_kc<5, TABLE, UNIT>(a, st);
+    case 6: return launch_kc<6, TABLE, UNIT>(a, st);
+    case 7: return launch_kc<7, TABLE, UNIT>(a, st);
+    case 8: return launch_kc<8, TABLE, UNIT>(a, st);
     default:
-      if (kc <= 16) return launch_kc<16, TABLE>(a, st);
-      return launch_kc<32, TABLE>(a, st);
+      if (kc <= 16) return launch_kc<16, TABLE, UNIT>(a, st);
+      return launch_kc<32, TABLE, UNIT>(a, st);
   }
 }
 }  // namespace
 
 int launch_reinsert(const ReinsertArgs& a, cudaStream_t st) {
   if (a.S <= 0) return 0;
-  return a.table ? by_kc<true>(a, st) : by_kc<false>(a, st);
+  const bool unit = a.c != 0.f;
+  if (a.table) return unit ? by_kc<true, true>(a, st) : by_kc<true, false>(a, st);
+  return unit ? by_kc<false, true>(a, st) : by_kc<false, false>(a, st);
 }
 
 }  // namespace sdp

@@ -206,7 +206,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     int e = deque_max_ctas_per_sm(cfg, hist != nullptr, a->pred_dtype, pred != nullptr, &occ);
     if (e) return cuda_fail((cudaError_t)e, "deque occupancy");
     if (occ < 1) return fail(SDP_ERR_UNSUPPORTED, "DEQUE configuration does not fit on an SM");
-    const int64_t tiles = (a->S + 31) / 32;
+    const int64_t tiles = (a->S + 32 * cfg.ns - 1) / (32 * cfg.ns);
     const int64_t ctas_needed = (tiles + warps - 1) / warps;
     const int grid = (int)(ctas_needed < (int64_t)occ * sms ? ctas_needed : (int64_t)occ * sms);
     SplitDequeArgs d{};
@@ -465,9 +465,11 @@ int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
   if (a->I0 < 0 || a->I0 > a->U) return fail(SDP_ERR_INVALID_ARG, "I0 = %d outside 0..U", a->I0);
   if (a->S < 0) return fail(SDP_ERR_INVALID_ARG, "S < 0");
   const int kc = a->U + 1 <= 256 ? (a->U + 1 + 31) / 32 : (a->U + 1 <= 512 ? 16 : 32);
-  if ((int64_t)a->T * kc > 2048)
-    return fail(SDP_ERR_UNSUPPORTED, "T * ceil((U+1)/32) = %lld above 2048 (decision bits kept on chip)",
-                (long long)a->T * kc);
+  const int64_t words = (int64_t)a->T * ((kc + 7) & ~7);
+  if (words > 4096)
+    return fail(SDP_ERR_UNSUPPORTED,
+                "T = %d with U = %d needs %lld decision words per scenario, above 4096 "
+                "(decision bits are kept on chip)", a->T, a->U, (long long)words);
   if (a->S > 0) {
     if (!is_device_ptr(a->fixed)) return fail(SDP_ERR_INVALID_ARG, "fixed must be a device pointer");
     if (!is_device_ptr(a->consumption)) return fail(SDP_ERR_INVALID_ARG, "consumption must be a device pointer");

@@ -85,7 +85,8 @@ struct DequeConfig {
   int qbytes;       // 1 (uint8 staging) or 2 (uint16 staging)
   int row_stride;   // bytes per staged demand row (shared-memory staging)
   bool rec_in_smem; // tour records copied to shared memory (n <= 4096)
-  bool tmem;        // demand rows staged in tensor memory (16 warps, 1 CTA/SM)
+  bool tmem;        // demand rows staged in tensor memory (one CTA per SM)
+  int ns;           // scenarios per lane (tile = ns * 32 scenarios)
   size_t smem;      // dynamic shared memory per CTA
 };
 bool deque_supported(int n, int Q);
@@ -116,7 +117,9 @@ struct BatchKernelArgs {
   uint32_t* fb_count;
   uint32_t* status;
 };
+// warps == 0: tensor-memory staging (warps per CTA chosen from n_max)
 size_t batch_smem(int n_max, int Q, int warps, int ring);
+int batch_tmem_warps(int n_max, int Q);
 struct BatchPrepArgs {
   const int32_t* n;
   const int64_t* tour_off;

@@ -101,7 +101,8 @@ int configure(sdp_plan* p, int warps, int ring) {
   if (e) return pcuda((cudaError_t)e, "batch occupancy");
   if (occ < 1) return SDP_ERR_UNSUPPORTED;
   const int64_t items = (int64_t)p->B * ((p->S + 31) / 32);
-  const int64_t want = (items + warps - 1) / warps;
+  const int eff = warps > 0 ? warps : batch_tmem_warps(p->n_max, p->Q);
+  const int64_t want = (items + eff - 1) / eff;
   p->warps = warps;
   p->ring = ring;
   p->grid = (int)std::min<int64_t>(want, (int64_t)occ * num_sms());
@@ -231,7 +232,8 @@ int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out) {
     return e == cudaErrorMemoryAllocation ? pfail(SDP_ERR_OOM, "plan allocation failed")
                                           : pcuda(e, "plan create");
   }
-  int rc = configure(p, 4, 16);
+  int rc = configure(p, 0, 16);  // TMEM staging when the tours fit
+  if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 4, 16);
   if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 1, 8);
   if (rc) {
     sdp_plan_destroy(p);
@@ -303,7 +305,7 @@ int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
           fclose(f);
           drop_graph(p);
           int rc = configure(p, w, r);
-          return rc ? configure(p, 4, 16) : SDP_OK;
+          return rc ? configure(p, 1, 8) : SDP_OK;
         }
       }
       fclose(f);
@@ -312,7 +314,7 @@ int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
   uint32_t* status;
   int rc = status_word(&status);
   if (rc) return rc;
-  const int warps_c[] = {1, 2, 4, 8};
+  const int warps_c[] = {0, 1, 2, 4, 8};  // 0 = TMEM staging
   const int ring_c[] = {8, 16};
   float best = 1e30f;
   int bw = p->warps, br = p->ring;

@@ -31,8 +31,10 @@
 //   one tcgen05.ld.32x32b per step (issued a step ahead) delivers all 32
 //   demands.  Shared memory then holds only the deque rings, so 16 warps fit
 //   per SM instead of 8.
-// While a tile is processed, the warp's next tile is prefetched into L2 with
-// one bulk prefetch (cp.async.bulk.prefetch.L2).
+// (A bulk L2 prefetch of the next tile was measured: it raised DRAM reads from
+// 2.2 to 3.8 GB per launch at n = 500, S = 10^6 -- prefetched lines were
+// evicted before use -- for 3% less time, so tiles are read on demand, with
+// 16 loads in flight per lane in the tensor-memory ingest.)
 //
 // Outputs.  Predecessors are staged per 16 positions in a small shared buffer
 // and written as coalesced row segments.  The fused adjoint instead writes the
@@ -64,22 +66,6 @@ __device__ __forceinline__ int ld_s32(const int32_t* p) {
   int v;
   asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
-}
-
-// Bulk prefetch of [p, p+bytes) into L2 (executed by the TMA engine; p and
-// bytes must be multiples of 16).
-__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes)
-               : "memory");
-}
-
-// Warm L2 with `bytes` bytes at p (16-byte aligned interior only).
-__device__ __forceinline__ void prefetch_region(const void* p, int64_t bytes) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-  const uintptr_t pa = (a + 15) & ~(uintptr_t)15;
-  int64_t rem = ((bytes - (int64_t)(pa - a)) / 16) * 16;
-  for (int64_t o = 0; rem > 0; o += 1 << 20, rem -= 1 << 20)
-    prefetch_l2_bulk(reinterpret_cast<const void*>(pa + o), (uint32_t)imin64(rem, 1 << 20));
 }
 
 // Generic 16-byte record load (shared memory when the records fit, else
@@ -217,7 +203,9 @@ __host__ __device__ __forceinline__ int tmem_row_words(int n, int qbytes) {
 
 namespace {
 
-constexpr int kStagePitch = 33;  // predecessor stage: [16 positions][33] elements
+constexpr int kBatch = 16;       // positions per predecessor output batch (16 or 32)
+// Dynamic shared memory that keeps a TMEM-owning kernel at one CTA per SM.
+constexpr size_t kOneCtaPerSmSmem = 120 * 1024;
 
 // Coalesced 16-byte loads of `rows` contiguous demand rows of n int32 each,
 // clamped to [0, Q+1] and stored as narrow shared-memory rows.
@@ -304,7 +292,7 @@ __device__ __forceinline__ TileFlags ingest_tile_tmem(const int32_t* src, int ro
   bool zero = false, neg = false, inf = false;
   const bool vec = ((n & 3) == 0) && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
   if (vec) {
-    constexpr int WPI = 8;  // words per iteration
+    constexpr int WPI = 16;  // words per iteration (16 x 16-byte loads in flight for uint8)
     constexpr int LOADS = WPI * PER / 4;
     for (int w0 = 0; w0 < words; w0 += WPI) {
       int4 x[LOADS];
@@ -317,8 +305,9 @@ __device__ __forceinline__ TileFlags ingest_tile_tmem(const int32_t* src, int ro
       uint32_t pk[WPI];
 #pragma unroll
       for (int k = 0; k < WPI; ++k) pk[k] = pack_q<QT>(xv + k * PER, Q, zero, neg, inf);
-      tmem_st4(taddr + w0, pk[0], pk[1], pk[2], pk[3]);
-      if (w0 + 4 < words) tmem_st4(taddr + w0 + 4, pk[4], pk[5], pk[6], pk[7]);
+#pragma unroll
+      for (int k = 0; k < WPI; k += 4)
+        if (w0 + k < words) tmem_st4(taddr + w0 + k, pk[k], pk[k + 1], pk[k + 2], pk[k + 3]);
     }
   } else {
     for (int w0 = 0; w0 < words; w0 += 4) {
@@ -348,132 +337,182 @@ constexpr int kOutStream = 1;  // predecessors streamed out every 16 positions
 constexpr int kOutDelta = 2;   // i - pred(i) written in place over the consumed
                                // demand byte (on-chip backtrack of the adjoint)
 
-// Where the next tile's demand rows are warmed into L2: late in the current
-// tile's DP, so that the prefetched bytes are not evicted before use.
-struct NextTile {
-  const void* ptr;   // nullptr: nothing to prefetch
-  int64_t bytes;
-  int at;            // first 16-position batch at or after this position
+// Deque state of one scenario (see the file comment): ring[head .. tail) in
+// shared memory ([entry][lane] layout), the front and the back's psi in
+// registers.  Each DP step is split into phases so that several scenarios of a
+// lane can be interleaved and share the warp votes that route the rare extra
+// pops to a loop.
+template <int RING>
+struct DequeState {
+  float* rpsi;        // this scenario's ring of psi values (+lane applied)
+  uint32_t* rmeta;    // (16-bit prefix load << 16) | index
+  int head, tail, maxcnt, L, fL, fidx;
+  float K, bpsi, fpsi;
+
+  __device__ __forceinline__ void init(float* ring_psi, uint32_t* ring_meta, int lane) {
+    rpsi = ring_psi + lane;
+    rmeta = ring_meta + lane;
+    head = tail = maxcnt = L = fL = fidx = 0;
+    K = bpsi = fpsi = 0.f;
+  }
+  __device__ __forceinline__ float at_psi(int k) const { return rpsi[(k & (RING - 1)) * 32]; }
+  // first back pop (straight-line); true if this scenario needs more
+  __device__ __forceinline__ bool back1(float psi) {
+    const bool pb = tail > head && bpsi > psi;
+    if (pb) {
+      --tail;
+      bpsi = at_psi(tail - 1);
+    }
+    return pb && tail > head && bpsi > psi;
+  }
+  __device__ __forceinline__ void back_more(float psi) {
+    while (tail > head && bpsi > psi) {
+      --tail;
+      if (tail > head) bpsi = at_psi(tail - 1);
+    }
+  }
+  // push p = i-1 (an equal psi stays behind the older entry: smallest p wins)
+  __device__ __forceinline__ void push(float psi, int i) {
+    const int slot = (tail & (RING - 1)) * 32;
+    rpsi[slot] = psi;
+    rmeta[slot] = ((uint32_t)L << 16) | (uint32_t)(i - 1);
+    const bool alone = tail == head;
+    ++tail;
+    bpsi = psi;
+    if (alone) { fpsi = psi; fL = L; fidx = i - 1; }
+    maxcnt = max(maxcnt, tail - head);
+  }
+  __device__ __forceinline__ void pop_front() {
+    ++head;
+    const int h = (head & (RING - 1)) * 32;
+    fpsi = rpsi[h];
+    const uint32_t m = rmeta[h];
+    fidx = (int)(m & 0xFFFFu);
+    fL = L - (int)(((uint32_t)L - (m >> 16)) & 0xFFFFu);  // 16-bit prefix load, widened
+  }
+  // extend the window to customer s_i, first front pop; true if more needed
+  __device__ __forceinline__ bool front1(int q, int Q) {
+    L += q;
+    const bool pf = tail - head > 1 && L - fL > Q;
+    if (pf) pop_front();
+    return pf && tail - head > 1 && L - fL > Q;
+  }
+  __device__ __forceinline__ void front_more(int Q) {
+    while (tail - head > 1 && L - fL > Q) pop_front();
+  }
 };
 
-// The DP of one scenario per lane (see the file comment).  Every lane of the
-// warp runs it (lanes >= rows on stale data, outputs dropped) so that TMEM
-// loads and the 16-position output batches stay warp-collective.
+// The DP of NS scenarios per lane (see the file comment).  Every lane of the
+// warp runs it (lanes beyond the tile on stale data, outputs dropped) so that
+// TMEM loads and the 16-position output batches stay warp-collective.
+// Scenario s of the lane is tile row s * 32 + lane.
 // CHECK: the tile holds a scenario with a demand above Q; first_inf records
-// the first such position of this lane's scenario.
+// the first such position of each scenario.
 // REC_SHARED: rec points to shared memory (loaded as LDS.128).
-template <typename QT, typename PT, int RING, int OUT, bool CHECK, bool REC_SHARED,
+// OUT == kOutDelta (NS = 1, shared-memory row): i - pred(i) overwrites the
+// consumed demand byte of customer s_i.
+template <int NS, typename QT, typename PT, int RING, int OUT, bool CHECK, bool REC_SHARED,
           typename SRC>
-__device__ __forceinline__ float dp_row(SRC src, QT* row, int n, int Q, const StepRec* rec,
+__device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const StepRec* rec,
                                         float* ring_psi, uint32_t* ring_meta, int lane,
                                         PT* stage, PT* pred_tile, int rows, bool check_delta,
-                                        NextTile nxt, uint32_t& first_inf, bool& bad) {
-  int head = 0, tail = 0;  // deque = ring[head .. tail)
-  int L = 0;               // prefix load of the current position
-  float K = 0.f;
-  float bpsi = 0.f;        // psi of the back entry
-  float fpsi = 0.f;        // the front entry: psi, prefix load, index
-  int fL = 0, fidx = 0;
+                                        uint32_t* first_inf, bool* bad, float* K_out) {
+  constexpr int kPitch = NS * 32 + 1;  // predecessor stage pitch (elements)
+  DequeState<RING> st[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+    st[s].init(ring_psi + s * RING * 32, ring_meta + s * RING * 32, lane);
   const uint32_t rec_s = REC_SHARED ? (uint32_t)__cvta_generic_to_shared(rec) : 0u;
   auto load_rec = [&](int k) -> StepRec {
     if (REC_SHARED) return ld_rec_shared(rec_s + 16u * (uint32_t)k);
     return ld_rec_any(rec + k);
   };
   StepRec rn = load_rec(0);
-  src.prefetch(rn.col);
-  for (int i0 = 1; i0 <= n; i0 += 16) {
-    const int ie = min(n, i0 + 15);
-    if (nxt.ptr && lane == 0 && i0 <= nxt.at && nxt.at < i0 + 16)
-      prefetch_region(nxt.ptr, nxt.bytes);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) src[s].prefetch(rn.col);
+  for (int i0 = 1; i0 <= n; i0 += kBatch) {
+    const int ie = min(n, i0 + kBatch - 1);
+#pragma unroll 2
     for (int i = i0; i <= ie; ++i) {
       const StepRec r = rn;
-      const int q = src.take(r.col);
-      if (i < n) {
-        rn = load_rec(i);
-        src.prefetch(rn.col);
+      int q[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) q[s] = src[s].take(r.col);
+      // next position's record and demand (the last step re-reads position n)
+      rn = load_rec(min(i, n - 1));
+#pragma unroll
+      for (int s = 0; s < NS; ++s) src[s].prefetch(rn.col);
+      float psi[NS];
+      bool more = false;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        psi[s] = __fadd_rn(st[s].K, r.a);
+        more |= st[s].back1(psi[s]);
       }
-      // push p = i-1 after dropping every back entry with a larger psi (an
-      // equal psi stays: it is older, so the smallest p wins ties).  The
-      // first pop is straight-line code; more pops are rare and looped.
-      const float psi = __fadd_rn(K, r.a);
-      const bool pb = tail > head && bpsi > psi;
-      if (pb) {
-        --tail;
-        bpsi = ring_psi[((tail - 1) & (RING - 1)) * 32 + lane];
+      if (__any_sync(0xffffffffu, more)) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) st[s].back_more(psi[s]);
       }
-      if (__any_sync(0xffffffffu, pb && tail > head && bpsi > psi)) {
-        while (tail > head && bpsi > psi) {
-          --tail;
-          if (tail > head) bpsi = ring_psi[((tail - 1) & (RING - 1)) * 32 + lane];
+      more = false;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        st[s].push(psi[s], i);
+        if (CHECK && q[s] > Q && first_inf[s] > (uint32_t)n) first_inf[s] = (uint32_t)i;
+        more |= st[s].front1(q[s], Q);
+      }
+      if (__any_sync(0xffffffffu, more)) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) st[s].front_more(Q);
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        st[s].K = __fadd_rn(st[s].fpsi, r.ce);
+        if (OUT == kOutStream) {
+          int p = st[s].fidx;
+          if (CHECK && (uint32_t)i >= first_inf[s]) p = -1;
+          stage[(i - i0) * kPitch + s * 32 + lane] = (PT)p;
+        } else if (OUT == kOutDelta) {
+          const uint32_t delta = (uint32_t)(i - st[s].fidx);
+          if (check_delta && delta > (sizeof(QT) == 1 ? 255u : 65535u)) bad[s] = true;
+          row[r.col] = (QT)delta;
         }
-      }
-      const int slot = (tail & (RING - 1)) * 32 + lane;
-      ring_psi[slot] = psi;
-      ring_meta[slot] = ((uint32_t)L << 16) | (uint32_t)(i - 1);
-      const bool alone = tail == head;
-      ++tail;
-      bpsi = psi;
-      if (alone) { fpsi = psi; fL = L; fidx = i - 1; }
-      bad |= (tail - head) > RING;
-      // extend the window's right end to customer s_i
-      L += q;
-      if (CHECK && q > Q && first_inf > (uint32_t)n) first_inf = (uint32_t)i;
-      // drop predecessors whose route s_{p+1..i} exceeds Q (first pop
-      // straight-line, further pops looped)
-      const bool pf = tail - head > 1 && L - fL > Q;
-      if (pf) {
-        ++head;
-        const int h = (head & (RING - 1)) * 32 + lane;
-        fpsi = ring_psi[h];
-        const uint32_t m = ring_meta[h];
-        fidx = (int)(m & 0xFFFFu);
-        fL = L - (int)(((uint32_t)L - (m >> 16)) & 0xFFFFu);  // 16-bit prefix load, widened
-      }
-      if (__any_sync(0xffffffffu, pf && tail - head > 1 && L - fL > Q)) {
-        while (tail - head > 1 && L - fL > Q) {
-          ++head;
-          const int h = (head & (RING - 1)) * 32 + lane;
-          fpsi = ring_psi[h];
-          const uint32_t m = ring_meta[h];
-          fidx = (int)(m & 0xFFFFu);
-          fL = L - (int)(((uint32_t)L - (m >> 16)) & 0xFFFFu);
-        }
-      }
-      K = __fadd_rn(fpsi, r.ce);
-      if (OUT == kOutStream) {
-        int p = fidx;
-        if (CHECK && (uint32_t)i >= first_inf) p = -1;
-        stage[(i - i0) * kStagePitch + lane] = (PT)p;
-      } else if (OUT == kOutDelta) {
-        const uint32_t delta = (uint32_t)(i - fidx);
-        if (check_delta && delta > (sizeof(QT) == 1 ? 255u : 65535u)) bad = true;
-        row[r.col] = (QT)delta;
       }
     }
     if (OUT == kOutStream) {
       // rows x positions [i0, ie] of the staged batch -> coalesced row segments
       __syncwarp();
+      constexpr int kRowsPerPass = 32 / kBatch;
       const int cnt = ie - i0 + 1;
-      const int u = lane & 15;
-      PT* dst = pred_tile + (int64_t)(lane >> 4) * n + (i0 - 1) + u;
-      const PT* s = stage + u * kStagePitch + (lane >> 4);
-      const int64_t step2 = 2 * (int64_t)n;
+      const int u = lane % kBatch;
+      const int r0 = lane / kBatch;
+      PT* dst = pred_tile + (int64_t)r0 * n + (i0 - 1) + u;
+      const PT* sp = stage + u * kPitch + r0;
+      const int64_t stepr = kRowsPerPass * (int64_t)n;
       if (u < cnt) {
 #pragma unroll 4
-        for (int r2 = 0; r2 < rows - (lane >> 4); r2 += 2) {
-          *dst = s[r2];
-          dst += step2;
+        for (int r2 = 0; r2 < rows - r0; r2 += kRowsPerPass) {
+          *dst = sp[r2];
+          dst += stepr;
         }
       }
       __syncwarp();
     }
   }
-  return K;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    bad[s] |= st[s].maxcnt > RING;
+    K_out[s] = st[s].K;
+  }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ kernels
+template <typename PT, int NS>
+__host__ __device__ constexpr size_t stage_bytes_of() {
+  return (((size_t)kBatch * (NS * 32 + 1) * sizeof(PT)) + 15) & ~(size_t)15;
+}
+
 // Single tour, shared-memory staging (all output modes, incl. the adjoint).
 template <typename QT, typename PT, int RING, int OUT>
 __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
@@ -506,8 +545,7 @@ __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
     for (int k = threadIdx.x; k < n; k += blockDim.x) cols_sm[k] = a.cols[k];
     for (int k = threadIdx.x; k < 2 * n + 1; k += blockDim.x) hist_sm[k] = 0u;
   }
-  const size_t stage_bytes =
-      OUT == kOutStream ? (((size_t)16 * kStagePitch * sizeof(PT) + 15) & ~(size_t)15) : 0;
+  const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, 1>() : 0;
   const size_t per_warp = (size_t)32 * row_stride + (size_t)RING * 32 * 8 + stage_bytes;
   unsigned char* wbase = smem + off + per_warp * warp;
   QT* qb = reinterpret_cast<QT*>(wbase);
@@ -527,28 +565,23 @@ __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
     const int rows = (int)imin64(32, a.S - s0);
     const TileFlags tf = ingest_tile<QT>(a.demands + s0 * n, rows, n, rs_elems, Q, qb, lane);
     neg |= tf.neg;
-    NextTile nxt{nullptr, 0, 0};
-    if (tile + wstride < tiles) {
-      const int64_t ns0 = (tile + wstride) * 32;
-      nxt = NextTile{a.demands + ns0 * n, imin64(32, a.S - ns0) * n * 4, (3 * n) / 4};
-    }
     __syncwarp();
 
     uint32_t first_inf = (uint32_t)n + 1;
     bool bad = false;
+    float K;
     QT* row = qb + lane * rs_elems;
     PT* pred_tile = a.pred ? reinterpret_cast<PT*>(a.pred) + s0 * n : nullptr;
     const bool valid = lane < rows;
     SmemQ<QT> src{row, 0};
-    float K;
     if (tf.inf_rows)
-      K = dp_row<QT, PT, RING, OUT, true, false>(src, row, n, Q, rec, ring_psi, ring_meta, lane,
-                                                stage, pred_tile, pred_tile ? rows : 0, tf.zero,
-                                                nxt, first_inf, bad);
+      dp_rows<1, QT, PT, RING, OUT, true, false>(&src, row, n, Q, rec, ring_psi, ring_meta, lane,
+                                                 stage, pred_tile, pred_tile ? rows : 0, tf.zero,
+                                                 &first_inf, &bad, &K);
     else
-      K = dp_row<QT, PT, RING, OUT, false, false>(src, row, n, Q, rec, ring_psi, ring_meta,
-                                                 lane, stage, pred_tile, pred_tile ? rows : 0,
-                                                 tf.zero, nxt, first_inf, bad);
+      dp_rows<1, QT, PT, RING, OUT, false, false>(&src, row, n, Q, rec, ring_psi, ring_meta,
+                                                  lane, stage, pred_tile, pred_tile ? rows : 0,
+                                                  tf.zero, &first_inf, &bad, &K);
     bad = bad && valid;
     if (valid) {
       if (bad) {
@@ -586,10 +619,12 @@ __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
   }
 }
 
-// Single tour, TMEM staging (cost + streamed predecessors).  One CTA per SM
-// (the dynamic shared memory request guarantees it) allocates all 512 TMEM
-// columns; warp w uses its quadrant's lanes (w % 4) and column block w / 4.
-template <typename QT, typename PT, int RING, int OUT>
+// Single tour, TMEM staging (cost + streamed predecessors), NS scenarios per
+// lane (a tile is NS * 32 scenarios).  One CTA per SM (its dynamic shared
+// memory request guarantees it) allocates all 512 TMEM columns; warp w uses
+// lane quadrant w % 4 and column block w / 4 of cols_per_warp columns, row s of
+// the lane at column offset s * words.
+template <typename QT, typename PT, int RING, int OUT, int NS>
 __global__ void __launch_bounds__(512, 1) split_tmem_kernel(SplitDequeArgs a, int64_t tiles,
                                                             int rec_in_smem, int cols_per_warp) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -598,6 +633,7 @@ __global__ void __launch_bounds__(512, 1) split_tmem_kernel(SplitDequeArgs a, in
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
+  const int words = tmem_row_words(n, (int)sizeof(QT));
 
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
@@ -611,13 +647,12 @@ __global__ void __launch_bounds__(512, 1) split_tmem_kernel(SplitDequeArgs a, in
     rec = rs;
     off += (size_t)n * sizeof(StepRec);
   }
-  const size_t stage_bytes =
-      OUT == kOutStream ? (((size_t)16 * kStagePitch * sizeof(PT) + 15) & ~(size_t)15) : 0;
-  const size_t per_warp = (size_t)RING * 32 * 8 + stage_bytes;
+  const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, NS>() : 0;
+  const size_t per_warp = (size_t)NS * RING * 32 * 8 + stage_bytes;
   unsigned char* wbase = smem + off + per_warp * warp;
-  float* ring_psi = reinterpret_cast<float*>(wbase);
-  uint32_t* ring_meta = reinterpret_cast<uint32_t*>(ring_psi + RING * 32);
-  PT* stage = reinterpret_cast<PT*>(ring_meta + RING * 32);
+  float* ring_psi = reinterpret_cast<float*>(wbase);                        // [NS][RING][32]
+  uint32_t* ring_meta = reinterpret_cast<uint32_t*>(ring_psi + NS * RING * 32);
+  PT* stage = reinterpret_cast<PT*>(ring_meta + NS * RING * 32);
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
@@ -629,41 +664,52 @@ __global__ void __launch_bounds__(512, 1) split_tmem_kernel(SplitDequeArgs a, in
   uint32_t any_inf = 0, any_fb = 0;
   const int64_t wstride = (int64_t)gridDim.x * nwarps;
   for (int64_t tile = (int64_t)blockIdx.x * nwarps + warp; tile < tiles; tile += wstride) {
-    const int64_t s0 = tile * 32;
-    const int rows = (int)imin64(32, a.S - s0);
-    const TileFlags tf = ingest_tile_tmem<QT>(a.demands + s0 * n, rows, n, Q, taddr, lane);
-    neg |= tf.neg;
-    NextTile nxt{nullptr, 0, 0};
-    if (tile + wstride < tiles) {
-      const int64_t ns0 = (tile + wstride) * 32;
-      nxt = NextTile{a.demands + ns0 * n, imin64(32, a.S - ns0) * n * 4, (3 * n) / 4};
+    const int64_t s0 = tile * (NS * 32);
+    const int rows = (int)imin64(NS * 32, a.S - s0);
+    uint32_t inf_rows[NS];
+    bool any_inf_tile = false;
+    TmemQ<QT> src[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int rs_ = max(0, min(32, rows - 32 * s));
+      const TileFlags tf = ingest_tile_tmem<QT>(a.demands + (s0 + 32 * s) * n, rs_, n, Q,
+                                                taddr + s * words, lane);
+      neg |= tf.neg;
+      inf_rows[s] = tf.inf_rows;
+      any_inf_tile |= tf.inf_rows != 0u;
+      src[s] = TmemQ<QT>{taddr + (uint32_t)(s * words), 0u};
     }
-    uint32_t first_inf = (uint32_t)n + 1;
-    bool bad = false;
+    uint32_t first_inf[NS];
+    bool bad[NS];
+    float K[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) { first_inf[s] = (uint32_t)n + 1; bad[s] = false; }
     PT* pred_tile = a.pred ? reinterpret_cast<PT*>(a.pred) + s0 * n : nullptr;
-    const bool valid = lane < rows;
-    TmemQ<QT> src{taddr, 0u};
-    float K;
-    if (tf.inf_rows)
-      K = dp_row<QT, PT, RING, OUT, true, true>(src, (QT*)nullptr, n, Q, rec, ring_psi,
-                                               ring_meta, lane, stage, pred_tile,
-                                               pred_tile ? rows : 0, false, nxt, first_inf, bad);
+    if (any_inf_tile)
+      dp_rows<NS, QT, PT, RING, OUT, true, true>(src, (QT*)nullptr, n, Q, rec, ring_psi,
+                                                 ring_meta, lane, stage, pred_tile,
+                                                 pred_tile ? rows : 0, false, first_inf, bad, K);
     else
-      K = dp_row<QT, PT, RING, OUT, false, true>(src, (QT*)nullptr, n, Q, rec, ring_psi,
-                                                ring_meta, lane, stage, pred_tile,
-                                                pred_tile ? rows : 0, false, nxt, first_inf, bad);
-    bad = bad && valid;
-    if (valid) {
-      if (bad) {
-        const uint32_t k = atomicAdd(a.fb_count, 1u);
-        a.fb_list[k] = (uint32_t)(s0 + lane);
-      } else if (a.cost) {
-        a.cost[s0 + lane] = first_inf <= (uint32_t)n ? CUDART_INF_F
-                                                      : (float)((double)K + Dn);
+      dp_rows<NS, QT, PT, RING, OUT, false, true>(src, (QT*)nullptr, n, Q, rec, ring_psi,
+                                                  ring_meta, lane, stage, pred_tile,
+                                                  pred_tile ? rows : 0, false, first_inf, bad, K);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int r = 32 * s + lane;
+      const bool valid = r < rows;
+      const bool b = bad[s] && valid;
+      if (valid) {
+        if (b) {
+          const uint32_t k = atomicAdd(a.fb_count, 1u);
+          a.fb_list[k] = (uint32_t)(s0 + r);
+        } else if (a.cost) {
+          a.cost[s0 + r] = first_inf[s] <= (uint32_t)n ? CUDART_INF_F
+                                                        : (float)((double)K[s] + Dn);
+        }
       }
+      any_inf |= inf_rows[s];
+      any_fb |= __ballot_sync(0xffffffffu, b);
     }
-    any_inf |= tf.inf_rows;
-    any_fb |= __ballot_sync(0xffffffffu, bad);
     __syncwarp();
   }
   if (lane == 0) {
@@ -679,8 +725,7 @@ __global__ void __launch_bounds__(512, 1) split_tmem_kernel(SplitDequeArgs a, in
 
 // Batched Split: a persistent grid pulls work items (tour, 32-scenario tile)
 // from a global counter; items are ordered longest tour first, so the uneven
-// tours finish together.  Each warp grabs its next item before working on the
-// current one and warms L2 with that item's demand rows.
+// tours finish together.
 template <typename QT, int RING>
 __global__ void __launch_bounds__(256, 1) split_batch_kernel(BatchKernelArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -714,29 +759,21 @@ __global__ void __launch_bounds__(256, 1) split_batch_kernel(BatchKernelArgs a) 
                                          Q, qb, lane);
     neg |= tf.neg;
     const int64_t next = pop();
-    NextTile nxt{nullptr, 0, 0};
-    if (next < items) {
-      const int nb = a.order[next / tiles];
-      const int64_t ns0 = (next % tiles) * 32;
-      const int nn = a.n[nb];
-      nxt = NextTile{a.demands + a.dem_off[nb] + ns0 * nn, imin64(32, a.S - ns0) * nn * 4,
-                     (3 * n) / 4};
-    }
     __syncwarp();
     uint32_t first_inf = (uint32_t)n + 1;
     bool bad = false;
+    float K;
     QT* row = qb + lane * rs_elems;
     const StepRec* rec = a.rec + a.rec_off[b];
     SmemQ<QT> src{row, 0};
-    float K;
     if (tf.inf_rows)
-      K = dp_row<QT, int32_t, RING, kOutNone, true, false>(src, row, n, Q, rec, ring_psi,
+      dp_rows<1, QT, int32_t, RING, kOutNone, true, false>(&src, row, n, Q, rec, ring_psi,
                                                            ring_meta, lane, nullptr, nullptr, 0,
-                                                           false, nxt, first_inf, bad);
+                                                           false, &first_inf, &bad, &K);
     else
-      K = dp_row<QT, int32_t, RING, kOutNone, false, false>(src, row, n, Q, rec, ring_psi,
+      dp_rows<1, QT, int32_t, RING, kOutNone, false, false>(&src, row, n, Q, rec, ring_psi,
                                                             ring_meta, lane, nullptr, nullptr, 0,
-                                                            false, nxt, first_inf, bad);
+                                                            false, &first_inf, &bad, &K);
     const bool valid = lane < rows;
     bad = bad && valid;
     if (valid) {
@@ -761,6 +798,104 @@ __global__ void __launch_bounds__(256, 1) split_batch_kernel(BatchKernelArgs a) 
   }
 }
 
+// Batched Split with TMEM staging: one CTA per SM owns all 512 TMEM columns;
+// warp w holds its tile in lane quadrant w % 4, column block w / 4 of
+// cols_per_warp columns (16 warps x 128, 8 x 256 or 4 x 512 columns), and
+// copies the current tour's records into its own shared-memory slice.
+template <typename QT, int RING>
+__global__ void __launch_bounds__(512, 1) split_batch_tmem_kernel(BatchKernelArgs a,
+                                                                  int cols_per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t tmem_base;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int Q = a.Q;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  const size_t rec_bytes = (size_t)a.n_max * sizeof(StepRec);
+  const size_t per_warp = (size_t)RING * 32 * 8 + rec_bytes;
+  unsigned char* wbase = smem + per_warp * warp;
+  float* ring_psi = reinterpret_cast<float*>(wbase);
+  uint32_t* ring_meta = reinterpret_cast<uint32_t*>(ring_psi + RING * 32);
+  StepRec* rec_sm = reinterpret_cast<StepRec*>(ring_meta + RING * 32);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t taddr = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) +
+                         (uint32_t)((warp >> 2) * cols_per_warp);
+  const int64_t tiles = (a.S + 31) / 32;
+  const int64_t items = tiles * a.B;
+  bool neg = false;
+  uint32_t any_inf = 0, any_fb = 0;
+
+  auto pop = [&]() -> int64_t {
+    unsigned long long k = 0;
+    if (lane == 0) k = atomicAdd(a.counter, 1ull);
+    return (int64_t)__shfl_sync(0xffffffffu, k, 0);
+  };
+  int64_t item = pop();
+  int cur_b = -1;
+  while (item < items) {
+    const int b = a.order[item / tiles];
+    const int64_t s0 = (item % tiles) * 32;
+    const int n = a.n[b];
+    const int rows = (int)imin64(32, a.S - s0);
+    if (b != cur_b) {  // this tour's records into the warp's slice
+      __syncwarp();
+      const int4* src4 = reinterpret_cast<const int4*>(a.rec + a.rec_off[b]);
+      int4* dst4 = reinterpret_cast<int4*>(rec_sm);
+      for (int k = lane; k < n; k += 32) dst4[k] = __ldg(src4 + k);
+      __syncwarp();
+      cur_b = b;
+    }
+    const TileFlags tf =
+        ingest_tile_tmem<QT>(a.demands + a.dem_off[b] + s0 * n, rows, n, Q, taddr, lane);
+    neg |= tf.neg;
+    const int64_t next = pop();
+    uint32_t first_inf = (uint32_t)n + 1;
+    bool bad = false;
+    float K;
+    TmemQ<QT> src{taddr, 0u};
+    if (tf.inf_rows)
+      dp_rows<1, QT, int32_t, RING, kOutNone, true, true>(&src, (QT*)nullptr, n, Q, rec_sm,
+                                                          ring_psi, ring_meta, lane, nullptr,
+                                                          nullptr, 0, false, &first_inf, &bad,
+                                                          &K);
+    else
+      dp_rows<1, QT, int32_t, RING, kOutNone, false, true>(&src, (QT*)nullptr, n, Q, rec_sm,
+                                                           ring_psi, ring_meta, lane, nullptr,
+                                                           nullptr, 0, false, &first_inf, &bad,
+                                                           &K);
+    const bool valid = lane < rows;
+    bad = bad && valid;
+    if (valid) {
+      const int64_t g = (int64_t)b * a.S + s0 + lane;
+      if (bad) {
+        const uint32_t k = atomicAdd(a.fb_count, 1u);
+        a.fb_list[k] = (unsigned long long)g;
+      } else {
+        a.costs[g] = first_inf <= (uint32_t)n ? CUDART_INF_F
+                                               : (float)((double)K + a.Dn[b]);
+      }
+    }
+    any_inf |= tf.inf_rows;
+    any_fb |= __ballot_sync(0xffffffffu, bad);
+    __syncwarp();
+    item = next;
+  }
+  if (lane == 0) {
+    if (any_inf) atomicOr(a.status, SDP_FLAG_INFEASIBLE);
+    if (any_fb) atomicOr(a.status, SDP_FLAG_FALLBACK);
+    if (neg) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(tmem_base, 512);
+}
+
 // ------------------------------------------------------------------ host side
 bool deque_supported(int n, int Q) { return n >= 1 && n <= 65534 && Q >= 1 && Q <= 32767; }
 
@@ -768,12 +903,17 @@ namespace {
 int out_mode(bool hist, bool want_pred) {
   return hist ? kOutDelta : (want_pred ? kOutStream : kOutNone);
 }
-size_t stage_bytes_for(int pred_bytes) {
-  return pred_bytes > 0 ? (((size_t)16 * kStagePitch * pred_bytes + 15) & ~(size_t)15) : 0;
+size_t stage_bytes_for(int pred_bytes, int ns) {
+  return pred_bytes > 0 ? (((size_t)kBatch * (ns * 32 + 1) * pred_bytes + 15) & ~(size_t)15) : 0;
 }
-constexpr int kTmemWarps = 16;         // 4 warps per TMEM lane quadrant
-constexpr int kTmemColsPerWarp = 128;  // 512 columns / 4 warps per quadrant
-constexpr size_t kOneCtaPerSmSmem = 120 * 1024;
+// TMEM single-tour launch: kTmemNS scenarios per lane; 16 / kTmemNS warps per
+// SM with 128 * kTmemNS columns each.  Measured at n = 500, S = 10^6: one
+// scenario per lane with 16 warps (2.07 ms) beats two per lane with 8 warps
+// (2.72 ms) -- more warps hide the deque's dependent latencies better than two
+// interleaved chains per thread.
+constexpr int kTmemNS = 1;
+constexpr int kTmemWarps = 16 / kTmemNS;
+constexpr int kTmemColsPerWarp = 512 / (kTmemWarps / 4);
 }  // namespace
 
 DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_bytes,
@@ -783,14 +923,17 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
   c.ring = ring;
   c.rec_in_smem = n <= 4096;
   c.row_stride = staged_row_stride(n, c.qbytes);
+  c.ns = 1;
   const size_t rec = c.rec_in_smem ? (size_t)n * sizeof(StepRec) : 0;
-  const size_t stage = hist ? 0 : stage_bytes_for(pred_bytes);
-  // TMEM staging when the row fits a warp's 128 columns and no in-place
+  // TMEM staging when kTmemNS rows fit a warp's columns and no in-place
   // deltas are needed.
-  c.tmem = allow_tmem && !hist && tmem_row_words(n, c.qbytes) <= kTmemColsPerWarp;
+  c.tmem = allow_tmem && !hist &&
+           kTmemNS * tmem_row_words(n, c.qbytes) <= kTmemColsPerWarp;
   if (c.tmem) {
+    c.ns = kTmemNS;
     c.warps = kTmemWarps;
-    const size_t need = rec + (size_t)c.warps * ((size_t)ring * 32 * 8 + stage);
+    const size_t need =
+        rec + (size_t)c.warps * ((size_t)c.ns * ring * 32 * 8 + stage_bytes_for(pred_bytes, c.ns));
     c.smem = need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
     return c;
   }
@@ -800,6 +943,7 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
     off += ((size_t)n * 2 + 15) & ~(size_t)15;
     off += ((size_t)(2 * n + 1) * 4 + 15) & ~(size_t)15;
   }
+  const size_t stage = hist ? 0 : stage_bytes_for(pred_bytes, 1);
   c.smem = off + (size_t)c.warps * ((size_t)32 * c.row_stride + (size_t)ring * 32 * 8 + stage);
   return c;
 }
@@ -808,9 +952,8 @@ namespace {
 template <typename QT, typename PT, int RING, int OUT>
 int launch_t(const SplitDequeArgs& a, const DequeConfig& c, int grid, cudaStream_t st,
              int* occ_out) {
-  const int64_t tiles = (a.S + 31) / 32;
   if (OUT != kOutDelta && c.tmem) {
-    auto k = split_tmem_kernel<QT, PT, RING, OUT>;
+    auto k = split_tmem_kernel<QT, PT, RING, OUT, kTmemNS>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)c.smem);
     if (e != cudaSuccess) return (int)e;
@@ -819,9 +962,11 @@ int launch_t(const SplitDequeArgs& a, const DequeConfig& c, int grid, cudaStream
       if (*occ_out > 1) *occ_out = 1;  // one TMEM owner per SM
       return (int)e;
     }
+    const int64_t tiles = (a.S + 32 * kTmemNS - 1) / (32 * kTmemNS);
     k<<<grid, c.warps * 32, c.smem, st>>>(a, tiles, c.rec_in_smem ? 1 : 0, kTmemColsPerWarp);
     return (int)cudaGetLastError();
   }
+  const int64_t tiles = (a.S + 31) / 32;
   auto k = split_deque_kernel<QT, PT, RING, OUT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)c.smem);
@@ -865,16 +1010,49 @@ int launch_split_deque(const SplitDequeArgs& a, const DequeConfig& c, int grid,
   return dispatch(a, c, out_mode(a.hist != nullptr, a.pred != nullptr), grid, st, nullptr);
 }
 
+// Batched launch shapes: warps > 0 = shared-memory staging with that many
+// warps per CTA; warps == 0 = TMEM staging (warps per CTA from n_max).
+int batch_tmem_warps(int n_max, int Q) {
+  const int words = tmem_row_words(n_max, Q <= 254 ? 1 : 2);
+  if (words <= 128) return 16;
+  if (words <= 256) return 8;
+  if (words <= 512) return 4;
+  return 0;  // too long for TMEM
+}
+
 size_t batch_smem(int n_max, int Q, int warps, int ring) {
   const int qbytes = Q <= 254 ? 1 : 2;
+  if (warps == 0) {
+    const int tw = batch_tmem_warps(n_max, Q);
+    const size_t need = (size_t)tw * ((size_t)ring * 32 * 8 + (size_t)n_max * sizeof(StepRec));
+    return need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
+  }
   return (size_t)warps * ((size_t)32 * staged_row_stride(n_max, qbytes) + (size_t)ring * 32 * 8);
 }
 
 namespace {
 template <typename QT, int RING>
 int batch_t(const BatchKernelArgs& a, int warps, int grid, cudaStream_t st, int* occ) {
-  auto k = split_batch_kernel<QT, RING>;
   const size_t smem = batch_smem(a.n_max, a.Q, warps, RING);
+  if (warps == 0) {
+    const int tw = batch_tmem_warps(a.n_max, a.Q);
+    if (tw == 0) {
+      if (occ) *occ = 0;
+      return 0;
+    }
+    auto k = split_batch_tmem_kernel<QT, RING>;
+    if (occ) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return (int)e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, tw * 32, smem);
+      if (*occ > 1) *occ = 1;  // one TMEM owner per SM
+      return (int)e;
+    }
+    k<<<grid, tw * 32, smem, st>>>(a, 512 / (tw / 4));
+    return (int)cudaGetLastError();
+  }
+  auto k = split_batch_kernel<QT, RING>;
   if (occ) {  // configuration query (never during a stream capture)
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
