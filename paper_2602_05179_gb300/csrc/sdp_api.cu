@@ -206,7 +206,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     int e = deque_max_ctas_per_sm(cfg, hist != nullptr, a->pred_dtype, pred != nullptr, &occ);
     if (e) return cuda_fail((cudaError_t)e, "deque occupancy");
     if (occ < 1) return fail(SDP_ERR_UNSUPPORTED, "DEQUE configuration does not fit on an SM");
-    const int64_t tiles = (a->S + 32 * cfg.ns - 1) / (32 * cfg.ns);
+    const int64_t tiles = (a->S + 31) / 32;
     const int64_t ctas_needed = (tiles + warps - 1) / warps;
     const int grid = (int)(ctas_needed < (int64_t)occ * sms ? ctas_needed : (int64_t)occ * sms);
     SplitDequeArgs d{};

@@ -86,7 +86,6 @@ struct DequeConfig {
   int row_stride;   // bytes per staged demand row (shared-memory staging)
   bool rec_in_smem; // tour records copied to shared memory (n <= 4096)
   bool tmem;        // demand rows staged in tensor memory (one CTA per SM)
-  int ns;           // scenarios per lane (tile = ns * 32 scenarios)
   size_t smem;      // dynamic shared memory per CTA
 };
 bool deque_supported(int n, int Q);

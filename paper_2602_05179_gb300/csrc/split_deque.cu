@@ -76,7 +76,7 @@ __device__ __forceinline__ StepRec ld_rec_any(const StepRec* p) {
   r.col = (uint32_t)v.x;
   r.a = __int_as_float(v.y);
   r.ce = __int_as_float(v.z);
-  r.pad = 0u;
+  r.pad = (uint32_t)v.w;
   return r;
 }
 
@@ -91,7 +91,7 @@ __device__ __forceinline__ StepRec ld_rec_shared(uint32_t saddr) {
   r.col = (uint32_t)v.x;
   r.a = __int_as_float(v.y);
   r.ce = __int_as_float(v.z);
-  r.pad = 0u;
+  r.pad = (uint32_t)v.w;
   return r;
 }
 
@@ -144,29 +144,54 @@ __device__ __forceinline__ void tmem_wait_st() {
 }
 
 // ------------------------------------------------------------ demand sources
-// Shared-memory row of one scenario.
+// Shared-memory row of one scenario: demand of customer r.col.
 template <typename QT>
 struct SmemQ {
   QT* row;
   int pending;
-  __device__ __forceinline__ void prefetch(uint32_t col) { pending = (int)row[col]; }
-  __device__ __forceinline__ int take(uint32_t /*col*/) { return pending; }
+  __device__ __forceinline__ void prefetch(const StepRec& r) { pending = (int)row[r.col]; }
+  __device__ __forceinline__ int take(const StepRec& /*r*/) { return pending; }
 };
 
-// TMEM row: 32-bit column c / (4 / sizeof(QT)) of the warp's lane.
+// TMEM row of the warp's lane.  The TMEM kernels rewrite their shared copy of
+// the records (tmem_rec): col = the 32-bit column holding customer s_i's
+// demand, pad = the byte-permute selector that extracts it.
+template <typename QT>
+__device__ __forceinline__ StepRec tmem_rec(StepRec r) {
+  const uint32_t c = r.col;
+  if (sizeof(QT) == 1) {
+    r.col = c >> 2;
+    r.pad = 0x4440u | (c & 3u);  // byte c % 4, upper bytes from the zero operand
+  } else {
+    const uint32_t b = 2u * (c & 1u);
+    r.col = c >> 1;
+    r.pad = 0x4400u | ((b + 1u) << 4) | b;  // half c % 2
+  }
+  return r;
+}
+
 template <typename QT>
 struct TmemQ {
   uint32_t taddr;  // lane field = warp quadrant, column = first word of the row
   uint32_t word;
-  __device__ __forceinline__ void prefetch(uint32_t col) {
+  // Issued with the warp converged: at the start of a row and right after take.
+  __device__ __forceinline__ void prefetch(const StepRec& r) { word = tmem_ld1(taddr + r.col); }
+  __device__ __forceinline__ int take(const StepRec& r) {
     __syncwarp();  // the deque loops diverge; tcgen05 ops need the whole warp
-    word = tmem_ld1(taddr + (sizeof(QT) == 1 ? (col >> 2) : (col >> 1)));
-  }
-  __device__ __forceinline__ int take(uint32_t col) {
-    __syncwarp();
     tmem_wait_ld(word);
-    if (sizeof(QT) == 1) return (int)((word >> ((col & 3u) * 8u)) & 0xFFu);
-    return (int)((word >> ((col & 1u) * 16u)) & 0xFFFFu);
+    return (int)__byte_perm(word, 0u, r.pad);
+  }
+};
+
+// Shared-memory row read through the TMEM records (col = 32-bit word, pad =
+// byte-permute selector), for the extra shared-memory warps of the TMEM kernel.
+template <typename QT>
+struct SmemWordQ {
+  const uint32_t* row;
+  uint32_t word;
+  __device__ __forceinline__ void prefetch(const StepRec& r) { word = row[r.col]; }
+  __device__ __forceinline__ int take(const StepRec& r) {
+    return (int)__byte_perm(word, 0u, r.pad);
   }
 };
 
@@ -174,6 +199,7 @@ struct TileFlags {
   uint32_t inf_rows;  // rows with a demand above Q
   bool zero;          // some demand <= 0 in the tile (routes may exceed 255)
   bool neg;
+  bool small_loads;   // every row's total demand is below 2^16 (n * max < 2^16)
 };
 
 template <typename QT>
@@ -258,6 +284,7 @@ __device__ __forceinline__ TileFlags ingest_tile(const int32_t* src, int rows, i
   t.inf_rows = __reduce_or_sync(0xffffffffu, inf_rows);
   t.zero = __any_sync(0xffffffffu, zero);
   t.neg = __any_sync(0xffffffffu, neg);
+  t.small_loads = false;
   return t;
 }
 
@@ -282,7 +309,18 @@ __device__ __forceinline__ uint32_t pack_q(const int* v, int Q, bool& zero, bool
   return word;
 }
 
+// Low bytes (uint8 rows) or halves (uint16 rows) of PER int32 demands packed
+// into one word, element e at bits [e * 8 * sizeof(QT), ...).
 template <typename QT>
+__device__ __forceinline__ uint32_t pack_raw(const int* v) {
+  if (sizeof(QT) == 1)
+    return __byte_perm(__byte_perm(v[0], v[1], 0x0040), __byte_perm(v[2], v[3], 0x0040), 0x5410);
+  return __byte_perm(v[0], v[1], 0x5410);
+}
+
+// WPI: 32-bit words per lane per iteration (WPI * 4 / sizeof(QT) / 4 16-byte
+// loads in flight per lane).
+template <typename QT, int WPI = 16>
 __device__ __forceinline__ TileFlags ingest_tile_tmem(const int32_t* src, int rows, int n,
                                                       int Q, uint32_t taddr, int lane) {
   constexpr int PER = 4 / (int)sizeof(QT);  // demands per word
@@ -292,7 +330,45 @@ __device__ __forceinline__ TileFlags ingest_tile_tmem(const int32_t* src, int ro
   bool zero = false, neg = false, inf = false;
   const bool vec = ((n & 3) == 0) && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
   if (vec) {
-    constexpr int WPI = 16;  // words per iteration (16 x 16-byte loads in flight for uint8)
+    // Fast pass: pack without clamping, tracking each row's minimum and
+    // maximum; a tile with a demand outside [0, Q] is packed again below with
+    // the clamp and the per-row flags.
+    constexpr int LOADS = WPI * PER / 4;
+    int mn = 0, mx = 0;  // the zero padding is inside [0, Q] anyway
+    for (int w0 = 0; w0 < words; w0 += WPI) {
+      int4 x[LOADS];
+#pragma unroll
+      for (int k = 0; k < LOADS; ++k) {
+        const int c = w0 * PER + 4 * k;
+        x[k] = (live && c < n) ? ld_v4(row + c) : make_int4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < LOADS; ++k) {
+        mn = __vimin3_s32(mn, x[k].x, x[k].y);
+        mn = __vimin3_s32(mn, x[k].z, x[k].w);
+        mx = __vimax3_s32(mx, x[k].x, x[k].y);
+        mx = __vimax3_s32(mx, x[k].z, x[k].w);
+      }
+      const int* xv = reinterpret_cast<const int*>(x);
+      uint32_t pk[WPI];
+#pragma unroll
+      for (int k = 0; k < WPI; ++k) pk[k] = pack_raw<QT>(xv + k * PER);
+#pragma unroll
+      for (int k = 0; k < WPI; k += 4)
+        if (w0 + k < words) tmem_st4(taddr + w0 + k, pk[k], pk[k + 1], pk[k + 2], pk[k + 3]);
+    }
+    tmem_wait_st();
+    if (!__any_sync(0xffffffffu, mn < 0 || mx > Q)) {
+      TileFlags t;
+      t.inf_rows = 0u;
+      t.zero = true;  // conservative (the TMEM kernels write no in-place deltas)
+      t.neg = false;
+      t.small_loads = !__any_sync(0xffffffffu, n * mx >= 65536);  // n <= 512, mx <= Q
+      return t;
+    }
+  }
+  // General pass: clamp to [0, Q + 1] and flag rows with a demand above Q.
+  if (vec) {
     constexpr int LOADS = WPI * PER / 4;
     for (int w0 = 0; w0 < words; w0 += WPI) {
       int4 x[LOADS];
@@ -326,81 +402,166 @@ __device__ __forceinline__ TileFlags ingest_tile_tmem(const int32_t* src, int ro
   tmem_wait_st();
   TileFlags t;
   t.inf_rows = __ballot_sync(0xffffffffu, inf && live);
-  t.zero = __any_sync(0xffffffffu, zero);
-  t.neg = __any_sync(0xffffffffu, neg);
+  t.zero = __any_sync(0xffffffffu, zero && live);
+  t.neg = __any_sync(0xffffffffu, neg && live);
+  t.small_loads = false;
   return t;
 }
 
 // Output modes of the DP
 constexpr int kOutNone = 0;    // cost only (batched plans)
 constexpr int kOutStream = 1;  // predecessors streamed out every 16 positions
+constexpr int kOutDirect = 3;  // predecessors stored by each lane, 4 per store
 constexpr int kOutDelta = 2;   // i - pred(i) written in place over the consumed
                                // demand byte (on-chip backtrack of the adjoint)
 
+// Ring bytes per warp: RING entries x 32 lanes of an 8-byte (psi, prefix load)
+// pair and a 16-bit position.
+__host__ __device__ constexpr size_t ring_bytes(int ring) { return (size_t)ring * 32 * 10; }
+
 // Deque state of one scenario (see the file comment): ring[head .. tail) in
 // shared memory ([entry][lane] layout), the front and the back's psi in
-// registers.  Each DP step is split into phases so that several scenarios of a
-// lane can be interleaved and share the warp votes that route the rare extra
-// pops to a loop.
-template <int RING>
+// registers.  Prefix loads are kept mod 2^32: every difference taken is a
+// route load below 2^32, so unsigned subtraction is exact.  Each DP step is
+// split into phases so that several scenarios of a lane can be interleaved and
+// share the warp votes that route the extra pops to loops.
+//  - An empty deque has bpsi = -inf, so "pop the back" is a single compare.
+//  - The front registers are refreshed by the back phase when it empties the
+//    deque (the new entry becomes the front), and start as entry p = 0.
+//  - Without over-capacity demands in the tile (CHECK false) the newest entry
+//    (route s_i alone, load q_i <= Q) never pops, so the straight-line first
+//    front pop needs no size test.  The pop loop keeps it: every loop here ends
+//    after at most n iterations whatever the data (rows of idle lanes may hold
+//    stale values).
+// PACKED (every prefix load of the tile below 2^16): an entry is one 8-byte
+// word pair (psi bits, L(p) << 16 | p) and the position ring is unused.
+template <int RING, bool PACKED = false>
 struct DequeState {
-  float* rpsi;        // this scenario's ring of psi values (+lane applied)
-  uint32_t* rmeta;    // (16-bit prefix load << 16) | index
-  int head, tail, maxcnt, L, fL, fidx;
+  uint2* rpl;         // (psi bits, prefix load L(p)) of this scenario's ring (+lane)
+  uint16_t* ridx;     // position p of each entry
+  int head, tail, maxcnt, fidx;
+  uint32_t L, fL;     // prefix load through the current position, at the front
   float K, bpsi, fpsi;
 
-  __device__ __forceinline__ void init(float* ring_psi, uint32_t* ring_meta, int lane) {
-    rpsi = ring_psi + lane;
-    rmeta = ring_meta + lane;
-    head = tail = maxcnt = L = fL = fidx = 0;
-    K = bpsi = fpsi = 0.f;
+  __device__ __forceinline__ void init(uint2* ring_pl, uint16_t* ring_idx, int lane,
+                                       float psi0) {
+    rpl = ring_pl + lane;
+    ridx = ring_idx + lane;
+    head = tail = maxcnt = fidx = 0;
+    L = fL = 0u;
+    K = 0.f;
+    bpsi = -CUDART_INF_F;
+    fpsi = psi0;  // entry p = 0, pushed by the first step
   }
-  __device__ __forceinline__ float at_psi(int k) const { return rpsi[(k & (RING - 1)) * 32]; }
+  __device__ __forceinline__ bool back_needed(float psi) const { return bpsi > psi; }
+  __device__ __forceinline__ void pop_back() {
+    --tail;
+    bpsi = tail > head ? __uint_as_float(rpl[((tail - 1) & (RING - 1)) * 32].x) : -CUDART_INF_F;
+  }
   // first back pop (straight-line); true if this scenario needs more
   __device__ __forceinline__ bool back1(float psi) {
-    const bool pb = tail > head && bpsi > psi;
-    if (pb) {
-      --tail;
-      bpsi = at_psi(tail - 1);
-    }
-    return pb && tail > head && bpsi > psi;
+    const bool pb = back_needed(psi);
+    if (pb) pop_back();
+    return pb && back_needed(psi);
   }
   __device__ __forceinline__ void back_more(float psi) {
-    while (tail > head && bpsi > psi) {
-      --tail;
-      if (tail > head) bpsi = at_psi(tail - 1);
+    while (back_needed(psi)) pop_back();
+  }
+  // after the back pops: an emptied deque's front is the entry pushed next
+  __device__ __forceinline__ void refront(float psi, int i) {
+    if (tail == head) {
+      fpsi = psi;
+      fL = L;
+      fidx = i - 1;
     }
   }
   // push p = i-1 (an equal psi stays behind the older entry: smallest p wins)
   __device__ __forceinline__ void push(float psi, int i) {
     const int slot = (tail & (RING - 1)) * 32;
-    rpsi[slot] = psi;
-    rmeta[slot] = ((uint32_t)L << 16) | (uint32_t)(i - 1);
-    const bool alone = tail == head;
+    if (PACKED) {
+      rpl[slot] = make_uint2(__float_as_uint(psi), __byte_perm((uint32_t)(i - 1), L, 0x5410));
+    } else {
+      rpl[slot] = make_uint2(__float_as_uint(psi), L);
+      ridx[slot] = (uint16_t)(i - 1);
+    }
     ++tail;
     bpsi = psi;
-    if (alone) { fpsi = psi; fL = L; fidx = i - 1; }
     maxcnt = max(maxcnt, tail - head);
   }
   __device__ __forceinline__ void pop_front() {
     ++head;
     const int h = (head & (RING - 1)) * 32;
-    fpsi = rpsi[h];
-    const uint32_t m = rmeta[h];
-    fidx = (int)(m & 0xFFFFu);
-    fL = L - (int)(((uint32_t)L - (m >> 16)) & 0xFFFFu);  // 16-bit prefix load, widened
+    const uint2 v = rpl[h];
+    fpsi = __uint_as_float(v.x);
+    if (PACKED) {
+      fL = v.y >> 16;
+      fidx = (int)(v.y & 0xFFFFu);
+    } else {
+      fL = v.y;
+      fidx = (int)ridx[h];
+    }
+  }
+  template <bool CHECK>
+  __device__ __forceinline__ bool front_needed(int Q) const {
+    return (!CHECK || tail - head > 1) && L - fL > (uint32_t)Q;
   }
   // extend the window to customer s_i, first front pop; true if more needed
+  template <bool CHECK>
   __device__ __forceinline__ bool front1(int q, int Q) {
-    L += q;
-    const bool pf = tail - head > 1 && L - fL > Q;
+    L += (uint32_t)q;
+    const bool pf = front_needed<CHECK>(Q);
     if (pf) pop_front();
-    return pf && tail - head > 1 && L - fL > Q;
+    return pf && front_needed<CHECK>(Q);
   }
   __device__ __forceinline__ void front_more(int Q) {
-    while (tail - head > 1 && L - fL > Q) pop_front();
+    while (front_needed<true>(Q)) pop_front();
   }
 };
+
+// Predecessor stage: [NS * 32 rows][kBatch positions] with an odd word pitch,
+// so the per-step writes of the 32 lanes (one row each) hit 32 banks.
+template <typename PT>
+__host__ __device__ constexpr int stage_pitch() {
+  return sizeof(PT) == 2 ? kBatch + 2 : kBatch + 1;  // 9 or 17 words
+}
+
+// Rows x positions [i0, i0 + cnt) of the stage -> coalesced row segments of
+// the [S, n] predecessor array.  uint16 pairs go out as 32-bit stores when
+// every segment starts on 4 bytes (n even, aligned base): 8 lanes per row.
+template <typename PT>
+__device__ __forceinline__ void flush_stage(const PT* stage, PT* pred_tile, int n, int i0,
+                                            int cnt, int rows, bool pairs, int lane) {
+  constexpr int P = stage_pitch<PT>();
+  __syncwarp();
+  if (sizeof(PT) == 2 && pairs) {
+    const int k = lane & 7, r0 = lane >> 3;  // pair k of row r0 + 4j
+    if (2 * k < cnt) {
+      const uint32_t* sp = reinterpret_cast<const uint32_t*>(stage) + r0 * (P / 2) + k;
+      uint32_t* dst = reinterpret_cast<uint32_t*>(pred_tile + (int64_t)r0 * n + (i0 - 1)) + k;
+      const int64_t step = 2 * (int64_t)n;  // 4 rows, in 32-bit words
+#pragma unroll 4
+      for (int r = r0; r < rows; r += 4) {
+        *dst = *sp;
+        sp += 4 * (P / 2);
+        dst += step;
+      }
+    }
+  } else {
+    const int k = lane & 15, r0 = lane >> 4;  // position k of row r0 + 2j
+    if (k < cnt) {
+      const PT* sp = stage + r0 * P + k;
+      PT* dst = pred_tile + (int64_t)r0 * n + (i0 - 1) + k;
+      const int64_t step = 2 * (int64_t)n;
+#pragma unroll 4
+      for (int r = r0; r < rows; r += 2) {
+        *dst = *sp;
+        sp += 2 * P;
+        dst += step;
+      }
+    }
+  }
+  __syncwarp();
+}
 
 // The DP of NS scenarios per lane (see the file comment).  Every lane of the
 // warp runs it (lanes beyond the tile on stale data, outputs dropped) so that
@@ -408,94 +569,128 @@ struct DequeState {
 // Scenario s of the lane is tile row s * 32 + lane.
 // CHECK: the tile holds a scenario with a demand above Q; first_inf records
 // the first such position of each scenario.
-// REC_SHARED: rec points to shared memory (loaded as LDS.128).
+// REC_SHARED: rec points to shared memory (loaded as LDS.128) and holds a copy
+// of position n after it.
+// OUT == kOutStream: predecessors through the shared-memory stage (any n);
+// OUT == kOutDirect: each lane stores its own row, 4 positions per 8-byte
+// (uint16) or 16-byte (int32) store, when n % 4 == 0 and the rows are aligned
+// -- no stage, and 4 row segments complete a 32-byte sector.
 // OUT == kOutDelta (NS = 1, shared-memory row): i - pred(i) overwrites the
 // consumed demand byte of customer s_i.
+// UNR: unroll factor of the position loop (1 where registers are tight).
+// PACKED: every prefix load of the tile is below 2^16 (see DequeState).
 template <int NS, typename QT, typename PT, int RING, int OUT, bool CHECK, bool REC_SHARED,
-          typename SRC>
+          typename SRC, int UNR = 2, bool PACKED = false>
 __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const StepRec* rec,
-                                        float* ring_psi, uint32_t* ring_meta, int lane,
+                                        uint2* ring_pl, uint16_t* ring_idx, int lane,
                                         PT* stage, PT* pred_tile, int rows, bool check_delta,
                                         uint32_t* first_inf, bool* bad, float* K_out) {
-  constexpr int kPitch = NS * 32 + 1;  // predecessor stage pitch (elements)
-  DequeState<RING> st[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s)
-    st[s].init(ring_psi + s * RING * 32, ring_meta + s * RING * 32, lane);
+  constexpr int kP = stage_pitch<PT>();
   const uint32_t rec_s = REC_SHARED ? (uint32_t)__cvta_generic_to_shared(rec) : 0u;
   auto load_rec = [&](int k) -> StepRec {
     if (REC_SHARED) return ld_rec_shared(rec_s + 16u * (uint32_t)k);
     return ld_rec_any(rec + k);
   };
   StepRec rn = load_rec(0);
+  DequeState<RING, PACKED> st[NS];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) src[s].prefetch(rn.col);
-  for (int i0 = 1; i0 <= n; i0 += kBatch) {
-    const int ie = min(n, i0 + kBatch - 1);
-#pragma unroll 2
-    for (int i = i0; i <= ie; ++i) {
-      const StepRec r = rn;
-      int q[NS];
+  for (int s = 0; s < NS; ++s)
+    st[s].init(ring_pl + s * RING * 32, ring_idx + s * RING * 32, lane, __fadd_rn(0.f, rn.a));
 #pragma unroll
-      for (int s = 0; s < NS; ++s) q[s] = src[s].take(r.col);
-      // next position's record and demand (the last step re-reads position n)
-      rn = load_rec(min(i, n - 1));
+  for (int s = 0; s < NS; ++s) src[s].prefetch(rn);
+
+  // One DP step at position i; p[s] = pred(i) of scenario s (-1 once infeasible).
+  auto step = [&](int i, int* p) {
+    const StepRec r = rn;
+    int q[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) src[s].prefetch(rn.col);
-      float psi[NS];
-      bool more = false;
+    for (int s = 0; s < NS; ++s) q[s] = src[s].take(r);
+    // next position's record and demand
+    rn = load_rec(REC_SHARED ? i : min(i, n - 1));
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        psi[s] = __fadd_rn(st[s].K, r.a);
-        more |= st[s].back1(psi[s]);
-      }
+    for (int s = 0; s < NS; ++s) src[s].prefetch(rn);
+    // Back pops depend mostly on the tour (psi differences are dominated by
+    // the a_i), so the lanes of a warp pop together or not at all: one vote
+    // skips the whole phase on the steps without pops.
+    float psi[NS];
+    bool more = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      psi[s] = __fadd_rn(st[s].K, r.a);
+      more |= st[s].back_needed(psi[s]);
+    }
+    if (__any_sync(0xffffffffu, more)) {
+      more = false;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) more |= st[s].back1(psi[s]);
       if (__any_sync(0xffffffffu, more)) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) st[s].back_more(psi[s]);
       }
-      more = false;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) st[s].refront(psi[s], i);
+    }
+    more = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      st[s].push(psi[s], i);
+      if (CHECK && q[s] > Q && first_inf[s] > (uint32_t)n) first_inf[s] = (uint32_t)i;
+      more |= st[s].template front1<CHECK>(q[s], Q);
+    }
+    if (__any_sync(0xffffffffu, more)) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) st[s].front_more(Q);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      st[s].K = __fadd_rn(st[s].fpsi, r.ce);
+      p[s] = (CHECK && (uint32_t)i >= first_inf[s]) ? -1 : st[s].fidx;
+      if (OUT == kOutDelta) {
+        const uint32_t delta = (uint32_t)(i - st[s].fidx);
+        if (check_delta && delta > (sizeof(QT) == 1 ? 255u : 65535u)) bad[s] = true;
+        row[r.col] = (QT)delta;
+      }
+    }
+  };
+
+  if (OUT == kOutDirect) {
+    PT* prow[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) prow[s] = pred_tile + (int64_t)(s * 32 + lane) * n;
+    for (int i = 1; i <= n; i += 4) {
+      int p[4][NS];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) step(i + u, p[u]);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        st[s].push(psi[s], i);
-        if (CHECK && q[s] > Q && first_inf[s] > (uint32_t)n) first_inf[s] = (uint32_t)i;
-        more |= st[s].front1(q[s], Q);
-      }
-      if (__any_sync(0xffffffffu, more)) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) st[s].front_more(Q);
-      }
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        st[s].K = __fadd_rn(st[s].fpsi, r.ce);
-        if (OUT == kOutStream) {
-          int p = st[s].fidx;
-          if (CHECK && (uint32_t)i >= first_inf[s]) p = -1;
-          stage[(i - i0) * kPitch + s * 32 + lane] = (PT)p;
-        } else if (OUT == kOutDelta) {
-          const uint32_t delta = (uint32_t)(i - st[s].fidx);
-          if (check_delta && delta > (sizeof(QT) == 1 ? 255u : 65535u)) bad[s] = true;
-          row[r.col] = (QT)delta;
+        if (s * 32 + lane < rows) {
+          if (sizeof(PT) == 2) {
+            *reinterpret_cast<uint2*>(prow[s] + (i - 1)) =
+                make_uint2(__byte_perm(p[0][s], p[1][s], 0x5410),
+                           __byte_perm(p[2][s], p[3][s], 0x5410));
+          } else {
+            *reinterpret_cast<int4*>(prow[s] + (i - 1)) =
+                make_int4(p[0][s], p[1][s], p[2][s], p[3][s]);
+          }
         }
       }
     }
-    if (OUT == kOutStream) {
-      // rows x positions [i0, ie] of the staged batch -> coalesced row segments
-      __syncwarp();
-      constexpr int kRowsPerPass = 32 / kBatch;
-      const int cnt = ie - i0 + 1;
-      const int u = lane % kBatch;
-      const int r0 = lane / kBatch;
-      PT* dst = pred_tile + (int64_t)r0 * n + (i0 - 1) + u;
-      const PT* sp = stage + u * kPitch + r0;
-      const int64_t stepr = kRowsPerPass * (int64_t)n;
-      if (u < cnt) {
-#pragma unroll 4
-        for (int r2 = 0; r2 < rows - r0; r2 += kRowsPerPass) {
-          *dst = sp[r2];
-          dst += stepr;
+  } else {
+    const bool pairs = sizeof(PT) == 2 && (n & 1) == 0 &&
+                       (reinterpret_cast<uintptr_t>(pred_tile) & 3) == 0;
+    for (int i0 = 1; i0 <= n; i0 += kBatch) {
+      const int ie = min(n, i0 + kBatch - 1);
+#pragma unroll UNR
+      for (int i = i0; i <= ie; ++i) {
+        int p[NS];
+        step(i, p);
+        if (OUT == kOutStream) {
+#pragma unroll
+          for (int s = 0; s < NS; ++s) stage[(s * 32 + lane) * kP + (i - i0)] = (PT)p[s];
         }
       }
-      __syncwarp();
+      if (OUT == kOutStream)
+        flush_stage<PT>(stage, pred_tile, n, i0, ie - i0 + 1, rows, pairs, lane);
     }
   }
 #pragma unroll
@@ -510,7 +705,7 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
 // ------------------------------------------------------------------ kernels
 template <typename PT, int NS>
 __host__ __device__ constexpr size_t stage_bytes_of() {
-  return (((size_t)kBatch * (NS * 32 + 1) * sizeof(PT)) + 15) & ~(size_t)15;
+  return (((size_t)NS * 32 * stage_pitch<PT>() * sizeof(PT)) + 15) & ~(size_t)15;
 }
 
 // Single tour, shared-memory staging (all output modes, incl. the adjoint).
@@ -546,12 +741,12 @@ __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
     for (int k = threadIdx.x; k < 2 * n + 1; k += blockDim.x) hist_sm[k] = 0u;
   }
   const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, 1>() : 0;
-  const size_t per_warp = (size_t)32 * row_stride + (size_t)RING * 32 * 8 + stage_bytes;
+  const size_t per_warp = (size_t)32 * row_stride + ring_bytes(RING) + stage_bytes;
   unsigned char* wbase = smem + off + per_warp * warp;
   QT* qb = reinterpret_cast<QT*>(wbase);
-  float* ring_psi = reinterpret_cast<float*>(wbase + (size_t)32 * row_stride);
-  uint32_t* ring_meta = reinterpret_cast<uint32_t*>(ring_psi + RING * 32);
-  PT* stage = reinterpret_cast<PT*>(ring_meta + RING * 32);
+  uint2* ring_pl = reinterpret_cast<uint2*>(wbase + (size_t)32 * row_stride);
+  uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + RING * 32);
+  PT* stage = reinterpret_cast<PT*>(ring_idx + RING * 32);
   __syncthreads();
 
   const double Dn = *a.Dn;
@@ -575,11 +770,11 @@ __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
     const bool valid = lane < rows;
     SmemQ<QT> src{row, 0};
     if (tf.inf_rows)
-      dp_rows<1, QT, PT, RING, OUT, true, false>(&src, row, n, Q, rec, ring_psi, ring_meta, lane,
+      dp_rows<1, QT, PT, RING, OUT, true, false>(&src, row, n, Q, rec, ring_pl, ring_idx, lane,
                                                  stage, pred_tile, pred_tile ? rows : 0, tf.zero,
                                                  &first_inf, &bad, &K);
     else
-      dp_rows<1, QT, PT, RING, OUT, false, false>(&src, row, n, Q, rec, ring_psi, ring_meta,
+      dp_rows<1, QT, PT, RING, OUT, false, false>(&src, row, n, Q, rec, ring_pl, ring_idx,
                                                   lane, stage, pred_tile, pred_tile ? rows : 0,
                                                   tf.zero, &first_inf, &bad, &K);
     bad = bad && valid;
@@ -619,40 +814,45 @@ __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
   }
 }
 
-// Single tour, TMEM staging (cost + streamed predecessors), NS scenarios per
-// lane (a tile is NS * 32 scenarios).  One CTA per SM (its dynamic shared
-// memory request guarantees it) allocates all 512 TMEM columns; warp w uses
-// lane quadrant w % 4 and column block w / 4 of cols_per_warp columns, row s of
-// the lane at column offset s * words.
-template <typename QT, typename PT, int RING, int OUT, int NS>
-__global__ void __launch_bounds__(512, 1) split_tmem_kernel(SplitDequeArgs a, int64_t tiles,
-                                                            int rec_in_smem, int cols_per_warp) {
+// Single tour, TMEM staging (cost + streamed predecessors).  One CTA per SM
+// (its dynamic shared memory request guarantees it) allocates all 512 TMEM
+// columns; warp w < 16 holds its tile in lane quadrant w % 4, column block
+// w / 4 of cols_per_warp columns.  XW more warps stage their tiles in shared
+// memory (rows of row_stride bytes) with the same records: more warps per SM
+// hide more of the deque's dependent latencies, and the TMEM alone holds 16
+// tiles.
+template <typename QT, typename PT, int RING, int OUT, int XW>
+__global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDequeArgs a,
+                                                                     int64_t tiles,
+                                                                     int cols_per_warp,
+                                                                     int row_stride) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t tmem_base;
   const int n = a.n, Q = a.Q;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int words = tmem_row_words(n, (int)sizeof(QT));
+  const bool in_tmem = warp < 16;
 
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
     tmem_relinquish();
   }
-  size_t off = 0;
-  const StepRec* rec = a.rec;
-  if (rec_in_smem) {
-    StepRec* rs = reinterpret_cast<StepRec*>(smem);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) rs[k] = a.rec[k];
-    rec = rs;
-    off += (size_t)n * sizeof(StepRec);
-  }
-  const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, NS>() : 0;
-  const size_t per_warp = (size_t)NS * RING * 32 * 8 + stage_bytes;
+  // tour records in shared memory (a row that fits a warp's TMEM columns has
+  // n <= 512), plus a copy of position n after them
+  StepRec* rec = reinterpret_cast<StepRec*>(smem);
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
+  const size_t off = ((size_t)n + 1) * sizeof(StepRec);
+  const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, 1>() : 0;
+  const size_t per_warp = ring_bytes(RING) + stage_bytes;
   unsigned char* wbase = smem + off + per_warp * warp;
-  float* ring_psi = reinterpret_cast<float*>(wbase);                        // [NS][RING][32]
-  uint32_t* ring_meta = reinterpret_cast<uint32_t*>(ring_psi + NS * RING * 32);
-  PT* stage = reinterpret_cast<PT*>(ring_meta + NS * RING * 32);
+  uint2* ring_pl = reinterpret_cast<uint2*>(wbase);
+  uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + RING * 32);
+  PT* stage = reinterpret_cast<PT*>(ring_idx + RING * 32);
+  QT* qb = in_tmem ? nullptr
+                   : reinterpret_cast<QT*>(smem + off + per_warp * nwarps +
+                                           (size_t)(warp - 16) * 32 * row_stride);
+  const int rs_elems = row_stride / (int)sizeof(QT);
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
@@ -664,52 +864,60 @@ __global__ void __launch_bounds__(512, 1) split_tmem_kernel(SplitDequeArgs a, in
   uint32_t any_inf = 0, any_fb = 0;
   const int64_t wstride = (int64_t)gridDim.x * nwarps;
   for (int64_t tile = (int64_t)blockIdx.x * nwarps + warp; tile < tiles; tile += wstride) {
-    const int64_t s0 = tile * (NS * 32);
-    const int rows = (int)imin64(NS * 32, a.S - s0);
-    uint32_t inf_rows[NS];
-    bool any_inf_tile = false;
-    TmemQ<QT> src[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int rs_ = max(0, min(32, rows - 32 * s));
-      const TileFlags tf = ingest_tile_tmem<QT>(a.demands + (s0 + 32 * s) * n, rs_, n, Q,
-                                                taddr + s * words, lane);
-      neg |= tf.neg;
-      inf_rows[s] = tf.inf_rows;
-      any_inf_tile |= tf.inf_rows != 0u;
-      src[s] = TmemQ<QT>{taddr + (uint32_t)(s * words), 0u};
-    }
-    uint32_t first_inf[NS];
-    bool bad[NS];
-    float K[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) { first_inf[s] = (uint32_t)n + 1; bad[s] = false; }
+    const int64_t s0 = tile * 32;
+    const int rows = (int)imin64(32, a.S - s0);
+    const int32_t* tsrc = a.demands + s0 * n;
+    uint32_t first_inf = (uint32_t)n + 1;
+    bool bad = false;
+    float K;
     PT* pred_tile = a.pred ? reinterpret_cast<PT*>(a.pred) + s0 * n : nullptr;
-    if (any_inf_tile)
-      dp_rows<NS, QT, PT, RING, OUT, true, true>(src, (QT*)nullptr, n, Q, rec, ring_psi,
-                                                 ring_meta, lane, stage, pred_tile,
-                                                 pred_tile ? rows : 0, false, first_inf, bad, K);
-    else
-      dp_rows<NS, QT, PT, RING, OUT, false, true>(src, (QT*)nullptr, n, Q, rec, ring_psi,
-                                                  ring_meta, lane, stage, pred_tile,
-                                                  pred_tile ? rows : 0, false, first_inf, bad, K);
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int r = 32 * s + lane;
-      const bool valid = r < rows;
-      const bool b = bad[s] && valid;
-      if (valid) {
-        if (b) {
-          const uint32_t k = atomicAdd(a.fb_count, 1u);
-          a.fb_list[k] = (uint32_t)(s0 + r);
-        } else if (a.cost) {
-          a.cost[s0 + r] = first_inf[s] <= (uint32_t)n ? CUDART_INF_F
-                                                        : (float)((double)K[s] + Dn);
-        }
-      }
-      any_inf |= inf_rows[s];
-      any_fb |= __ballot_sync(0xffffffffu, b);
+    const int prow = pred_tile ? rows : 0;
+    TileFlags tf;
+    // 20 warps leave 96 registers per thread: no unrolling, fewer loads in flight
+    constexpr int UNR = XW == 0 ? 2 : 1;
+    if (XW == 0 || in_tmem) {
+      using Src = TmemQ<QT>;
+      tf = ingest_tile_tmem<QT, XW == 0 ? 16 : 8>(tsrc, rows, n, Q, taddr, lane);
+      Src src{taddr, 0u};
+      if (tf.inf_rows)
+        dp_rows<1, QT, PT, RING, OUT, true, true, Src, UNR>(
+            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
+            false, &first_inf, &bad, &K);
+      else if (tf.small_loads)
+        dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR, true>(
+            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
+            false, &first_inf, &bad, &K);
+      else
+        dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR>(
+            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
+            false, &first_inf, &bad, &K);
+    } else {
+      using Src = SmemWordQ<QT>;
+      tf = ingest_tile<QT>(tsrc, rows, n, rs_elems, Q, qb, lane);
+      __syncwarp();
+      Src src{reinterpret_cast<const uint32_t*>(qb + lane * rs_elems), 0u};
+      if (tf.inf_rows)
+        dp_rows<1, QT, PT, RING, OUT, true, true, Src, UNR>(
+            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
+            false, &first_inf, &bad, &K);
+      else
+        dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR>(
+            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
+            false, &first_inf, &bad, &K);
     }
+    neg |= tf.neg;
+    const bool valid = lane < rows;
+    bad = bad && valid;
+    if (valid) {
+      if (bad) {
+        const uint32_t k = atomicAdd(a.fb_count, 1u);
+        a.fb_list[k] = (uint32_t)(s0 + lane);
+      } else if (a.cost) {
+        a.cost[s0 + lane] = first_inf <= (uint32_t)n ? CUDART_INF_F : (float)((double)K + Dn);
+      }
+    }
+    any_inf |= tf.inf_rows;
+    any_fb |= __ballot_sync(0xffffffffu, bad);
     __syncwarp();
   }
   if (lane == 0) {
@@ -733,11 +941,11 @@ __global__ void __launch_bounds__(256, 1) split_batch_kernel(BatchKernelArgs a) 
   const int warp = threadIdx.x >> 5;
   const int Q = a.Q;
   const int row_bytes_max = staged_row_stride(a.n_max, (int)sizeof(QT));
-  const size_t per_warp = (size_t)32 * row_bytes_max + (size_t)RING * 32 * 8;
+  const size_t per_warp = (size_t)32 * row_bytes_max + ring_bytes(RING);
   unsigned char* wbase = smem + per_warp * warp;
   QT* qb = reinterpret_cast<QT*>(wbase);
-  float* ring_psi = reinterpret_cast<float*>(wbase + (size_t)32 * row_bytes_max);
-  uint32_t* ring_meta = reinterpret_cast<uint32_t*>(ring_psi + RING * 32);
+  uint2* ring_pl = reinterpret_cast<uint2*>(wbase + (size_t)32 * row_bytes_max);
+  uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + RING * 32);
   const int64_t tiles = (a.S + 31) / 32;
   const int64_t items = tiles * a.B;
   bool neg = false;
@@ -767,12 +975,12 @@ __global__ void __launch_bounds__(256, 1) split_batch_kernel(BatchKernelArgs a) 
     const StepRec* rec = a.rec + a.rec_off[b];
     SmemQ<QT> src{row, 0};
     if (tf.inf_rows)
-      dp_rows<1, QT, int32_t, RING, kOutNone, true, false>(&src, row, n, Q, rec, ring_psi,
-                                                           ring_meta, lane, nullptr, nullptr, 0,
+      dp_rows<1, QT, int32_t, RING, kOutNone, true, false>(&src, row, n, Q, rec, ring_pl,
+                                                           ring_idx, lane, nullptr, nullptr, 0,
                                                            false, &first_inf, &bad, &K);
     else
-      dp_rows<1, QT, int32_t, RING, kOutNone, false, false>(&src, row, n, Q, rec, ring_psi,
-                                                            ring_meta, lane, nullptr, nullptr, 0,
+      dp_rows<1, QT, int32_t, RING, kOutNone, false, false>(&src, row, n, Q, rec, ring_pl,
+                                                            ring_idx, lane, nullptr, nullptr, 0,
                                                             false, &first_inf, &bad, &K);
     const bool valid = lane < rows;
     bad = bad && valid;
@@ -814,12 +1022,12 @@ __global__ void __launch_bounds__(512, 1) split_batch_tmem_kernel(BatchKernelArg
     tmem_alloc(&tmem_base, 512);
     tmem_relinquish();
   }
-  const size_t rec_bytes = (size_t)a.n_max * sizeof(StepRec);
-  const size_t per_warp = (size_t)RING * 32 * 8 + rec_bytes;
+  const size_t rec_bytes = ((size_t)a.n_max + 1) * sizeof(StepRec);
+  const size_t per_warp = ring_bytes(RING) + rec_bytes;
   unsigned char* wbase = smem + per_warp * warp;
-  float* ring_psi = reinterpret_cast<float*>(wbase);
-  uint32_t* ring_meta = reinterpret_cast<uint32_t*>(ring_psi + RING * 32);
-  StepRec* rec_sm = reinterpret_cast<StepRec*>(ring_meta + RING * 32);
+  uint2* ring_pl = reinterpret_cast<uint2*>(wbase);
+  uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + RING * 32);
+  StepRec* rec_sm = reinterpret_cast<StepRec*>(ring_idx + RING * 32);
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
@@ -844,9 +1052,8 @@ __global__ void __launch_bounds__(512, 1) split_batch_tmem_kernel(BatchKernelArg
     const int rows = (int)imin64(32, a.S - s0);
     if (b != cur_b) {  // this tour's records into the warp's slice
       __syncwarp();
-      const int4* src4 = reinterpret_cast<const int4*>(a.rec + a.rec_off[b]);
-      int4* dst4 = reinterpret_cast<int4*>(rec_sm);
-      for (int k = lane; k < n; k += 32) dst4[k] = __ldg(src4 + k);
+      const StepRec* src = a.rec + a.rec_off[b];
+      for (int k = lane; k <= n; k += 32) rec_sm[k] = tmem_rec<QT>(ld_rec_any(src + min(k, n - 1)));
       __syncwarp();
       cur_b = b;
     }
@@ -860,12 +1067,12 @@ __global__ void __launch_bounds__(512, 1) split_batch_tmem_kernel(BatchKernelArg
     TmemQ<QT> src{taddr, 0u};
     if (tf.inf_rows)
       dp_rows<1, QT, int32_t, RING, kOutNone, true, true>(&src, (QT*)nullptr, n, Q, rec_sm,
-                                                          ring_psi, ring_meta, lane, nullptr,
+                                                          ring_pl, ring_idx, lane, nullptr,
                                                           nullptr, 0, false, &first_inf, &bad,
                                                           &K);
     else
       dp_rows<1, QT, int32_t, RING, kOutNone, false, true>(&src, (QT*)nullptr, n, Q, rec_sm,
-                                                           ring_psi, ring_meta, lane, nullptr,
+                                                           ring_pl, ring_idx, lane, nullptr,
                                                            nullptr, 0, false, &first_inf, &bad,
                                                            &K);
     const bool valid = lane < rows;
@@ -904,16 +1111,18 @@ int out_mode(bool hist, bool want_pred) {
   return hist ? kOutDelta : (want_pred ? kOutStream : kOutNone);
 }
 size_t stage_bytes_for(int pred_bytes, int ns) {
-  return pred_bytes > 0 ? (((size_t)kBatch * (ns * 32 + 1) * pred_bytes + 15) & ~(size_t)15) : 0;
+  if (pred_bytes <= 0) return 0;
+  const int pitch = pred_bytes == 2 ? stage_pitch<uint16_t>() : stage_pitch<int32_t>();
+  return (((size_t)ns * 32 * pitch * pred_bytes) + 15) & ~(size_t)15;
 }
-// TMEM single-tour launch: kTmemNS scenarios per lane; 16 / kTmemNS warps per
-// SM with 128 * kTmemNS columns each.  Measured at n = 500, S = 10^6: one
-// scenario per lane with 16 warps (2.07 ms) beats two per lane with 8 warps
-// (2.72 ms) -- more warps hide the deque's dependent latencies better than two
-// interleaved chains per thread.
-constexpr int kTmemNS = 1;
-constexpr int kTmemWarps = 16 / kTmemNS;
-constexpr int kTmemColsPerWarp = 512 / (kTmemWarps / 4);
+// TMEM single-tour launch: 16 warps with 128 TMEM columns each, plus
+// kTmemExtraWarps warps staging in shared memory when their rows fit.
+// Measured at n = 500, S = 10^6: one scenario per lane with 16 warps (2.07 ms)
+// beats two per lane with 8 warps (2.72 ms) -- the DP is bound by dependent
+// latencies, which more warps hide better than two chains per thread.
+constexpr int kTmemColsPerWarp = 128;
+constexpr int kTmemExtraWarps = 0;
+constexpr size_t kMaxSmemPerCta = 227 * 1024;
 }  // namespace
 
 DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_bytes,
@@ -923,17 +1132,20 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
   c.ring = ring;
   c.rec_in_smem = n <= 4096;
   c.row_stride = staged_row_stride(n, c.qbytes);
-  c.ns = 1;
   const size_t rec = c.rec_in_smem ? (size_t)n * sizeof(StepRec) : 0;
-  // TMEM staging when kTmemNS rows fit a warp's columns and no in-place
-  // deltas are needed.
-  c.tmem = allow_tmem && !hist &&
-           kTmemNS * tmem_row_words(n, c.qbytes) <= kTmemColsPerWarp;
+  // TMEM staging when a row fits a warp's columns and no in-place deltas are
+  // needed.
+  c.tmem = allow_tmem && !hist && tmem_row_words(n, c.qbytes) <= kTmemColsPerWarp;
   if (c.tmem) {
-    c.ns = kTmemNS;
-    c.warps = kTmemWarps;
-    const size_t need =
-        rec + (size_t)c.warps * ((size_t)c.ns * ring * 32 * 8 + stage_bytes_for(pred_bytes, c.ns));
+    const size_t base = ((size_t)n + 1) * sizeof(StepRec);
+    const size_t per_warp = ring_bytes(ring) + stage_bytes_for(pred_bytes, 1);
+    c.warps = 16 + kTmemExtraWarps;
+    size_t need = base + (size_t)c.warps * per_warp +
+                  (size_t)kTmemExtraWarps * 32 * c.row_stride;
+    if (need > kMaxSmemPerCta) {
+      c.warps = 16;
+      need = base + (size_t)c.warps * per_warp;
+    }
     c.smem = need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
     return c;
   }
@@ -944,7 +1156,7 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
     off += ((size_t)(2 * n + 1) * 4 + 15) & ~(size_t)15;
   }
   const size_t stage = hist ? 0 : stage_bytes_for(pred_bytes, 1);
-  c.smem = off + (size_t)c.warps * ((size_t)32 * c.row_stride + (size_t)ring * 32 * 8 + stage);
+  c.smem = off + (size_t)c.warps * ((size_t)32 * c.row_stride + ring_bytes(ring) + stage);
   return c;
 }
 
@@ -953,7 +1165,13 @@ template <typename QT, typename PT, int RING, int OUT>
 int launch_t(const SplitDequeArgs& a, const DequeConfig& c, int grid, cudaStream_t st,
              int* occ_out) {
   if (OUT != kOutDelta && c.tmem) {
-    auto k = split_tmem_kernel<QT, PT, RING, OUT, kTmemNS>;
+    // predecessors stored 4 per lane when every row segment is aligned
+    const bool direct = OUT == kOutStream && (a.n & 3) == 0 &&
+                        (reinterpret_cast<uintptr_t>(a.pred) & 15) == 0;
+    auto k = direct ? (c.warps > 16 ? split_tmem_kernel<QT, PT, RING, kOutDirect, kTmemExtraWarps>
+                                    : split_tmem_kernel<QT, PT, RING, kOutDirect, 0>)
+                    : (c.warps > 16 ? split_tmem_kernel<QT, PT, RING, OUT, kTmemExtraWarps>
+                                    : split_tmem_kernel<QT, PT, RING, OUT, 0>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)c.smem);
     if (e != cudaSuccess) return (int)e;
@@ -962,8 +1180,8 @@ int launch_t(const SplitDequeArgs& a, const DequeConfig& c, int grid, cudaStream
       if (*occ_out > 1) *occ_out = 1;  // one TMEM owner per SM
       return (int)e;
     }
-    const int64_t tiles = (a.S + 32 * kTmemNS - 1) / (32 * kTmemNS);
-    k<<<grid, c.warps * 32, c.smem, st>>>(a, tiles, c.rec_in_smem ? 1 : 0, kTmemColsPerWarp);
+    const int64_t tiles = (a.S + 31) / 32;
+    k<<<grid, c.warps * 32, c.smem, st>>>(a, tiles, kTmemColsPerWarp, c.row_stride);
     return (int)cudaGetLastError();
   }
   const int64_t tiles = (a.S + 31) / 32;
@@ -1024,10 +1242,10 @@ size_t batch_smem(int n_max, int Q, int warps, int ring) {
   const int qbytes = Q <= 254 ? 1 : 2;
   if (warps == 0) {
     const int tw = batch_tmem_warps(n_max, Q);
-    const size_t need = (size_t)tw * ((size_t)ring * 32 * 8 + (size_t)n_max * sizeof(StepRec));
+    const size_t need = (size_t)tw * (ring_bytes(ring) + ((size_t)n_max + 1) * sizeof(StepRec));
     return need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
   }
-  return (size_t)warps * ((size_t)32 * staged_row_stride(n_max, qbytes) + (size_t)ring * 32 * 8);
+  return (size_t)warps * ((size_t)32 * staged_row_stride(n_max, qbytes) + ring_bytes(ring));
 }
 
 namespace {

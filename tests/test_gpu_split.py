@@ -76,6 +76,8 @@ def _random_case(seed, n, S, Q, qlo, qhi, dist_mode=False):
     (6, 129, 64, 300, 0, 3, False),     # long windows: > 255 customers per route
     (7, 250, 131, 30000, 1, 500, False),  # uint16, large Q, long routes
     (8, 600, 70, 200, 1, 30, False),      # row too long for tensor memory
+    (9, 256, 96, 30000, 1, 600, False),   # uint16, n % 4 == 0, loads above 2^16
+    (10, 300, 64, 254, 200, 254, False),  # uint8, n % 4 == 0, loads above 2^16
 ])
 def test_split_edge_cases(algo, warps, case):
     """warps=0: default launch (tensor-memory staging when rows fit 512 B);
@@ -111,6 +113,34 @@ def test_split_deque_tilings_bit_identical(ring, warps):
     assert torch.equal(r["cost"], ref["cost"])
     assert torch.equal(r["pred"], ref["pred"])
     assert float(r["mean"]) == float(ref["mean"])
+
+
+@pytest.mark.parametrize("pred_dtype", ["u16", "i32"])
+def test_split_unaligned_pred_output(pred_dtype):
+    """A predecessor array that starts off a 16-byte boundary (a view one
+    element in) takes the staged output path; results equal the aligned call."""
+    import ctypes
+    api = sdp()
+    spec = wl.SPLIT_C1
+    tour, xy, _ = wl.split_tour(spec)
+    q = wl.split_demands(spec)
+    t, c, qd = _cuda(tour), _cuda(xy), _cuda(q)
+    ref = api.split_eval(t, spec.Q, qd, coords=c, preds=pred_dtype)
+    S, n = q.shape
+    buf = torch.full((S * n + 1,), -7, dtype=ref["pred"].dtype, device="cuda")
+    pred = buf[1:].view(S, n)
+    cost = torch.empty(S, dtype=torch.float32, device="cuda")
+    a = api._split_struct(t, spec.Q, qd, c, None, cost, pred, api.PRED_DTYPES[pred_dtype],
+                          "deque", None, 0, 0)
+    lib = api._load()
+    ws = torch.empty(lib.sdp_split_workspace_bytes(ctypes.byref(a)), dtype=torch.uint8,
+                     device="cuda")
+    a.workspace, a.workspace_bytes = ws.data_ptr(), ws.numel()
+    assert lib.sdp_split_eval(ctypes.byref(a), None) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(cost, ref["cost"])
+    assert torch.equal(pred, ref["pred"])
+    assert int(buf[0]) == -7
 
 
 def test_split_deque_ring_overflow_fallback():
