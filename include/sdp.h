@@ -101,7 +101,18 @@ int sdp_device_status(int clear, uint32_t* flags_out);
  *   dist   [(n+1)*(n+1)] fp32 row-major, c(a,b) = dist[a*(n+1)+b].
  * The destination depot n+1 is the same node as the depot 0.
  * demands [S*n] int32, demands[s*n + c-1] = demand of customer c in scenario
- *   s (indexed by customer id; the tour permutes them).  A demand above Q
+ *   s (indexed by customer id; the tour permutes them).  Device memory, or
+ *   page-locked host memory the device can address (cudaHostAlloc, or
+ *   cudaHostRegister with cudaHostRegisterMapped), which must stay unchanged
+ *   until the call's work on the stream has finished.  With host demands,
+ *   sdp_split_eval copies them in chunks of 65,536 scenarios into two staging
+ *   buffers (part of its workspace, which is then larger) on a copy stream
+ *   of the library's own, each chunk's copy overlapping the evaluation of the
+ *   previous one; the copy stream and its events are created on the first
+ *   such call on a device and kept until the process exits, and such calls
+ *   are enqueued one at a time.  sdp_split_count_arcs and
+ *   sdp_split_backward read host demands in place over the host link.
+ *   A demand above Q
  *   makes the scenario infeasible: cost +inf, predecessors -1 (0xFFFF for
  *   uint16), SDP_FLAG_INFEASIBLE raised.  Negative demands raise
  *   SDP_FLAG_NEG_INPUT and are read as 0.

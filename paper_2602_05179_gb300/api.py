@@ -126,6 +126,18 @@ def _dev_ptr(t, name, dtype=None):
     return t.data_ptr()
 
 
+def _demands_ptr(t):
+    """demands: a CUDA tensor, or a page-locked (pinned) CPU tensor that the
+    kernels read over the host link without a staging copy."""
+    if isinstance(t, torch.Tensor) and not t.is_cuda:
+        if not t.is_pinned():
+            raise ValueError("host demands must be in pinned memory (tensor.pin_memory())")
+        if t.dtype != torch.int32 or not t.is_contiguous():
+            raise ValueError("demands must be contiguous int32")
+        return t.data_ptr()
+    return _dev_ptr(t, "demands", torch.int32)
+
+
 def _stream(stream):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -164,7 +176,7 @@ def _split_struct(tour, Q, demands, coords, dist, cost, pred, pred_dtype, algo, 
     a.tour = _dev_ptr(tour, "tour", torch.int32)
     a.coords = _dev_ptr(coords, "coords", torch.float32)
     a.dist = _dev_ptr(dist, "dist", torch.float32)
-    a.demands = _dev_ptr(demands, "demands", torch.int32)
+    a.demands = _demands_ptr(demands)
     a.cost_out = _dev_ptr(cost, "cost")
     a.pred_out = _dev_ptr(pred, "pred")
     a.pred_dtype = pred_dtype
@@ -179,14 +191,15 @@ def split_eval(tour, Q, demands, *, coords=None, dist=None, preds=None, algo="au
                mean=True, warps=0, ring=0, stream=None):
     """Split of one giant tour over S demand scenarios (Eq. eqdpA).
 
-    tour int32 [n] (permutation of 1..n), demands int32 [S, n] by customer id,
+    tour int32 [n] (permutation of 1..n), demands int32 [S, n] by customer id
+    (CUDA, or pinned host memory read by the kernels over the host link),
     coords fp32 [n+1, 2] (node 0 = depot) or dist fp32 [n+1, n+1].
     preds: None, "u16" (returned as int16 holding the uint16 bits) or "i32".
     Returns dict(cost fp32 [S], pred [S, n] or None, mean fp64 0-d tensor or
     None).  Asynchronous on the current stream.
     """
     _load()
-    dev = demands.device
+    dev = tour.device
     n = int(tour.numel())
     S = int(demands.shape[0])
     cost = torch.empty(S, dtype=torch.float32, device=dev)
@@ -209,7 +222,7 @@ def split_count_arcs(tour, Q, demands, *, coords=None, dist=None, per_scenario=T
     """Capacity-feasible arcs (p, i) per scenario (int64 [S]) and their total
     (uint64 stored in an int64 0-d tensor)."""
     _load()
-    dev = demands.device
+    dev = tour.device
     S = int(demands.shape[0])
     arcs = torch.empty(S, dtype=torch.int64, device=dev) if per_scenario else None
     total = torch.zeros((), dtype=torch.int64, device=dev)
@@ -227,7 +240,7 @@ def split_backward(tour, Q, demands, dist, grad_mean, *, pred=None, pred_dtype=N
     times grad_mean (device fp32 scalar).  pred: the forward's predecessors,
     or None to recompute them in the fused forward + backtrack kernel."""
     _load()
-    dev = demands.device
+    dev = tour.device
     n = int(tour.numel())
     grad = torch.empty((n + 1, n + 1), dtype=torch.float32, device=dev)
     hist = torch.empty(2 * n, dtype=torch.int64, device=dev) if want_hist else None

@@ -77,6 +77,40 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The address under which the current device reads p: device or managed
+// memory as is, page-locked host memory mapped for the device through its
+// device pointer; NULL for memory the device cannot read.
+const void* device_readable(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeHost) return at.devicePointer;
+  return nullptr;
+}
+
+// True for page-locked host memory (the device reads it over the host link).
+bool is_host_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+// The arguments with demands replaced by their device-readable address.
+sdp_split_args with_readable_demands(const sdp_split_args* a) {
+  sdp_split_args b = *a;
+  if (a->demands)
+    b.demands = static_cast<const int32_t*>(device_readable(a->demands));
+  return b;
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // workspace carving (every block 256-byte aligned)
@@ -94,7 +128,13 @@ struct Carver {
 constexpr int64_t kPlainSlots = 262144;   // PLAIN: threads in flight (grid-stride)
 constexpr int64_t kFallbackSlots = 4096;  // DEQUE fallback path
 
+// Host demands (sdp_split_eval): chunks of this many scenarios are copied
+// into two device staging buffers while the previous chunk is evaluated.
+constexpr int64_t kHostChunkRows = 65536;
+
 struct SplitWs {
+  int32_t* stage[2];  // host-demand staging buffers [kHostChunkRows * n], or NULL
+  int64_t stage_rows;
   TourPrep prep;
   double* mean_partial;
   uint32_t* fb_count;
@@ -133,8 +173,79 @@ SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
   w.kscratch = c.take<float>((size_t)(n + 1) * w.nslots);
   w.pscratch = backward ? c.take<int32_t>((size_t)n * w.nslots) : nullptr;
   w.hist = backward ? c.take<unsigned long long>(2 * (size_t)n + 1) : nullptr;
+  w.stage[0] = w.stage[1] = nullptr;
+  w.stage_rows = 0;
+  if (!backward && n > 0 && a->S > 0 && is_host_ptr(a->demands)) {
+    w.stage_rows = a->S < kHostChunkRows ? a->S : kHostChunkRows;
+    w.stage[0] = c.take<int32_t>((size_t)w.stage_rows * n);
+    w.stage[1] = c.take<int32_t>((size_t)w.stage_rows * n);
+  }
   w.bytes = c.off;
   return w;
+}
+
+int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
+                   unsigned long long* hist, cudaStream_t st);
+
+// Copy stream and events of the host-demand pipeline, made once per device on
+// first use and kept for the life of the process.
+struct HostPipe {
+  cudaStream_t copy = nullptr;
+  cudaEvent_t start = nullptr, ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
+};
+HostPipe g_pipe[kMaxDev];
+std::mutex g_pipe_mu;
+
+// Split with demands in page-locked host memory: chunk k is copied on the
+// pipeline's copy stream into staging buffer k % 2 while chunk k - 1 runs on
+// the caller's stream; copy k waits for the evaluation of chunk k - 2, which
+// read the same buffer.  The caller's stream ends with every chunk evaluated.
+int run_split_host_chunks(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
+                          cudaStream_t st) {
+  int dev;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  HostPipe& hp = g_pipe[dev];
+  if (!hp.copy) {
+    cudaError_t e = cudaStreamCreateWithFlags(&hp.copy, cudaStreamNonBlocking);
+    for (int b = 0; e == cudaSuccess && b < 2; ++b) {
+      e = cudaEventCreateWithFlags(&hp.ready[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp.done[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp.start, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "host pipeline setup");
+  }
+  // the staging buffers may still be read by earlier work on the caller's stream
+  cudaError_t e = cudaEventRecord(hp.start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.copy, hp.start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "host pipeline start");
+  const int n = a->n;
+  const size_t pbytes = a->pred_dtype == SDP_PRED_U16 ? 2 : 4;
+  int k = 0;
+  for (int64_t s0 = 0; s0 < a->S; s0 += w.stage_rows, ++k) {
+    const int b = k & 1;
+    const int64_t cnt = a->S - s0 < w.stage_rows ? a->S - s0 : w.stage_rows;
+    if (k >= 2) e = cudaStreamWaitEvent(hp.copy, hp.done[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(w.stage[b], a->demands + s0 * n, sizeof(int32_t) * (size_t)cnt * n,
+                          cudaMemcpyHostToDevice, hp.copy);
+    if (e == cudaSuccess) e = cudaEventRecord(hp.ready[b], hp.copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, hp.ready[b], 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.fb_count, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "host pipeline copy");
+    sdp_split_args c = *a;
+    c.S = cnt;
+    c.demands = w.stage[b];
+    c.cost_out = a->cost_out + s0;
+    if (a->pred_out)
+      c.pred_out = static_cast<unsigned char*>(a->pred_out) + (size_t)s0 * n * pbytes;
+    rc = run_split_core(&c, w, status, nullptr, st);
+    if (rc) return rc;
+    e = cudaEventRecord(hp.done[b], st);
+    if (e != cudaSuccess) return cuda_fail(e, "host pipeline record");
+  }
+  return SDP_OK;
 }
 
 int check_split(const sdp_split_args* a, bool need_cost) {
@@ -157,7 +268,9 @@ int check_split(const sdp_split_args* a, bool need_cost) {
       return fail(SDP_ERR_INVALID_ARG, "coords must be a device pointer");
     if (a->dist && !is_device_ptr(a->dist))
       return fail(SDP_ERR_INVALID_ARG, "dist must be a device pointer");
-    if (!is_device_ptr(a->demands)) return fail(SDP_ERR_INVALID_ARG, "demands must be a device pointer");
+    if (!device_readable(a->demands))
+      return fail(SDP_ERR_INVALID_ARG,
+                  "demands must be device memory or page-locked host memory mapped for the device");
   }
   if (a->pred_out) {
     if (a->pred_dtype != SDP_PRED_U16 && a->pred_dtype != SDP_PRED_I32)
@@ -302,9 +415,11 @@ size_t sdp_split_backward_workspace_bytes(const sdp_split_args* a) {
   return carve_split(a, nullptr, true).bytes;
 }
 
-int sdp_split_eval(const sdp_split_args* a, void* stream) {
-  int rc = check_split(a, true);
+int sdp_split_eval(const sdp_split_args* args, void* stream) {
+  int rc = check_split(args, true);
   if (rc) return rc;
+  const sdp_split_args rd = with_readable_demands(args);
+  const sdp_split_args* a = &rd;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const SplitWs need = carve_split(a, nullptr, false);
   rc = check_ws(a->workspace, a->workspace_bytes, need.bytes);
@@ -320,7 +435,10 @@ int sdp_split_eval(const sdp_split_args* a, void* stream) {
     launch_tour_prep(a->tour, a->n, a->coords, a->dist, w.prep, status, w.fb_count, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tour_prep launch");
-    rc = run_split_core(a, w, status, nullptr, st);
+    // host demands: copied chunk by chunk (from the caller's host address)
+    // behind the evaluation of the previous chunk
+    rc = w.stage_rows > 0 ? run_split_host_chunks(args, w, status, st)
+                          : run_split_core(a, w, status, nullptr, st);
     if (rc) return rc;
   }
   if (a->mean_out) {
@@ -381,10 +499,12 @@ int sdp_split_eval_noalloc(const sdp_split_args* a, void* stream) {
   return sdp_split_eval(&b, stream);
 }
 
-int sdp_split_count_arcs(const sdp_split_args* a, int64_t* arcs_out, uint64_t* total_out,
+int sdp_split_count_arcs(const sdp_split_args* args, int64_t* arcs_out, uint64_t* total_out,
                          void* stream) {
-  int rc = check_split(a, false);
+  int rc = check_split(args, false);
   if (rc) return rc;
+  const sdp_split_args rd = with_readable_demands(args);
+  const sdp_split_args* a = &rd;
   if (arcs_out && !is_device_ptr(arcs_out)) return fail(SDP_ERR_INVALID_ARG, "arcs_out must be a device pointer");
   if (total_out && !is_device_ptr(total_out)) return fail(SDP_ERR_INVALID_ARG, "total_out must be a device pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -415,10 +535,12 @@ int sdp_split_count_arcs(const sdp_split_args* a, int64_t* arcs_out, uint64_t* t
   return SDP_OK;
 }
 
-int sdp_split_backward(const sdp_split_args* fwd, const void* pred, const float* grad_mean,
+int sdp_split_backward(const sdp_split_args* args, const void* pred, const float* grad_mean,
                        float* grad_dist, int64_t* route_hist_out, void* stream) {
-  int rc = check_split(fwd, false);
+  int rc = check_split(args, false);
   if (rc) return rc;
+  const sdp_split_args rd = with_readable_demands(args);
+  const sdp_split_args* fwd = &rd;
   if (!fwd->dist) return fail(SDP_ERR_UNSUPPORTED, "the adjoint is taken with respect to dist: set dist, not coords");
   if (!is_device_ptr(grad_mean)) return fail(SDP_ERR_INVALID_ARG, "grad_mean must be a device pointer");
   if (!is_device_ptr(grad_dist)) return fail(SDP_ERR_INVALID_ARG, "grad_dist must be a device pointer");

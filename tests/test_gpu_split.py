@@ -205,3 +205,40 @@ def test_split_c2_full_size_sampled():
     host_mean = r["cost"].double().mean().item()
     assert abs(float(r["mean"]) - host_mean) <= 1e-12 * host_mean
     assert sdp().status() & (sdp().FLAG_INFEASIBLE | sdp().FLAG_FALLBACK) == 0
+
+
+def test_split_host_demands_chunked_pipeline():
+    """Demands in pinned host memory: copied in 65,536-scenario chunks behind
+    the evaluation (three chunks here, the last one ragged); every output
+    equals the call on device demands, including on a second call that reuses
+    the staging buffers."""
+    rng = np.random.default_rng(21)
+    n, S, Q = 24, 150_001, 60
+    xy = rng.uniform(0, 100, (n + 1, 2)).astype(np.float32)
+    tour = (rng.permutation(n) + 1).astype(np.int32)
+    q = rng.integers(1, 25, size=(S, n)).astype(np.int32)
+    q[7, 3] = 70  # one infeasible scenario
+    t, c, qd = _cuda(tour), _cuda(xy), _cuda(q)
+    qh = torch.from_numpy(q).pin_memory()
+    ref = sdp().split_eval(t, Q, qd, coords=c, preds="u16")
+    for _ in range(2):
+        r = sdp().split_eval(t, Q, qh, coords=c, preds="u16")
+        torch.cuda.synchronize()
+        assert torch.equal(r["cost"], ref["cost"])
+        assert torch.equal(r["pred"], ref["pred"])
+        assert np.isinf(float(r["mean"])) and np.isinf(float(ref["mean"]))
+    sdp().status()
+    sub = slice(0, 2000)
+    orc = oracle.split(tour, Q, q[sub], coords=xy, want_margin=True)
+    check_split(r["cost"][sub], r["pred"][sub], orc, min_checked=0.0)
+    arcs_d, tot_d = sdp().split_count_arcs(t, Q, qd, coords=c)
+    arcs_h, tot_h = sdp().split_count_arcs(t, Q, qh, coords=c)
+    assert torch.equal(arcs_d, arcs_h) and int(tot_d) == int(tot_h)
+
+
+def test_split_rejects_pageable_host_demands():
+    q = torch.ones((4, 3), dtype=torch.int32)
+    tour = torch.tensor([1, 2, 3], dtype=torch.int32, device="cuda")
+    xy = torch.zeros((4, 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        sdp().split_eval(tour, 10, q, coords=xy)
