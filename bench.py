@@ -191,7 +191,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="deque", choices=["deque", "plain"])
+    ap.add_argument("--algo", default="deque", choices=["deque", "stream", "plain"])
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -484,7 +484,8 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
             traffic = tj.get("dram_bytes_per_launch")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": "split_tmem_kernel" if args.algo == "deque" else "split_plain_kernel",
+            "kernel": {"deque": "split_tmem_kernel", "plain": "split_plain_kernel",
+                       "stream": "stream_prep_kernel + split_stream_kernel"}[args.algo],
             "kernel_ms": kern_ms,
             "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_src} hbm_gbs (copy)"}
     sms = torch.cuda.get_device_properties(dev).multi_processor_count

@@ -66,7 +66,10 @@ extern "C" {
 #define SDP_FLAG_FALLBACK 8u       /* a scenario took the per-scenario path */
 
 /* Split algorithms */
-#define SDP_ALGO_AUTO 0   /* DEQUE when supported, else PLAIN */
+#define SDP_ALGO_AUTO 0   /* DEQUE when a demand row fits 512 bytes (uint8
+                             for Q <= 254, else uint16); STREAM for longer
+                             rows it supports; else DEQUE; PLAIN when
+                             neither DEQUE nor STREAM applies */
 #define SDP_ALGO_PLAIN 1  /* one thread per scenario, demands read straight
                              from HBM, every feasible arc (p,i) relaxed in
                              turn: the min-plus column product of Eq. eqdpA */
@@ -74,6 +77,14 @@ extern "C" {
                              memory; the window minimum is kept in a monotone
                              deque (the linear split of Algorithm "2D Kernel
                              for Splitting"); needs Q <= 32767 */
+#define SDP_ALGO_STREAM 3 /* the DEQUE recursion with the gather by customer
+                             done once up front: a pre-pass narrows the
+                             demands (uint8 for Q <= 254, else uint16) into
+                             tour order in the workspace, then one lane per
+                             scenario streams its row from HBM; needs
+                             n <= 2048, Q <= 32767 and 16-byte aligned
+                             demands.  The workspace grows by about
+                             S * (n + 48) bytes (x2 for uint16) */
 
 /* predecessor dtypes */
 #define SDP_PRED_U16 1    /* uint16, requires n < 65535 */
@@ -139,9 +150,10 @@ typedef struct sdp_split_args {
   size_t workspace_bytes;
   int32_t warps_per_cta;  /* DEQUE tuning: 0 = default (demand rows staged in
                              tensor memory when a row fits 512 bytes, 16
-                             warps per SM; else shared memory, 4 warps per
-                             CTA); 1..8 = shared-memory staging with that
-                             many warps per CTA */
+                             warps per SM; else shared memory, up to 4 warps
+                             per CTA as the rows fit); 1..8 = shared-memory
+                             staging with that many warps per CTA (AUTO then
+                             stays on DEQUE).  Ignored by STREAM */
   int32_t ring;           /* DEQUE tuning: deque ring entries per scenario,
                              0 = default, else 8, 16 or 32 */
 } sdp_split_args;

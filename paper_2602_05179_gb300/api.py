@@ -22,7 +22,7 @@ _lib = None
 SDP_OK = 0
 SDP_WARN_INFEASIBLE = 1
 FLAG_INFEASIBLE, FLAG_NEG_INPUT, FLAG_DEVICE_CHECK, FLAG_FALLBACK = 1, 2, 4, 8
-ALGOS = {"auto": 0, "plain": 1, "deque": 2}
+ALGOS = {"auto": 0, "plain": 1, "deque": 2, "stream": 3}
 PRED_DTYPES = {"u16": 1, "i32": 2}
 
 P = ctypes.c_void_p

@@ -143,13 +143,25 @@ struct SplitWs {
   int32_t* pscratch;
   int64_t nslots;
   unsigned long long* hist;
+  unsigned char* qt;   // STREAM: narrowed demands in tour order
+  uint32_t* tflags;    // STREAM: per-tile rows with a demand above Q
   size_t bytes;
 };
 
+// AUTO: DEQUE while a demand row fits the tensor-memory staging (n bytes of
+// uint8 or 2n of uint16 within 512 bytes); longer rows go to STREAM, which
+// keeps 16 DP warps per SM whatever n is (measured at n = 600 / 1000:
+// 0.47 / 0.77 ms against 0.78 / 2.27 ms for DEQUE's shared-memory staging);
+// PLAIN where neither applies.
 int resolve_algo(const sdp_split_args* a) {
   int algo = a->algo;
-  if (algo == SDP_ALGO_AUTO) algo = deque_supported(a->n, a->Q) ? SDP_ALGO_DEQUE : SDP_ALGO_PLAIN;
-  return algo;
+  if (algo != SDP_ALGO_AUTO) return algo;
+  if (!deque_supported(a->n, a->Q)) return SDP_ALGO_PLAIN;
+  const int64_t row_bytes = (int64_t)a->n * (a->Q <= 254 ? 1 : 2);
+  if (row_bytes > 512 && a->warps_per_cta == 0 && stream_supported(a->n, a->Q) &&
+      (reinterpret_cast<uintptr_t>(a->demands) & 15) == 0)
+    return SDP_ALGO_STREAM;
+  return SDP_ALGO_DEQUE;
 }
 
 SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
@@ -162,7 +174,7 @@ SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
   w.prep.Dn = c.take<double>(1);
   w.mean_partial = c.take<double>(kMeanBlocks);
   w.fb_count = c.take<uint32_t>(1);
-  if (algo == SDP_ALGO_DEQUE) {
+  if (algo == SDP_ALGO_DEQUE || algo == SDP_ALGO_STREAM) {
     w.fb_list = c.take<uint32_t>((size_t)a->S);
     w.nslots = a->S < kFallbackSlots ? a->S : kFallbackSlots;
   } else {
@@ -173,6 +185,15 @@ SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
   w.kscratch = c.take<float>((size_t)(n + 1) * w.nslots);
   w.pscratch = backward ? c.take<int32_t>((size_t)n * w.nslots) : nullptr;
   w.hist = backward ? c.take<unsigned long long>(2 * (size_t)n + 1) : nullptr;
+  w.qt = nullptr;
+  w.tflags = nullptr;
+  if (algo == SDP_ALGO_STREAM && !backward && n > 0) {
+    const int64_t rows = (n > 0 && is_host_ptr(a->demands))
+                             ? (a->S < kHostChunkRows ? a->S : kHostChunkRows)
+                             : a->S;
+    w.qt = c.take<unsigned char>(stream_qt_bytes(n, a->Q, rows));
+    w.tflags = c.take<uint32_t>((size_t)((rows + 31) / 32));
+  }
   w.stage[0] = w.stage[1] = nullptr;
   w.stage_rows = 0;
   if (!backward && n > 0 && a->S > 0 && is_host_ptr(a->demands)) {
@@ -254,10 +275,14 @@ int check_split(const sdp_split_args* a, bool need_cost) {
   if (a->Q <= 0) return fail(SDP_ERR_INVALID_ARG, "Q = %d <= 0", a->Q);
   if (a->S < 0) return fail(SDP_ERR_INVALID_ARG, "S = %lld < 0", (long long)a->S);
   if (a->S > (int64_t)0xFFFFFFFFll) return fail(SDP_ERR_UNSUPPORTED, "S above 2^32-1");
-  if (a->algo < SDP_ALGO_AUTO || a->algo > SDP_ALGO_DEQUE)
+  if (a->algo < SDP_ALGO_AUTO || a->algo > SDP_ALGO_STREAM)
     return fail(SDP_ERR_INVALID_ARG, "unknown algo %d", a->algo);
   if (a->algo == SDP_ALGO_DEQUE && !deque_supported(a->n, a->Q))
     return fail(SDP_ERR_UNSUPPORTED, "DEQUE needs 1 <= n <= 65534 and Q <= 32767");
+  if (a->algo == SDP_ALGO_STREAM && !stream_supported(a->n, a->Q))
+    return fail(SDP_ERR_UNSUPPORTED, "STREAM needs 1 <= n <= %d and Q <= 32767", kStreamMaxN);
+  if (a->algo == SDP_ALGO_STREAM && (reinterpret_cast<uintptr_t>(a->demands) & 15))
+    return fail(SDP_ERR_UNSUPPORTED, "STREAM needs 16-byte aligned demands");
   if (need_cost && a->S > 0 && !is_device_ptr(a->cost_out))
     return fail(SDP_ERR_INVALID_ARG, "cost_out must be a device pointer");
   if (a->n > 0 && a->S > 0) {
@@ -301,10 +326,24 @@ int check_ws(void* ws, size_t have, size_t need) {
 // Runs the DEQUE kernel (+ plain fallback) or the PLAIN kernel over all S.
 int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
                    unsigned long long* hist, cudaStream_t st) {
-  const int algo = resolve_algo(a);
+  int algo = resolve_algo(a);
+  if (algo == SDP_ALGO_STREAM && hist) algo = SDP_ALGO_DEQUE;  // the fused adjoint is DEQUE's
   const int sms = num_sms();
   float* cost = hist ? nullptr : a->cost_out;
   void* pred = hist ? nullptr : a->pred_out;
+  if (algo == SDP_ALGO_STREAM) {
+    StreamArgs sa{};
+    sa.n = a->n; sa.Q = a->Q; sa.S = a->S;
+    sa.rec = w.prep.rec; sa.cols = w.prep.cols; sa.Dn = w.prep.Dn;
+    sa.demands = a->demands; sa.qt = w.qt; sa.stride = stream_row_stride(a->n, a->Q);
+    sa.tflags = w.tflags; sa.cost = cost; sa.pred = pred; sa.pred_dtype = a->pred_dtype;
+    sa.fb_list = w.fb_list; sa.fb_count = w.fb_count; sa.status = status;
+    sa.ctas_per_sm = 0;
+    prof_begin(st);  // both kernels of the path: pre-pass + DP
+    const int e = launch_split_stream(sa, st);
+    prof_end(st);
+    if (e) return cuda_fail((cudaError_t)e, "split_stream launch");
+  }
   if (algo == SDP_ALGO_DEQUE) {
     const int ring = a->ring > 0 ? a->ring : 16;
     const int pbytes = pred ? (a->pred_dtype == SDP_PRED_U16 ? 2 : 4) : 0;
@@ -338,12 +377,12 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
   p.cost = cost; p.pred = pred; p.pred_dtype = a->pred_dtype;
   p.kscratch = w.kscratch; p.pscratch = (hist && !pred) ? w.pscratch : nullptr;
   p.nslots = w.nslots; p.hist = hist;
-  p.fb_list = algo == SDP_ALGO_DEQUE ? w.fb_list : nullptr;
+  p.fb_list = algo != SDP_ALGO_PLAIN ? w.fb_list : nullptr;
   p.fb_count = w.fb_count; p.status = status;
   const int grid = (int)((w.nslots + 255) / 256);
-  if (algo != SDP_ALGO_DEQUE) prof_begin(st);
+  if (algo == SDP_ALGO_PLAIN) prof_begin(st);
   launch_split_plain(p, grid, st);
-  if (algo != SDP_ALGO_DEQUE) prof_end(st);
+  if (algo == SDP_ALGO_PLAIN) prof_end(st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "split_plain launch");
   return SDP_OK;

@@ -155,6 +155,32 @@ void launch_batch_fallback(const BatchFallbackArgs& a, cudaStream_t st);
 int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int grid,
                        cudaStream_t st, int* occ_out);
 
+// Split with demands streamed in tour order (SDP_ALGO_STREAM): a pre-pass
+// narrows and permutes the demand rows, then the DP streams them.
+constexpr int kStreamMaxN = 2048;
+struct StreamArgs {
+  int n, Q;
+  int64_t S;
+  const StepRec* rec;       // [n]
+  const uint16_t* cols;     // [n] column (customer - 1) of each tour position
+  const double* Dn;
+  const int32_t* demands;   // [S, n] by customer, 16-byte aligned
+  unsigned char* qt;        // [S, stride] narrowed demands in tour order
+  int64_t stride;           // bytes per qt row (stream_row_stride)
+  uint32_t* tflags;         // [ceil(S/32)] rows with a demand above Q, per tile
+  float* cost;
+  void* pred;               // nullable
+  int pred_dtype;
+  uint32_t* fb_list;        // [S] scenarios recomputed by the plain kernel
+  uint32_t* fb_count;
+  uint32_t* status;
+  int ctas_per_sm;          // CTAs per SM (0 = 1)
+};
+bool stream_supported(int n, int Q);
+int64_t stream_row_stride(int n, int Q);
+size_t stream_qt_bytes(int n, int Q, int64_t S);
+int launch_split_stream(const StreamArgs& a, cudaStream_t st);
+
 // arc counting (capacity-feasible (p,i) pairs)
 void launch_count_arcs(int n, int Q, int64_t S, const StepRec* rec,
                        const int32_t* demands, int64_t* arcs,

@@ -423,8 +423,7 @@ __host__ __device__ constexpr size_t ring_bytes(int ring) { return (size_t)ring 
 // shared memory ([entry][lane] layout), the front and the back's psi in
 // registers.  Prefix loads are kept mod 2^32: every difference taken is a
 // route load below 2^32, so unsigned subtraction is exact.  Each DP step is
-// split into phases so that several scenarios of a lane can be interleaved and
-// share the warp votes that route the extra pops to loops.
+// split into phases so that several scenarios of a lane can be interleaved.
 //  - An empty deque has bpsi = -inf, so "pop the back" is a single compare.
 //  - The front registers are refreshed by the back phase when it empties the
 //    deque (the new entry becomes the front), and start as entry p = 0.
@@ -457,12 +456,6 @@ struct DequeState {
   __device__ __forceinline__ void pop_back() {
     --tail;
     bpsi = tail > head ? __uint_as_float(rpl[((tail - 1) & (RING - 1)) * 32].x) : -CUDART_INF_F;
-  }
-  // first back pop (straight-line); true if this scenario needs more
-  __device__ __forceinline__ bool back1(float psi) {
-    const bool pb = back_needed(psi);
-    if (pb) pop_back();
-    return pb && back_needed(psi);
   }
   __device__ __forceinline__ void back_more(float psi) {
     while (back_needed(psi)) pop_back();
@@ -609,37 +602,22 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
     rn = load_rec(REC_SHARED ? i : min(i, n - 1));
 #pragma unroll
     for (int s = 0; s < NS; ++s) src[s].prefetch(rn);
-    // Back pops depend mostly on the tour (psi differences are dominated by
-    // the a_i), so the lanes of a warp pop together or not at all: one vote
-    // skips the whole phase on the steps without pops.
+    // Each lane pops on its own: warp votes that skipped the pop phases when
+    // no lane needed them were measured slower (1.77 ms against 1.61 ms at
+    // n = 500, S = 10^6) -- a vote waits for the whole warp to reconverge.
     float psi[NS];
-    bool more = false;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       psi[s] = __fadd_rn(st[s].K, r.a);
-      more |= st[s].back_needed(psi[s]);
+      st[s].back_more(psi[s]);
+      st[s].refront(psi[s], i);
     }
-    if (__any_sync(0xffffffffu, more)) {
-      more = false;
-#pragma unroll
-      for (int s = 0; s < NS; ++s) more |= st[s].back1(psi[s]);
-      if (__any_sync(0xffffffffu, more)) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) st[s].back_more(psi[s]);
-      }
-#pragma unroll
-      for (int s = 0; s < NS; ++s) st[s].refront(psi[s], i);
-    }
-    more = false;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       st[s].push(psi[s], i);
       if (CHECK && q[s] > Q && first_inf[s] > (uint32_t)n) first_inf[s] = (uint32_t)i;
-      more |= st[s].template front1<CHECK>(q[s], Q);
-    }
-    if (__any_sync(0xffffffffu, more)) {
-#pragma unroll
-      for (int s = 0; s < NS; ++s) st[s].front_more(Q);
+      st[s].template front1<CHECK>(q[s], Q);
+      st[s].front_more(Q);
     }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -1149,14 +1127,17 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
     c.smem = need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
     return c;
   }
-  c.warps = warps > 0 ? warps : 4;
   size_t off = rec;
   if (hist) {
     off += ((size_t)n * 2 + 15) & ~(size_t)15;
     off += ((size_t)(2 * n + 1) * 4 + 15) & ~(size_t)15;
   }
   const size_t stage = hist ? 0 : stage_bytes_for(pred_bytes, 1);
-  c.smem = off + (size_t)c.warps * ((size_t)32 * c.row_stride + ring_bytes(ring) + stage);
+  const size_t per_warp = (size_t)32 * c.row_stride + ring_bytes(ring) + stage;
+  // default: 4 warps per CTA, fewer when long rows would not fit
+  c.warps = warps > 0 ? warps : 4;
+  while (warps == 0 && c.warps > 1 && off + (size_t)c.warps * per_warp > kMaxSmemPerCta) --c.warps;
+  c.smem = off + (size_t)c.warps * per_warp;
   return c;
 }
 
