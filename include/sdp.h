@@ -269,6 +269,14 @@ void sdp_plan_destroy(sdp_plan* p);
  * end_cost_table != NULL, e(x) = end_cost_table[max(0,x)].  Terminal cost 0.
  * Backward DP C_T = 0, C_t(I) = min(no delivery, delivery), ties to no
  * delivery; value = C_0(I0); policy = decisions along the optimal path. */
+/* Reinsertion kernels */
+#define SDP_REINSERT_AUTO 0  /* WARP (measured faster at T = 60, U = 200) */
+#define SDP_REINSERT_WARP 1  /* one warp per scenario, states across lanes */
+#define SDP_REINSERT_LANE 2  /* one lane per scenario, its cost-to-go in shared
+                                memory; needs U <= 255 (and T <= 768 at
+                                U >= 224); with a policy, its decision bits
+                                take workspace (SMs x 7 x T x ceil((U+1)/32)
+                                x 128 bytes) */
 typedef struct sdp_reinsert_args {
   int32_t T;                  /* 1 <= T; T * W <= 4096 where W = 8 for
                                  U < 256, 16 for U < 512, 32 for U < 1024
@@ -276,7 +284,7 @@ typedef struct sdp_reinsert_args {
                                  SDP_ERR_UNSUPPORTED */
   int32_t U;                  /* 0 <= U <= 1023 */
   int32_t I0;                 /* 0 <= I0 <= U */
-  int32_t algo;               /* 0 = default */
+  int32_t algo;               /* SDP_REINSERT_AUTO / _WARP / _LANE */
   float h, p, unit_cost;
   int64_t S;                  /* scenarios, S >= 0 */
   const float* fixed;         /* [T] per-day routing/insertion cost f_t */

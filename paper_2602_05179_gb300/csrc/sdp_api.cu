@@ -614,9 +614,21 @@ int sdp_split_backward(const sdp_split_args* args, const void* pred, const float
   return SDP_OK;
 }
 
+namespace {
+// the lane kernel keeps its decision bits in the workspace when the policy
+// is wanted
+bool reinsert_uses_lane(const sdp_reinsert_args* a) {
+  return a->algo == SDP_REINSERT_LANE && reinsert_lane_supported(a->T, a->U);
+}
+size_t reinsert_scratch_bytes(const sdp_reinsert_args* a) {
+  return (reinsert_uses_lane(a) && a->policy_out && a->S > 0)
+             ? reinsert_lane_scratch_bytes(a->T, a->U) : 0;
+}
+}  // namespace
+
 size_t sdp_reinsert_workspace_bytes(const sdp_reinsert_args* a) {
-  if (!a || a->S < 0) return 0;
-  return (size_t)kMeanBlocks * sizeof(double);
+  if (!a || a->S < 0 || a->T < 1 || a->U < 0) return 0;
+  return align_up((size_t)kMeanBlocks * sizeof(double), 256) + reinsert_scratch_bytes(a);
 }
 
 int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
@@ -625,6 +637,10 @@ int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
   if (a->U < 0 || a->U > 1023) return fail(SDP_ERR_INVALID_ARG, "U = %d outside 0..1023", a->U);
   if (a->I0 < 0 || a->I0 > a->U) return fail(SDP_ERR_INVALID_ARG, "I0 = %d outside 0..U", a->I0);
   if (a->S < 0) return fail(SDP_ERR_INVALID_ARG, "S < 0");
+  if (a->algo < SDP_REINSERT_AUTO || a->algo > SDP_REINSERT_LANE)
+    return fail(SDP_ERR_INVALID_ARG, "unknown reinsertion algo %d", a->algo);
+  if (a->algo == SDP_REINSERT_LANE && !reinsert_lane_supported(a->T, a->U))
+    return fail(SDP_ERR_UNSUPPORTED, "SDP_REINSERT_LANE needs U <= 255 and its shared memory to fit");
   const int kc = a->U + 1 <= 256 ? (a->U + 1 + 31) / 32 : (a->U + 1 <= 512 ? 16 : 32);
   const int64_t words = (int64_t)a->T * ((kc + 7) & ~7);
   if (words > 4096)
@@ -644,16 +660,21 @@ int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
   }
   if (a->mean_out && !is_device_ptr(a->mean_out)) return fail(SDP_ERR_INVALID_ARG, "mean_out must be a device pointer");
   const size_t need = sdp_reinsert_workspace_bytes(a);
-  int rc = a->mean_out ? check_ws(a->workspace, a->workspace_bytes, need) : SDP_OK;
+  const size_t scratch = reinsert_scratch_bytes(a);
+  int rc = (a->mean_out || scratch) ? check_ws(a->workspace, a->workspace_bytes, need) : SDP_OK;
   if (rc) return rc;
   uint32_t* status;
   rc = status_ptr(&status);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ReinsertArgs r{};
-  r.T = a->T; r.U = a->U; r.I0 = a->I0; r.h = a->h; r.p = a->p; r.c = a->unit_cost;
+  r.algo = a->algo; r.T = a->T; r.U = a->U; r.I0 = a->I0; r.h = a->h; r.p = a->p; r.c = a->unit_cost;
   r.S = a->S; r.fixed = a->fixed; r.table = a->end_cost_table; r.cons = a->consumption;
   r.value = a->value_out; r.policy = a->policy_out; r.value0 = a->value0_out; r.status = status;
+  r.dscratch = scratch ? reinterpret_cast<uint32_t*>(
+                             static_cast<unsigned char*>(a->workspace) +
+                             align_up((size_t)kMeanBlocks * sizeof(double), 256))
+                       : nullptr;
   prof_begin(st);
   int e = launch_reinsert(r, st);
   prof_end(st);

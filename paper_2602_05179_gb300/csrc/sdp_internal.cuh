@@ -201,6 +201,7 @@ void launch_backtrack_hist(int n, int64_t S, const void* pred, int pred_dtype,
 
 // reinsertion
 struct ReinsertArgs {
+  int algo;  // SDP_REINSERT_*
   int T, U, I0;
   float h, p, c;
   int64_t S;
@@ -211,8 +212,14 @@ struct ReinsertArgs {
   uint8_t* policy;
   float* value0;
   uint32_t* status;
+  uint32_t* dscratch;  // lane kernel with a policy: reinsert_lane_scratch_bytes
 };
 int launch_reinsert(const ReinsertArgs& a, cudaStream_t st);
+// one-scenario-per-lane kernel: shapes it runs, its shared memory and the
+// decision scratch it needs when the policy is wanted
+bool reinsert_lane_supported(int T, int U);
+size_t reinsert_lane_smem(int T, int U, bool table);
+size_t reinsert_lane_scratch_bytes(int T, int U);
 
 int num_sms();
 

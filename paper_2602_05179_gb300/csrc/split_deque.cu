@@ -43,6 +43,7 @@
 #include <math_constants.h>
 
 #include "sdp_internal.cuh"
+#include "tmem.cuh"
 
 namespace sdp {
 
@@ -103,45 +104,6 @@ __device__ __forceinline__ int4 ld_v4(const int32_t* p) {
   return v;
 }
 
-// ------------------------------------------------------------------- TMEM
-// Thin wrappers over the tcgen05 instructions used here (all .sync.aligned:
-// every lane of the warp executes them together with the same address).
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(dst_smem);
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-               ::"r"(a), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-               ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tmem_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
-  uint32_t v;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
-  return v;
-}
-// Waits for this thread's outstanding tcgen05.ld; v is tied to the wait so
-// that no use of the loaded value is scheduled before it.
-__device__ __forceinline__ void tmem_wait_ld(uint32_t& v) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(v)::"memory");
-}
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c,
-                                         uint32_t d) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
-               ::"r"(taddr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
 
 // ------------------------------------------------------------ demand sources
 // Shared-memory row of one scenario: demand of customer r.col.

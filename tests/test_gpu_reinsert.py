@@ -1,5 +1,6 @@
-"""GPU parity of the reinsertion kernel against the FP64 oracle (backward DP
-of Algorithm SolveBatchDP), through the C ABI."""
+"""GPU parity of the reinsertion kernels (one scenario per warp, one per
+lane) against the FP64 oracle (backward DP of Algorithm SolveBatchDP) and
+against each other, through the C ABI."""
 import numpy as np
 import pytest
 
@@ -21,14 +22,15 @@ def _cuda(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def test_reinsert_paper_toy():
+@pytest.mark.parametrize("algo", ["warp", "lane"])
+def test_reinsert_paper_toy(algo):
     g = load("inventory_toy.json")
     T, U, I0 = g["T"], g["U"], g["I0"]
     table = np.asarray(g["end_cost_table"], np.float32)
     cons = arr(g["consumption"], np.int32)[None, :]
     fixed = np.zeros(T, np.float32)
     r = sdp().reinsert_eval(T, U, I0, 0.0, 0.0, 1.0, _cuda(fixed), _cuda(cons),
-                            table=_cuda(table), value0=True)
+                            table=_cuda(table), value0=True, algo=algo)
     torch.cuda.synchronize()
     assert float(r["value"][0]) == g["value"]
     assert r["policy"][0].tolist() == g["policy"]
@@ -39,6 +41,7 @@ def test_reinsert_paper_toy():
     assert float(r["mean"]) == g["value"]
 
 
+@pytest.mark.parametrize("algo", ["auto", "lane"])
 @pytest.mark.parametrize("case", [
     # seed, T, U, I0, S, lam, table, unit_cost
     (0, 8, 12, 5, 100, 4.0, False, 0.0),
@@ -47,9 +50,14 @@ def test_reinsert_paper_toy():
     (3, 25, 300, 17, 40, 50.0, False, 0.2),   # KC = 16; consumption > 32 (slow path)
     (4, 60, 0, 0, 33, 3.0, False, 0.0),       # U = 0
     (5, 1, 50, 50, 37, 20.0, False, 1.5),     # T = 1, I0 = U
+    (6, 64, 255, 9, 70, 40.0, False, 0.0),    # the largest lane-kernel shape, d > 32
+    (7, 40, 100, 60, 200, 8.0, False, 0.0),   # 200 = 6 tiles + 8 rows
+    (8, 12, 70, 3, 50, 90.0, True, 0.4),      # table + unit cost, d > U
 ])
-def test_reinsert_cases(case):
+def test_reinsert_cases(case, algo):
     seed, T, U, I0, S, lam, use_table, c = case
+    if algo == "lane" and U > 255:
+        pytest.skip("the one-scenario-per-lane kernel takes U <= 255")
     rng = np.random.default_rng(seed)
     cons = rng.poisson(lam, size=(S, T)).astype(np.int32)
     fixed = rng.uniform(5, 50, T).astype(np.float32)
@@ -58,7 +66,8 @@ def test_reinsert_cases(case):
                         H=None if table is None else table.astype(np.float64),
                         want_value0=True, want_margin=True)
     r = sdp().reinsert_eval(T, U, I0, 1.0, 20.0, c, _cuda(fixed), _cuda(cons),
-                            table=None if table is None else _cuda(table), value0=True)
+                            table=None if table is None else _cuda(table), value0=True,
+                            algo=algo)
     torch.cuda.synchronize()
     check_reinsert(r["value"], r["policy"], o, cons, U, I0)
     v0 = r["value0"].cpu().double().numpy()
@@ -86,3 +95,36 @@ def test_reinsert_c3_full_size_sampled():
     assert checked > 0.9 * len(rows) * spec.T
     host_mean = r["value"].double().mean().item()
     assert abs(float(r["mean"]) - host_mean) <= 1e-12 * host_mean
+
+
+@pytest.mark.parametrize("T,U,lam,table,c", [(60, 200, 8.0, False, 0.0), (33, 100, 30.0, False, 0.3),
+                                             (64, 255, 12.0, True, 0.0), (5, 31, 2.0, False, 0.0)])
+def test_reinsert_lane_and_warp_bit_identical(T, U, lam, table, c):
+    """The two mappings evaluate the same FP32 operations in the same order:
+    values, C_0 tables and policies agree bit for bit."""
+    rng = np.random.default_rng(T * 1000 + U)
+    S = 333
+    cons = rng.poisson(lam, size=(S, T)).astype(np.int32)
+    cons[5, :] = 0
+    cons[6, :] = 400  # every day empties the stock
+    fixed = rng.uniform(5, 50, T).astype(np.float32)
+    tab = _cuda(rng.uniform(0, 30, U + 1).astype(np.float32)) if table else None
+    out = {algo: sdp().reinsert_eval(T, U, U // 2, 1.0, 20.0, c, _cuda(fixed), _cuda(cons),
+                                     table=tab, value0=True, algo=algo)
+           for algo in ("warp", "lane")}
+    torch.cuda.synchronize()
+    for key in ("value", "policy", "value0"):
+        assert torch.equal(out["warp"][key], out["lane"][key]), key
+
+
+def test_reinsert_lane_rejects_unsupported_shapes():
+    fixed = torch.ones(10, dtype=torch.float32, device="cuda")
+    cons = torch.ones((4, 10), dtype=torch.int32, device="cuda")
+    with pytest.raises(sdp().SdpError) as e:
+        sdp().reinsert_eval(10, 256, 0, 1.0, 1.0, 0.0, fixed, cons, algo="lane")
+    assert e.value.code == -5
+    # a shape both kernels take, without a policy (no decision scratch)
+    r = sdp().reinsert_eval(10, 255, 3, 1.0, 1.0, 0.0, fixed, cons, algo="lane", policy=False)
+    w = sdp().reinsert_eval(10, 255, 3, 1.0, 1.0, 0.0, fixed, cons, algo="warp", policy=False)
+    torch.cuda.synchronize()
+    assert torch.equal(r["value"], w["value"])
