@@ -252,7 +252,11 @@ int sdp_plan_run(sdp_plan* p, void* stream);
 /* Device time of the persistent kernel in the most recent sdp_plan_run
  * (waits for it). */
 int sdp_plan_kernel_ms(sdp_plan* p, float* ms);
-/* Launch shape in use and the number of (tour, 32-scenario tile) items. */
+/* Launch shape in use and the number of (tour, 32-scenario tile) items.
+ * warps_per_cta = -1: the streaming kernel (tiles narrowed into tour order by
+ * producer warps; chosen when every dem_off is a multiple of 4, demands are
+ * 16-byte aligned and n_max <= 2048), 0: DEQUE with tensor-memory staging,
+ * k > 0: DEQUE with shared-memory staging and k warps per CTA. */
 int sdp_plan_info(const sdp_plan* p, int32_t* warps_per_cta, int32_t* ring,
                   int32_t* ctas, int64_t* items);
 /* Total feasible arcs of the whole batch (synchronous on `stream`). */

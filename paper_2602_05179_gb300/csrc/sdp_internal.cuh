@@ -177,7 +177,35 @@ struct StreamArgs {
   int ctas_per_sm;          // CTAs per SM (0 = 1)
 };
 bool stream_supported(int n, int Q);
-int64_t stream_row_stride(int n, int Q);
+// batched plan over tour-ordered row slots (one ring of slots per SM)
+struct BatchStreamArgs {
+  int B, Q;
+  int64_t S;
+  const int32_t* n;          // [B]
+  const int64_t* dem_off;    // [B] element offsets, multiples of 4
+  const int64_t* rec_off;    // [B]
+  const int32_t* order;      // [B] tours by decreasing n
+  const StepRec* rec;
+  const double* Dn;          // [B]
+  const int32_t* demands;    // 16-byte aligned
+  float* costs;              // [B*S]
+  unsigned long long* counter;  // group queue (reset by the prep kernel)
+  unsigned long long* fb_list;
+  uint32_t* fb_count;
+  uint32_t* status;
+  unsigned char* qt;         // batch_stream_qt_bytes
+  int64_t stride_max;        // bytes per row slot
+};
+bool batch_stream_supported(int n_max, int Q);
+int64_t batch_stream_stride(int n_max, int Q);
+size_t batch_stream_qt_bytes(int n_max, int Q);
+int launch_split_batch_stream(const BatchStreamArgs& a, cudaStream_t st);
+// bytes per tour-ordered row: n narrowed demands (uint8 for Q <= 254, else
+// uint16), >= 16 bytes of slack for the one-block look-ahead, 32-byte rows
+__host__ __device__ inline int64_t stream_row_stride(int n, int Q) {
+  const int64_t qb = Q <= 254 ? 1 : 2;
+  return ((int64_t)n * qb + 16 + 31) / 32 * 32;
+}
 size_t stream_qt_bytes(int n, int Q, int64_t S);
 int launch_split_stream(const StreamArgs& a, cudaStream_t st);
 

@@ -8,9 +8,12 @@
 // run = [tour prep for every tour (also resets the counter) -> persistent
 // DEQUE kernel over (tour, 32-scenario tile) items -> plain fallback for
 // flagged scenarios -> per-tour FP64 means], captured once in a CUDA graph
-// and replayed.  sdp_plan_autotune times the launch shapes (warps per CTA x
-// deque ring size) and keeps the fastest; choices can be cached in a text
-// file keyed by the device and the plan's shape.
+// and replayed.  The persistent kernel is the streaming one
+// (split_batch_stream_kernel, producer warps narrowing each tile's rows into
+// tour order) when the demand offsets allow bulk copies, else the DEQUE
+// batched kernel.  sdp_plan_autotune times the launch shapes (streaming;
+// DEQUE warps per CTA x deque ring size) and keeps the fastest; choices can
+// be cached in a text file keyed by the device and the plan's shape.
 #include <stdio.h>
 #include <string.h>
 
@@ -40,13 +43,14 @@ struct sdp_plan {
   float* d_kscratch = nullptr;
   int64_t nslots = 0;
   unsigned long long* d_total = nullptr;
+  unsigned char* d_qt = nullptr;  // row slots of the streaming kernel, or NULL
   // caller's arrays
   const int32_t* tours = nullptr;
   const float* coords = nullptr;
   const int32_t* demands = nullptr;
   float* costs = nullptr;
   double* means = nullptr;
-  // launch shape
+  // launch shape; warps == -1: the streaming kernel
   int warps = 4, ring = 16, grid = 0;
   // graph
   cudaGraphExec_t exec = nullptr;
@@ -92,6 +96,13 @@ BatchPrepArgs prep_args(const sdp_plan* p, uint32_t* status) {
 }
 
 int configure(sdp_plan* p, int warps, int ring) {
+  if (warps < 0) {  // streaming kernel: one CTA per SM, ring of 16 entries
+    if (!p->d_qt) return SDP_ERR_UNSUPPORTED;
+    p->warps = -1;
+    p->ring = 16;
+    p->grid = num_sms();
+    return SDP_OK;
+  }
   if (batch_smem(p->n_max, p->Q, warps, ring) > 227 * 1024) return SDP_ERR_UNSUPPORTED;
   BatchKernelArgs k{};
   k.n_max = p->n_max;
@@ -120,7 +131,18 @@ int enqueue(sdp_plan* p, cudaStream_t st, uint32_t* status, bool with_events) {
   // External records become event-record nodes of the captured graph (a plain
   // record inside a capture only orders streams and never fires).
   if (with_events) cudaEventRecordWithFlags(p->ev0, st, cudaEventRecordExternal);
-  int e = launch_split_batch(k, p->warps, p->ring, p->grid, st, nullptr);
+  int e;
+  if (p->warps < 0) {
+    BatchStreamArgs sa{};
+    sa.B = p->B; sa.Q = p->Q; sa.S = p->S;
+    sa.n = p->d_n; sa.dem_off = p->d_dem_off; sa.rec_off = p->d_rec_off; sa.order = p->d_order;
+    sa.rec = p->d_rec; sa.Dn = p->d_Dn; sa.demands = p->demands; sa.costs = p->costs;
+    sa.counter = p->d_counter; sa.fb_list = p->d_fb_list; sa.fb_count = p->d_fb_count;
+    sa.status = status; sa.qt = p->d_qt; sa.stride_max = batch_stream_stride(p->n_max, p->Q);
+    e = launch_split_batch_stream(sa, st);
+  } else {
+    e = launch_split_batch(k, p->warps, p->ring, p->grid, st, nullptr);
+  }
   if (with_events) cudaEventRecordWithFlags(p->ev1, st, cudaEventRecordExternal);
   if (e) return pcuda((cudaError_t)e, "batch kernel");
   BatchFallbackArgs f{};
@@ -169,7 +191,7 @@ void sdp_plan_destroy(sdp_plan* p) {
   cudaFree(p->d_n); cudaFree(p->d_tour_off); cudaFree(p->d_coord_off);
   cudaFree(p->d_dem_off); cudaFree(p->d_rec_off); cudaFree(p->d_order);
   cudaFree(p->d_rec); cudaFree(p->d_Dn); cudaFree(p->d_counter); cudaFree(p->d_fb_count);
-  cudaFree(p->d_fb_list); cudaFree(p->d_kscratch); cudaFree(p->d_total);
+  cudaFree(p->d_fb_list); cudaFree(p->d_kscratch); cudaFree(p->d_total); cudaFree(p->d_qt);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   cudaSetDevice(prev);
@@ -224,6 +246,12 @@ int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out) {
   p->nslots = std::min<int64_t>((int64_t)d->B * d->S, 4096);
   chk(alloc_copy<float>(&p->d_kscratch, nullptr, (size_t)(p->n_max + 1) * p->nslots));
   chk(alloc_copy<unsigned long long>(&p->d_total, nullptr, 1));
+  // the streaming kernel bulk-copies each tile's rows: they must start on
+  // 16 bytes (element offsets that are multiples of 4, an aligned base)
+  bool stream_ok = batch_stream_supported(p->n_max, p->Q) &&
+                   (reinterpret_cast<uintptr_t>(d->demands) & 15) == 0;
+  for (int b = 0; stream_ok && b < d->B; ++b) stream_ok = (d->dem_off_host[b] & 3) == 0;
+  if (stream_ok) chk(alloc_copy<unsigned char>(&p->d_qt, nullptr, batch_stream_qt_bytes(p->n_max, p->Q)));
   if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
   if (e != cudaSuccess) {
@@ -232,7 +260,8 @@ int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out) {
     return e == cudaErrorMemoryAllocation ? pfail(SDP_ERR_OOM, "plan allocation failed")
                                           : pcuda(e, "plan create");
   }
-  int rc = configure(p, 0, 16);  // TMEM staging when the tours fit
+  int rc = configure(p, -1, 16);  // streaming kernel when the plan allows it
+  if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 0, 16);  // TMEM staging when the tours fit
   if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 4, 16);
   if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 1, 8);
   if (rc) {
@@ -305,7 +334,7 @@ int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
           fclose(f);
           drop_graph(p);
           int rc = configure(p, w, r);
-          return rc ? configure(p, 1, 8) : SDP_OK;
+          return rc ? configure(p, 1, 8) : SDP_OK;  // cached shape no longer fits
         }
       }
       fclose(f);
@@ -314,7 +343,7 @@ int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
   uint32_t* status;
   int rc = status_word(&status);
   if (rc) return rc;
-  const int warps_c[] = {0, 1, 2, 4, 8};  // 0 = TMEM staging
+  const int warps_c[] = {-1, 0, 1, 2, 4, 8};  // -1 = streaming, 0 = TMEM staging
   const int ring_c[] = {8, 16};
   float best = 1e30f;
   int bw = p->warps, br = p->ring;
@@ -323,6 +352,7 @@ int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
   cudaEventCreate(&b);
   for (int w : warps_c)
     for (int r : ring_c) {
+      if (w < 0 && r != 16) continue;  // the streaming kernel has one ring size
       if (configure(p, w, r)) continue;
       float tsum = 0.f;
       bool ok = true;

@@ -253,17 +253,32 @@ struct PredOut {
   }
 };
 
+// Tour records (a_i, ce_i) of position k + 1: from shared memory (one tour
+// per launch) or through the read-only path from the plan's records.
+struct SmemRec {
+  const float2* p;
+  __device__ __forceinline__ float2 operator()(int k) const { return p[k]; }
+};
+struct GlobalRec {
+  const StepRec* p;
+  int last;  // n - 1 (the look-ahead past position n reads position n)
+  __device__ __forceinline__ float2 operator()(int k) const {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p + min(k, last)));
+    return make_float2(v.y, v.z);
+  }
+};
+
 // One 32-scenario tile: lane l runs scenario s0 + l over positions 1..n.
-template <typename QT, typename PT, int PACK, bool CHECK, bool PRED>
+template <typename QT, typename PT, int PACK, bool CHECK, bool PRED, typename REC>
 __device__ __forceinline__ void stream_tile(int n, int Q, const unsigned char* qrow,
-                                            uint32_t ring_base, const float2* rec2, int lane,
+                                            uint32_t ring_base, const REC rec2, int lane,
                                             PT* prow, float* K_out, uint32_t* first_inf,
                                             bool* bad) {
   constexpr int E = 16 / (int)sizeof(QT);  // positions per 16-byte block
   const uint32_t Qh = (uint32_t)Q << 16;
   const uint32_t Qc = Qh | 0xFFFFu;
   StreamDP<CHECK> st;
-  float2 r = rec2[0];  // record of the next position, loaded one step ahead
+  float2 r = rec2(0);  // record of the next position, loaded one step ahead
   st.init(ring_base, lane, r.x, n);
   PredOut<PT, PACK> po{PRED ? prow : nullptr, {}};
   const int nblk = n / E;
@@ -274,7 +289,7 @@ __device__ __forceinline__ void stream_tile(int n, int Q, const unsigned char* q
     const int i0 = b * E + 1;
 #pragma unroll
     for (int u = 0; u < E; ++u) {
-      const float2 rn = rec2[i0 + u];
+      const float2 rn = rec2(i0 + u);
       st.step(i0 + u, q_hi<QT>(cur, u), r, Qc, Qh, n);
       r = rn;
       if (PRED) {
@@ -291,7 +306,7 @@ __device__ __forceinline__ void stream_tile(int n, int Q, const unsigned char* q
     const uint32_t x = w == 0 ? cur.x : (w == 1 ? cur.y : (w == 2 ? cur.z : cur.w));
     const uint32_t qh = sizeof(QT) == 1 ? ((x >> (8 * e)) & 0xFFu) << 16
                                         : ((x >> (16 * e)) & 0xFFFFu) << 16;
-    const float2 rn = rec2[i];
+    const float2 rn = rec2(i);
     st.step(i, qh, r, Qc, Qh, n);
     r = rn;
     if (PRED && prow) prow[i - 1] = (PT)st.pred(i);
@@ -302,6 +317,68 @@ __device__ __forceinline__ void stream_tile(int n, int Q, const unsigned char* q
 }
 
 // --------------------------------------------------------------- producers
+// Narrow + permute `rows` staged int32 demand rows (sq, n per row, by
+// customer) into tour-ordered words: word k4 of row r holds positions
+// PER*k4 .. PER*k4 + PER-1 (zero past n), clamped to [0, Q+1]; out row r
+// starts at out + r * pitch (in words).  Work items (row, word) are dealt
+// round-robin to the producer threads, (r, k4) advanced without a division.
+// flag(r) is called for a row with a demand above Q; mn_all tracks the
+// minimum demand (negative demands are reported by the caller).
+template <typename QT, typename FLAG>
+__device__ __forceinline__ void narrow_rows(const int32_t* sq, int rows, int n, int Q,
+                                            const uint16_t* cols, int w4, uint32_t* out,
+                                            int64_t pitch, int ptid, int& mn_all, FLAG flag) {
+  constexpr int PER = 4 / (int)sizeof(QT);  // demands per 32-bit output word
+  const int dr = kProdThreads / w4, dk = kProdThreads % w4;
+  int r = ptid / w4, k4 = ptid % w4;
+  const int items = rows * w4;
+  for (int idx = ptid; idx < items; idx += kProdThreads) {
+    int col[PER];
+    if (sizeof(QT) == 1) {  // the 4 columns of word k4 in one 8-byte load
+      const uint2 c4 = *reinterpret_cast<const uint2*>(cols + 4 * k4);
+      col[0] = (int)(c4.x & 0xFFFFu);
+      col[1] = (int)(c4.x >> 16);
+      col[2 % PER] = (int)(c4.y & 0xFFFFu);
+      col[3 % PER] = (int)(c4.y >> 16);
+    } else {
+      const uint32_t c2 = *reinterpret_cast<const uint32_t*>(cols + 2 * k4);
+      col[0] = (int)(c2 & 0xFFFFu);
+      col[1 % PER] = (int)(c2 >> 16);
+    }
+    const int32_t* srow = sq + r * n;
+    int v[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) v[e] = k4 * PER + e < n ? srow[col[e]] : 0;
+    int mx = v[0], mn = v[0];
+#pragma unroll
+    for (int e = 1; e < PER; ++e) {
+      mx = max(mx, v[e]);
+      mn = min(mn, v[e]);
+    }
+    mn_all = min(mn_all, mn);
+    uint32_t word;
+    if (mx > Q || mn < 0) {  // clamp to [0, Q+1]; flag the row if above Q
+      if (mx > Q) flag(r);
+      word = 0;
+#pragma unroll
+      for (int e = 0; e < PER; ++e)
+        word |= (uint32_t)min(max(v[e], 0), Q + 1) << (e * 8 * (int)sizeof(QT));
+    } else if (sizeof(QT) == 1) {
+      word = __byte_perm(__byte_perm(v[0], v[1], 0x0040), __byte_perm(v[2 % PER], v[3 % PER], 0x0040),
+                         0x5410);
+    } else {
+      word = __byte_perm(v[0], v[1 % PER], 0x5410);
+    }
+    out[(int64_t)r * pitch + k4] = word;
+    r += dr;
+    k4 += dk;
+    if (k4 >= w4) {
+      k4 -= w4;
+      ++r;
+    }
+  }
+}
+
 // Chunks of R rows (R | 32, R * n * 4 <= kStage) walk this CTA's tiles in
 // order through the two stages.
 template <typename QT>
@@ -331,13 +408,7 @@ __device__ __forceinline__ void produce(const StreamArgs& a, int R, int64_t tb, 
     if (nchunks > 0) issue(0, 0);
     if (nchunks > 1) issue(1, 1);
   }
-  constexpr int PER = 4 / (int)sizeof(QT);  // demands per 32-bit output word
-  const int w4 = (int)(a.stride / 4);        // 32-bit words per output row
-  // Work items (row r, output word k4) of a chunk are dealt round-robin to
-  // the producer threads: item ptid + j * kProdThreads, whose (r, k4) is
-  // advanced by (dr, dk) per item without a division.
-  const int r_first = ptid / w4, k_first = ptid % w4;
-  const int dr = kProdThreads / w4, dk = kProdThreads % w4;
+  const int w4 = (int)(a.stride / 4);  // 32-bit words per output row
   int mn_all = 0;
   int64_t g = 0;
   for (; g < nchunks; ++g) {
@@ -355,56 +426,10 @@ __device__ __forceinline__ void produce(const StreamArgs& a, int R, int64_t tb, 
       sq[bulk_elems + ptid] = __ldg(a.demands + row0 * n + bulk_elems + ptid);
     if (prod_sync_or(!ok)) break;  // the producers leave together
     uint32_t* out = reinterpret_cast<uint32_t*>(a.qt + row0 * a.stride);
-    const int items = rows * w4;
-    int r = r_first, k4 = k_first;
-    for (int idx = ptid; idx < items; idx += kProdThreads) {
-      int col[PER];
-      if (sizeof(QT) == 1) {  // the 4 columns of word k4 in one 8-byte load
-        const uint2 c4 = *reinterpret_cast<const uint2*>(cols + 4 * k4);
-        col[0] = (int)(c4.x & 0xFFFFu);
-        col[1] = (int)(c4.x >> 16);
-        col[2 % PER] = (int)(c4.y & 0xFFFFu);
-        col[3 % PER] = (int)(c4.y >> 16);
-      } else {
-        const uint32_t c2 = *reinterpret_cast<const uint32_t*>(cols + 2 * k4);
-        col[0] = (int)(c2 & 0xFFFFu);
-        col[1 % PER] = (int)(c2 >> 16);
-      }
-      const int32_t* srow = sq + r * n;
-      int v[PER];
-#pragma unroll
-      for (int e = 0; e < PER; ++e) v[e] = k4 * PER + e < n ? srow[col[e]] : 0;
-      int mx = v[0], mn = v[0];
-#pragma unroll
-      for (int e = 1; e < PER; ++e) {
-        mx = max(mx, v[e]);
-        mn = min(mn, v[e]);
-      }
-      mn_all = min(mn_all, mn);
-      uint32_t word;
-      if (mx > Q || mn < 0) {  // clamp to [0, Q+1]; flag the row if above Q
-        if (mx > Q) {
-          const int64_t sidx = row0 + r;
-          atomicOr(&a.tflags[sidx >> 5], 1u << (sidx & 31));
-        }
-        word = 0;
-#pragma unroll
-        for (int e = 0; e < PER; ++e)
-          word |= (uint32_t)min(max(v[e], 0), Q + 1) << (e * 8 * (int)sizeof(QT));
-      } else if (sizeof(QT) == 1) {
-        word = __byte_perm(__byte_perm(v[0], v[1], 0x0040), __byte_perm(v[2 % PER], v[3 % PER], 0x0040),
-                           0x5410);
-      } else {
-        word = __byte_perm(v[0], v[1 % PER], 0x5410);
-      }
-      out[(int64_t)r * w4 + k4] = word;
-      r += dr;
-      k4 += dk;
-      if (k4 >= w4) {
-        k4 -= w4;
-        ++r;
-      }
-    }
+    narrow_rows<QT>(sq, rows, n, Q, cols, w4, out, w4, ptid, mn_all, [&](int r) {
+      const int64_t sidx = row0 + r;
+      atomicOr(&a.tflags[sidx >> 5], 1u << (sidx & 31));
+    });
     // publish a finished tile: every producer's rows, then the counter
     const bool tile_done = (g % subs) == subs - 1;
     if (tile_done) __threadfence_block();
@@ -513,10 +538,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_stream_kernel(StreamArgs a,
     uint32_t first_inf;
     bool bad;
     if (tf)
-      stream_tile<QT, PT, PACK, true, PRED>(n, a.Q, qrow, ring_base, rec2, lane, prow, &K,
+      stream_tile<QT, PT, PACK, true, PRED>(n, a.Q, qrow, ring_base, SmemRec{rec2}, lane, prow, &K,
                                             &first_inf, &bad);
     else
-      stream_tile<QT, PT, PACK, false, PRED>(n, a.Q, qrow, ring_base, rec2, lane, prow, &K,
+      stream_tile<QT, PT, PACK, false, PRED>(n, a.Q, qrow, ring_base, SmemRec{rec2}, lane, prow, &K,
                                              &first_inf, &bad);
     bad = bad && live;
     if (live) {
@@ -535,6 +560,234 @@ __global__ void __launch_bounds__(kThreads, 1) split_stream_kernel(StreamArgs a,
     if (any_fb) atomicOr(a.status, SDP_FLAG_FALLBACK);
     if (timed_out) atomicOr(a.status, SDP_FLAG_DEVICE_CHECK);
   }
+}
+
+// ------------------------------------------------------------ batched plan
+// split_batch_stream_kernel: the same producer / DP split over the items of a
+// batched plan.  A group is up to 16 consecutive 32-scenario tiles of one tour;
+// groups are numbered longest tour first and claimed from the plan's counter
+// by each CTA's producers.  The CTA's items (in claim order li = 0, 1, ...)
+// go through a ring of kSlots row slots in a workspace array (32 rows of
+// stride_max bytes each); DP warp w takes items w, w + 16, ...  A producer
+// reuses slot li % kSlots only after DP warp li % 16 has finished the item
+// that held it (per-warp done counters); after the last group it publishes
+// the CTA's item count, which releases the DP warps.
+constexpr int kSlots = 32;
+
+template <typename QT>
+__global__ void __launch_bounds__(kThreads, 1) split_batch_stream_kernel(BatchStreamArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t ready, final_count, done[kDpWarps], abort_flag;
+  __shared__ uint32_t meta_inf[kSlots];
+  __shared__ int32_t meta_b[kSlots];
+  __shared__ int64_t meta_s0[kSlots];
+  __shared__ int64_t group_id;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int Q = a.Q;
+  // shared: two stages | rings (aligned to their size) | columns of a padded row
+  int32_t* const stage_ptr[2] = {reinterpret_cast<int32_t*>(smem),
+                                 reinterpret_cast<int32_t*>(smem + kStage)};
+  const uint32_t s0addr = smem_u32(smem);
+  const uint32_t rings = (s0addr + 2 * kStage + kRingBytes - 1) & ~(kRingBytes - 1);
+  uint16_t* cols = reinterpret_cast<uint16_t*>(smem + (rings + kRingBytes * kDpWarps - s0addr));
+  const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+  if (threadIdx.x == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    mbar_fence_init();
+    ready = 0u;
+    final_count = 0xFFFFFFFFu;
+    abort_flag = 0u;
+  }
+  if (threadIdx.x < kDpWarps) done[threadIdx.x] = 0u;
+  __syncthreads();
+  unsigned char* qslots = a.qt + (int64_t)blockIdx.x * kSlots * 32 * a.stride_max;
+  const int64_t tpt = (a.S + 31) / 32;                 // tiles per tour
+  const int64_t gpt = (tpt + kDpWarps - 1) / kDpWarps;  // groups per tour
+  const int64_t groups = gpt * a.B;
+
+  if (warp >= kDpWarps) {
+    // ------------------------------------------------------------- producers
+    const int ptid = (int)threadIdx.x - kDpWarps * 32;
+    int cur_b = -1, n = 0, R = 32, subs = 1, w4 = 0;
+    uint32_t li = 0;    // items claimed by this CTA so far
+    int64_t gk = 0;     // chunks issued through the stages so far
+    int mn_all = 0;
+    bool failed = false;
+    while (!failed) {
+      if (ptid == 0) group_id = (int64_t)atomicAdd(a.counter, 1ull);
+      prod_sync();
+      const int64_t gid = group_id;
+      if (gid >= groups) break;
+      const int b = a.order[gid / gpt];
+      const int64_t t0 = (gid % gpt) * kDpWarps;
+      const int m = (int)imin64(kDpWarps, tpt - t0);  // items in the group
+      if (b != cur_b) {  // this tour's columns, row geometry and chunking
+        prod_sync();     // every producer is done with the old columns
+        cur_b = b;
+        n = a.n[b];
+        const int row_pos = (int)(stream_row_stride(n, Q) / (int64_t)sizeof(QT));
+        w4 = (int)(stream_row_stride(n, Q) / 4);
+        const StepRec* rec = a.rec + a.rec_off[b];
+        for (int k = ptid; k < row_pos; k += kProdThreads) cols[k] = k < n ? (uint16_t)rec[k].col : 0;
+        R = 32;
+        while ((size_t)R * n * 4 > kStage) R >>= 1;
+        subs = 32 / R;
+        prod_sync();
+      }
+      const int32_t* dem = a.demands + a.dem_off[b];
+      // the group's chunks: item j, sub-chunk q -> rows t0*32 + j*32 + q*R ...
+      const int nch = m * subs;
+      auto crow0 = [&](int c) -> int64_t { return (t0 + c / subs) * 32 + (int64_t)(c % subs) * R; };
+      auto crows = [&](int c) -> int {
+        const int64_t r0 = crow0(c);
+        return r0 >= a.S ? 0 : (int)imin64(R, a.S - r0);
+      };
+      auto issue = [&](int c, int st) {
+        const uint32_t bytes = ((uint32_t)crows(c) * (uint32_t)n * 4u) & ~15u;
+        const uint32_t bar = st ? bar1 : bar0;
+        mbar_arrive_tx(bar, bytes);
+        if (bytes) bulk_g2s(smem_u32(stage_ptr[st]), dem + crow0(c) * n, bytes, bar);
+      };
+      for (int c = 0; c < nch; ++c) {
+        const uint32_t item = li + (uint32_t)(c / subs);
+        const uint32_t slot = item % kSlots;
+        if (c % subs == 0) {
+          // the slot's previous item (item - kSlots) must be finished
+          if (item >= kSlots) {
+            const uint32_t need = (item - kSlots) / kDpWarps + 1;
+            bool ok = true;
+            if (ld_acquire_shared(&done[item % kDpWarps]) < need) {
+              const uint64_t tw = global_ns();
+              while (ld_acquire_shared(&done[item % kDpWarps]) < need) {
+                if (global_ns() - tw > kWaitLimitNs) { ok = false; break; }
+                __nanosleep(256);
+              }
+            }
+            if (prod_sync_or(!ok)) { failed = true; break; }
+          }
+          if (ptid == 0) {
+            meta_inf[slot] = 0u;
+            meta_b[slot] = b;
+            meta_s0[slot] = (t0 + c / subs) * 32;
+          }
+        }
+        // two chunks in flight: issue this one and the next at the group's
+        // start, later ones as their stage frees up
+        if (ptid == 0) {
+          if (c == 0) {
+            issue(0, (int)(gk & 1));
+            if (nch > 1) issue(1, (int)((gk + 1) & 1));
+          }
+        }
+        const int st = (int)(gk & 1);
+        const bool ok = mbar_wait(st ? bar1 : bar0, (uint32_t)(gk >> 1) & 1u);
+        const int rows = crows(c);
+        int32_t* sq = stage_ptr[st];
+        const int elems = rows * n;
+        const int bulk_elems = (int)((((uint32_t)elems * 4u) & ~15u) >> 2);
+        if (ok && ptid < elems - bulk_elems)
+          sq[bulk_elems + ptid] = __ldg(dem + crow0(c) * n + bulk_elems + ptid);
+        if (prod_sync_or(!ok)) { failed = true; break; }
+        const int rbase = (c % subs) * R;  // first row of the chunk within the item
+        uint32_t* out = reinterpret_cast<uint32_t*>(qslots + ((int64_t)slot * 32 + rbase) * a.stride_max);
+        narrow_rows<QT>(sq, rows, n, Q, cols, w4, out, a.stride_max / 4, ptid, mn_all,
+                        [&](int r) { atomicOr(&meta_inf[slot], 1u << (rbase + r)); });
+        const bool item_done = (c % subs) == subs - 1;
+        if (item_done) __threadfence_block();
+        prod_sync();  // also: the stage is free again
+        ++gk;
+        if (ptid == 0) {
+          if (item_done) st_release_shared(&ready, item + 1);
+          if (c + 2 < nch) {
+            fence_proxy_async();
+            issue(c + 2, (int)(gk + 1) & 1);
+          }
+        }
+      }
+      li += (uint32_t)m;
+    }
+    if (failed) {
+      if (ptid == 0) {
+        atomicOr(a.status, SDP_FLAG_DEVICE_CHECK);
+        st_release_shared(&abort_flag, 1u);
+        // let copies still in flight land before shared memory goes
+        mbar_wait((gk & 1) ? bar1 : bar0, (uint32_t)(gk >> 1) & 1u);
+        mbar_wait(((gk + 1) & 1) ? bar1 : bar0, (uint32_t)((gk + 1) >> 1) & 1u);
+      }
+      prod_sync();
+    } else if (ptid == 0) {
+      st_release_shared(&final_count, li);
+    }
+    if (mn_all < 0) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
+    return;
+  }
+
+  // ------------------------------------------------------------------ DP warps
+  const uint32_t ring_base = rings + kRingBytes * (uint32_t)warp;
+  uint32_t any_inf = 0, any_fb = 0;
+  bool timed_out = false;
+  for (uint32_t k = 0;; ++k) {
+    const uint32_t li = (uint32_t)warp + k * kDpWarps;
+    // wait until item li is published or the producers are done
+    bool have = ld_acquire_shared(&ready) > li;
+    if (!have) {
+      const uint64_t tw = global_ns();
+      while (true) {
+        if (ld_acquire_shared(&ready) > li) { have = true; break; }
+        if (ld_acquire_shared(&final_count) <= li) break;
+        if (ld_acquire_shared(&abort_flag) || global_ns() - tw > kWaitLimitNs) {
+          timed_out = !ld_acquire_shared(&abort_flag);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    if (!have) break;
+    const uint32_t slot = li % kSlots;
+    const int b = meta_b[slot];
+    const int64_t s0 = meta_s0[slot];
+    const uint32_t tf = meta_inf[slot];
+    const int n = a.n[b];
+    const int rows = (int)imin64(32, a.S - s0);
+    const bool live = lane < rows;
+    const unsigned char* qrow = qslots + ((int64_t)slot * 32 + (live ? lane : 0)) * a.stride_max;
+    const GlobalRec rec{a.rec + a.rec_off[b], n - 1};
+    float K;
+    uint32_t first_inf;
+    bool bad;
+    if (tf)
+      stream_tile<QT, int32_t, 1, true, false>(n, Q, qrow, ring_base, rec, lane, nullptr, &K,
+                                               &first_inf, &bad);
+    else
+      stream_tile<QT, int32_t, 1, false, false>(n, Q, qrow, ring_base, rec, lane, nullptr, &K,
+                                                &first_inf, &bad);
+    bad = bad && live;
+    if (live) {
+      const int64_t g = (int64_t)b * a.S + s0 + lane;
+      if (bad) {
+        const uint32_t f = atomicAdd(a.fb_count, 1u);
+        a.fb_list[f] = (unsigned long long)g;
+      } else {
+        a.costs[g] = first_inf <= (uint32_t)n ? CUDART_INF_F : (float)((double)K + a.Dn[b]);
+      }
+    }
+    any_inf |= tf;
+    any_fb |= __ballot_sync(0xffffffffu, bad);
+    __syncwarp();
+    if (lane == 0) st_release_shared(&done[warp], k + 1);
+  }
+  if (lane == 0) {
+    if (any_inf) atomicOr(a.status, SDP_FLAG_INFEASIBLE);
+    if (any_fb) atomicOr(a.status, SDP_FLAG_FALLBACK);
+    if (timed_out) atomicOr(a.status, SDP_FLAG_DEVICE_CHECK);
+  }
+}
+
+size_t batch_kernel_smem(int64_t stride_max) {
+  return 2 * (size_t)kStage + kRingBytes * (kDpWarps + 1) + (((size_t)stride_max * 2 + 15) & ~(size_t)15);
 }
 
 size_t kernel_smem(int n, int64_t stride) {
@@ -574,13 +827,25 @@ int launch_pt(const StreamArgs& a, int R, int pack, cudaStream_t st) {
 
 bool stream_supported(int n, int Q) { return n >= 1 && n <= kStreamMaxN && Q >= 1 && Q <= 32767; }
 
-int64_t stream_row_stride(int n, int Q) {
-  const int64_t qb = Q <= 254 ? 1 : 2;
-  return ((int64_t)n * qb + 16 + 31) / 32 * 32;  // >= 16 bytes of slack, 32-byte rows
-}
-
 size_t stream_qt_bytes(int n, int Q, int64_t S) {
   return (size_t)(S * stream_row_stride(n, Q)) + 64;
+}
+
+int64_t batch_stream_stride(int n_max, int Q) { return stream_row_stride(n_max, Q); }
+
+size_t batch_stream_qt_bytes(int n_max, int Q) {
+  return (size_t)num_sms() * kSlots * 32 * (size_t)stream_row_stride(n_max, Q) + 64;
+}
+
+bool batch_stream_supported(int n_max, int Q) { return stream_supported(n_max, Q); }
+
+int launch_split_batch_stream(const BatchStreamArgs& a, cudaStream_t st) {
+  const size_t smem = batch_kernel_smem(a.stride_max);
+  auto k = a.Q <= 254 ? split_batch_stream_kernel<uint8_t> : split_batch_stream_kernel<uint16_t>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  k<<<num_sms(), kThreads, smem, st>>>(a);
+  return (int)cudaGetLastError();
 }
 
 int launch_split_stream(const StreamArgs& a, cudaStream_t st) {

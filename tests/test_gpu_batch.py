@@ -43,7 +43,7 @@ def test_batch_small_vs_oracle_and_eager(Q, qhi, tmp_path):
     B, S = 37, 100
     n, tours, coords, dem = _batch(11 + Q, B, S, Q, 1, 300, qhi)
     plan, keep = _plan(n, tours, coords, dem, Q, S)
-    assert plan.info()["warps_per_cta"] == 0          # default: tensor-memory staging
+    assert plan.info()["warps_per_cta"] == -1         # default: the streaming kernel
     costs, means = plan.run()
     torch.cuda.synchronize()
     c1 = costs.clone()
@@ -64,7 +64,7 @@ def test_batch_small_vs_oracle_and_eager(Q, qhi, tmp_path):
     assert torch.equal(costs, c1)
     cache = str(tmp_path / "tune.txt")
     info = plan.autotune(cache)
-    assert info["warps_per_cta"] in (0, 1, 2, 4, 8) and info["ring"] in (8, 16)
+    assert info["warps_per_cta"] in (-1, 0, 1, 2, 4, 8) and info["ring"] in (8, 16)
     plan.run()
     torch.cuda.synchronize()
     assert torch.equal(costs, c1)
@@ -76,6 +76,40 @@ def test_batch_small_vs_oracle_and_eager(Q, qhi, tmp_path):
     assert plan.kernel_ms() > 0
     assert api().status() & api().FLAG_INFEASIBLE == 0
     plan.close()
+
+
+@pytest.mark.parametrize("Q,qhi", [(150, 40), (600, 90)])
+def test_batch_stream_and_deque_plans_bit_identical(Q, qhi):
+    """The streaming plan kernel and the DEQUE batched kernel (forced by
+    demand blocks that do not start on 16 bytes) give the same bits, on tours
+    shorter and longer than a tensor-memory row, with a ragged last tile
+    (S = 164: 5 tiles + 4 rows, every offset a multiple of 4) and a few
+    demands above Q."""
+    B, S = 29, 164
+    n, tours, coords, dem = _batch(77 + Q, B, S, Q, 1, 1100, qhi)
+    dem[3][7, 0] = Q + 1
+    plan_s, keep_s = _plan(n, tours, coords, dem, Q, S)
+    assert plan_s.info()["warps_per_cta"] == -1
+    # the same blocks, each one element further along: offsets not multiples of 4
+    off = np.zeros(B, np.int64)
+    off[1:] = np.cumsum(n[:-1].astype(np.int64) * S)
+    off = off + np.arange(1, B + 1)
+    buf = torch.zeros(int(off[-1] + n[-1] * S), dtype=torch.int32, device="cuda")
+    for b in range(B):
+        buf[off[b]:off[b] + n[b] * S] = torch.from_numpy(dem[b].reshape(-1)).cuda()
+    t, c, _ = keep_s
+    plan_d = api().SplitPlan(n, t, c, buf, Q, S, dem_off=off)
+    assert plan_d.info()["warps_per_cta"] >= 0
+    cs, ms = plan_s.run()
+    cd, md = plan_d.run()
+    torch.cuda.synchronize()
+    assert torch.equal(cs, cd)
+    assert torch.equal(ms.isinf(), md.isinf())
+    fin = ~ms.isinf()
+    assert torch.equal(ms[fin], md[fin])
+    assert api().status() & api().FLAG_INFEASIBLE
+    plan_s.close()
+    plan_d.close()
 
 
 def test_batch_infeasible_and_fallback():
