@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Bellman arc relaxations/s (Split, n=500, S=1e6 per GPU)"
 UNIT = "arcs/s"
 WORKLOAD = "split_n500_Q200_S1e6_U1-30"
+BATCH_TOURS = 0  # 0: the full 4096-tour batched workload
 
 
 def host_cores() -> int:
@@ -200,9 +201,14 @@ def main():
     ap.add_argument("--preds", default="u16", choices=["u16", "i32", "none"])
     ap.add_argument("--no-operators", action="store_true",
                     help="skip the reinsertion / batched / adjoint operator lines")
+    ap.add_argument("--batch-tours", type=int, default=0,
+                    help="override the batched line's tour count (its first B tours; small "
+                         "cases for ncu captures)")
     ap.add_argument("--scenarios", type=int, default=0,
                     help="override S per GPU (small cases for ncu captures)")
     args = ap.parse_args()
+    global BATCH_TOURS
+    BATCH_TOURS = args.batch_tours
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -437,6 +443,10 @@ def _operator_batch(api, wl, dev, steps, out, p_alu, hbm):
     import torch
     # ---- batched: 4096 tours, n ~ U{20..1000}, S=4096 (persistent + graph)
     bs = wl.BATCH_C4
+    if BATCH_TOURS and BATCH_TOURS != bs.B:
+        import dataclasses
+        bs = dataclasses.replace(bs, B=BATCH_TOURS,
+                                 name=f"batch_B{BATCH_TOURS}_n20-1000_S4096")
     nb = wl.batch_sizes(bs)
     tours, coords = zip(*(wl.batch_tour(bs, b, int(nb[b])) for b in range(bs.B)))
     dem_off = np.zeros(bs.B, np.int64)
