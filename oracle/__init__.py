@@ -64,6 +64,9 @@ def _load():
         lib.oracle_split.argtypes = [ctypes.c_int, P, P, P, i32, i64, P, P, P, P,
                                      P, P, ctypes.c_int]
         lib.oracle_split.restype = ctypes.c_int
+        lib.oracle_split_soft.argtypes = [ctypes.c_int, P, P, P, i32, f64, i64, P, P, P, P,
+                                          P, P, ctypes.c_int]
+        lib.oracle_split_soft.restype = ctypes.c_int
         lib.oracle_split_matrix.argtypes = [ctypes.c_int, P, P, P, i32, P, P, P]
         lib.oracle_split_matrix.restype = ctypes.c_int
         lib.oracle_split_route_counts.argtypes = [ctypes.c_int, i64, P, P, P, P]
@@ -132,6 +135,31 @@ def split(tour, Q, demands, coords=None, dist=None, *, want_pred=True,
                               _ptr(arcs), _ptr(mean), int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle_split failed: {rc}")
+    return {"cost": cost, "pred": pred, "margin": margin, "arcs": arcs,
+            "mean": float(mean[0])}
+
+
+def split_soft(tour, Q, beta, demands, coords=None, dist=None, *, want_pred=True,
+               want_margin=False, nthreads=0):
+    """Soft-capacity Split (every split allowed, beta per unit of route load
+    above Q).  Same arguments and results as split()."""
+    tour = _c(tour, np.int32)
+    n = int(tour.shape[0])
+    demands = _c(demands, np.int32)
+    if n > 0:
+        demands = demands.reshape(-1, n)
+    S = int(demands.shape[0]) if demands.ndim == 2 else 0
+    cost = np.empty(S, np.float64)
+    pred = np.empty((S, n), np.int32) if want_pred else None
+    margin = np.empty((S, n), np.float64) if want_margin else None
+    arcs = np.empty(S, np.int64)
+    mean = np.zeros(1, np.float64)
+    rc = _load().oracle_split_soft(n, _ptr(tour), _ptr(_c(coords, np.float32)),
+                                   _ptr(_c(dist, np.float32)), int(Q), float(beta), S,
+                                   _ptr(demands), _ptr(cost), _ptr(pred), _ptr(margin),
+                                   _ptr(arcs), _ptr(mean), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_split_soft failed: {rc}")
     return {"cost": cost, "pred": pred, "margin": margin, "arcs": arcs,
             "mean": float(mean[0])}
 

@@ -20,6 +20,9 @@
  *       J(0)=0, J(i) = min_{p<i} J(p) + A(p,i), A(p,i) = W(p,i) if the route
  *       sigma_{p+1..i} has load <= Q, +inf otherwise, with
  *       W(p,i) = c(0,s_{p+1}) + sum_{k=p+1}^{i-1} c(s_k,s_{k+1}) + c(s_i,n+1).
+ *   - oracle_split_soft: the same DP with the penalised (soft) capacity of
+ *       the paper's CVRPSD model: every split allowed, beta per unit of route
+ *       load above Q added to W.
  *   - oracle_split_matrix: the same DP through the explicit masked matrix A
  *       (Appendix "Illustrative Matrix Form of DP" for Split), one scenario.
  *   - oracle_split_route_counts: backtrack of the optimal split and the
@@ -178,6 +181,93 @@ int oracle_split(int n, const int32_t* tour, const float* coords,
         cost_out[s] = split_one(n, tour, &c, Q, demands + s * n, J,
                                 pred_out ? pred_out + s * n : NULL,
                                 margin_out ? margin_out + s * n : NULL, &a);
+        if (arcs_out) arcs_out[s] = a;
+      }
+      free(J);
+    }
+  }
+  if (bad) return -2;
+  if (mean_out) {
+    double sum = 0.0;
+    for (int64_t s = 0; s < S; ++s) sum += cost_out[s];
+    *mean_out = S > 0 ? sum / (double)S : 0.0;
+  }
+  return 0;
+}
+
+/* Soft-capacity Split, one scenario (the penalised route load of the
+ * paper's CVRPSD model, Sec. "MILP formulation": a route whose load exceeds
+ * the capacity pays beta per unit of excess, l_k >= load_k - C, l_k >= 0, in
+ * the objective).  Every split is allowed:
+ *   J(0) = 0,  J(i) = min_{0<=p<i} J(p) + W(p,i) + beta * max(0, load(s_{p+1..i}) - Q),
+ * W as in split_one.  Service times add the same constant to every split and
+ * are left out; the fleet is unlimited (reading S6).  Ties: smallest p.
+ * margin as in split_one; *arcs = i(i+1)/2 summed, every pair (p,i). */
+static double split_soft_one(int n, const int32_t* tour, const cost_t* c, int32_t Q,
+                             double beta, const int32_t* q_by_customer, double* J,
+                             int32_t* pred, double* margin, int64_t* arcs) {
+  int64_t narcs = 0;
+  J[0] = 0.0;
+  for (int i = 1; i <= n; ++i) {
+    double best = INFINITY, second = INFINITY;
+    int32_t bestp = -1;
+    int64_t load = 0;
+    double inner = 0.0; /* sum_{k=p+1}^{i-1} c(s_k, s_{k+1}) */
+    const int si = tour[i - 1];
+    const double back = cost_ab(c, si, 0);
+    for (int p = i - 1; p >= 0; --p) {
+      const int sp1 = tour[p];
+      load += q_by_customer[sp1 - 1];
+      ++narcs;
+      if (p < i - 1) inner += cost_ab(c, sp1, tour[p + 1]);
+      const double W = cost_ab(c, 0, sp1) + inner + back;
+      const double excess = load > Q ? (double)(load - Q) : 0.0;
+      const double cand = J[p] + W + beta * excess;
+      if (cand <= best) { /* p runs downwards: "<=" keeps the smallest p */
+        if (bestp >= 0) second = best < second ? best : second;
+        best = cand;
+        bestp = p;
+      } else if (cand < second) {
+        second = cand;
+      }
+    }
+    J[i] = best;
+    if (pred) pred[i - 1] = bestp;
+    if (margin) {
+      if (bestp < 0 || isinf(second)) margin[i - 1] = INFINITY;
+      else margin[i - 1] = (second - best) / fmax(fabs(best), 1e-300);
+    }
+  }
+  if (arcs) *arcs = narcs;
+  return J[n];
+}
+
+/* Soft-capacity Split over S scenarios (arguments as oracle_split, plus the
+ * penalty beta per unit of load above Q). */
+int oracle_split_soft(int n, const int32_t* tour, const float* coords, const float* dist,
+                      int32_t Q, double beta, int64_t S, const int32_t* demands,
+                      double* cost_out, int32_t* pred_out, double* margin_out,
+                      int64_t* arcs_out, double* mean_out, int nthreads) {
+  if (n < 0 || S < 0 || Q <= 0 || !cost_out || !(beta >= 0.0)) return -1;
+  if ((coords == NULL) == (dist == NULL) && n > 0) return -1;
+  cost_t c = {n, coords, dist};
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads) reduction(| : bad)
+#endif
+  {
+    double* J = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+    if (!J) bad = 1;
+    else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+      for (int64_t s = 0; s < S; ++s) {
+        int64_t a = 0;
+        cost_out[s] = split_soft_one(n, tour, &c, Q, beta, demands + s * n, J,
+                                     pred_out ? pred_out + s * n : NULL,
+                                     margin_out ? margin_out + s * n : NULL, &a);
         if (arcs_out) arcs_out[s] = a;
       }
       free(J);

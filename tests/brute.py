@@ -48,6 +48,35 @@ def split_brute(tour, q_by_customer, Q, cost):
     return best, arg
 
 
+def split_soft_brute(tour, q_by_customer, Q, beta, cost):
+    """Min over ALL partitions of the tour into consecutive routes of the
+    summed route costs plus beta per unit of each route's load above Q.
+    Returns (best cost, list of optimal partitions)."""
+    n = len(tour)
+    if n == 0:
+        return 0.0, [[]]
+    best, arg = math.inf, []
+    for mask in range(1 << (n - 1)):
+        cuts = [k for k in range(1, n) if mask >> (k - 1) & 1]
+        bounds = [0] + cuts + [n]
+        total = 0.0
+        routes = []
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            seg = tour[a:b]
+            load = sum(q_by_customer[c - 1] for c in seg)
+            r = cost(0, seg[0]) + cost(seg[-1], 0)
+            for x, y in zip(seg[:-1], seg[1:]):
+                r += cost(x, y)
+            total += r + beta * max(0, load - Q)
+            routes.append(list(seg))
+        tol = 1e-12 * max(1.0, abs(total))
+        if best == math.inf or total < best - tol:
+            best, arg = total, [routes]
+        elif abs(total - best) <= tol:
+            arg.append(routes)
+    return best, arg
+
+
 def reinsert_brute(T, U, I0, h, p, unit_cost, fixed, cons, H=None):
     """Min over all 2^T delivery sequences of the simulated total cost.
     Returns (best value, list of optimal 0/1 sequences)."""
