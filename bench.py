@@ -196,7 +196,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--only", default="", choices=["", "reinsert", "batch", "adjoint"],
+    ap.add_argument("--only", default="", choices=["", "reinsert", "batch", "adjoint", "soft"],
                     help="run one operator line alone (profiling)")
     ap.add_argument("--preds", default="u16", choices=["u16", "i32", "none"])
     ap.add_argument("--no-operators", action="store_true",
@@ -407,8 +407,44 @@ def operators(api, wl, dev, only="", steps=0):
     return _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm)
 
 
+def _operator_soft(api, wl, dev, steps, out, hbm):
+    """Soft-capacity Split: the bench workload (n=500, Q=200, S=10^6,
+    U{1..30}) with 10 per unit of route load above Q; DEQUE (hard window in
+    the deque, expired entries as one running minimum) against PLAIN (every
+    pair (p, i) relaxed), the latter on the first 65,536 scenarios."""
+    import torch
+    spec = wl.SPLIT_C2
+    beta = 10.0
+    tour, xy, _ = wl.split_tour(spec)
+    t = torch.from_numpy(tour).to(dev)
+    c = torch.from_numpy(xy).to(dev)
+    q = wl.split_demands_device(spec, dev)
+    fn = lambda: api.split_eval(t, spec.Q, q, coords=c, preds="u16", algo="deque",
+                                overload_penalty=beta)
+    ms, kms = _timed(fn, steps or 20)
+    n, S = spec.n, spec.S
+    dense = n * (n + 1) // 2 * S  # the pairs (p, i) the penalised recursion ranges over
+    byts = S * n * 4 + S * 4 + S * n * 2
+    sub = 65536
+    qs = q[:sub]
+    fnp = lambda: api.split_eval(t, spec.Q, qs, coords=c, preds="u16", algo="plain",
+                                 overload_penalty=beta)
+    pms, _ = _timed(fnp, 2, warmup=1, events=False)
+    out["split_soft_n500_S1e6_beta10"] = {
+        "value": S / (ms / 1e3), "unit": "scenarios/s", "ms_per_step": ms, "kernel_ms": kms,
+        "dense_relaxations_per_s": dense / (ms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": byts / (kms / 1e3) / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": byts / (kms / 1e3) / 1e9 / hbm},
+        "vs_plain": {"plain_ms_per_65536": pms, "plain_scenarios_per_s": sub / (pms / 1e3),
+                     "speedup_of_deque": (sub / (pms / 1e3)) and (S / (ms / 1e3)) / (sub / (pms / 1e3))}}
+    del q
+    return out
+
+
 def _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm):
     import torch
+    if only == "soft":
+        return _operator_soft(api, wl, dev, steps, out, hbm)
     if only and only != "adjoint":
         return _operator_batch(api, wl, dev, steps, out, p_alu, hbm)
     # ---- adjoint n=300, S=10^5 (fused forward + on-chip backtrack)
@@ -435,6 +471,7 @@ def _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm):
     del q
     if only:
         return out
+    _operator_soft(api, wl, dev, steps, out, hbm)
     return _operator_batch(api, wl, dev, steps, out, p_alu, hbm)
 
 

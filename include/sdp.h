@@ -156,7 +156,25 @@ typedef struct sdp_split_args {
                              stays on DEQUE).  Ignored by STREAM */
   int32_t ring;           /* DEQUE tuning: deque ring entries per scenario,
                              0 = default, else 8, 16 or 32 */
+  int32_t capacity_mode;  /* SDP_CAPACITY_HARD (0, Eq. eqdpA) or
+                             SDP_CAPACITY_SOFT */
+  float overload_penalty; /* SOFT: cost per unit of route load above Q
+                             (finite, >= 0) */
 } sdp_split_args;
+
+/* Capacity modes.  SOFT is the penalised load of the paper's CVRPSD model:
+ * every split is allowed and a route whose load exceeds Q pays
+ * overload_penalty per unit of excess,
+ *     J(i) = min_{0<=p<i} J(p) + W(p,i) + beta * max(0, load(s_{p+1..i}) - Q).
+ * No scenario is infeasible.  PLAIN relaxes all n(n+1)/2 pairs (p,i); DEQUE
+ * (tensor-memory staging, rows of at most 512 bytes) keeps the hard window in
+ * its deque and the entries that left it as one running minimum of
+ * psi(p) - beta L(p) (with equal slopes, an expired entry's penalised cost
+ * is that value plus beta (L(i) - Q)), O(1) per position.  AUTO takes DEQUE
+ * when it applies, else PLAIN; STREAM, plans and the adjoint take HARD only
+ * (SDP_ERR_UNSUPPORTED). */
+#define SDP_CAPACITY_HARD 0
+#define SDP_CAPACITY_SOFT 1
 
 size_t sdp_split_args_size(void);
 size_t sdp_split_workspace_bytes(const sdp_split_args* a);

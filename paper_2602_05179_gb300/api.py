@@ -34,7 +34,8 @@ class SplitArgs(ctypes.Structure):
                 ("cost_out", P), ("pred_out", P), ("pred_dtype", ctypes.c_int32),
                 ("algo", ctypes.c_int32), ("mean_out", P), ("workspace", P),
                 ("workspace_bytes", ctypes.c_size_t), ("warps_per_cta", ctypes.c_int32),
-                ("ring", ctypes.c_int32)]
+                ("ring", ctypes.c_int32), ("capacity_mode", ctypes.c_int32),
+                ("overload_penalty", ctypes.c_float)]
 
 
 class ReinsertArgs(ctypes.Structure):
@@ -168,7 +169,7 @@ def status(clear: bool = True) -> int:
 
 
 def _split_struct(tour, Q, demands, coords, dist, cost, pred, pred_dtype, algo, mean,
-                  warps, ring):
+                  warps, ring, overload_penalty=None):
     n = int(tour.numel())
     S = int(demands.shape[0]) if demands.dim() == 2 else (int(demands.numel()) // n if n else 0)
     a = SplitArgs()
@@ -184,11 +185,14 @@ def _split_struct(tour, Q, demands, coords, dist, cost, pred, pred_dtype, algo, 
     a.mean_out = _dev_ptr(mean, "mean")
     a.warps_per_cta = int(warps)
     a.ring = int(ring)
+    if overload_penalty is not None:  # soft capacity
+        a.capacity_mode = 1
+        a.overload_penalty = float(overload_penalty)
     return a
 
 
 def split_eval(tour, Q, demands, *, coords=None, dist=None, preds=None, algo="auto",
-               mean=True, warps=0, ring=0, stream=None):
+               mean=True, warps=0, ring=0, overload_penalty=None, stream=None):
     """Split of one giant tour over S demand scenarios (Eq. eqdpA).
 
     tour int32 [n] (permutation of 1..n), demands int32 [S, n] by customer id
@@ -196,7 +200,9 @@ def split_eval(tour, Q, demands, *, coords=None, dist=None, preds=None, algo="au
     coords fp32 [n+1, 2] (node 0 = depot) or dist fp32 [n+1, n+1].
     preds: None, "u16" (returned as int16 holding the uint16 bits) or "i32".
     Returns dict(cost fp32 [S], pred [S, n] or None, mean fp64 0-d tensor or
-    None).  Asynchronous on the current stream.
+    None).  overload_penalty (float): soft capacity -- every split allowed,
+    that much per unit of route load above Q.  Asynchronous on the current
+    stream.
     """
     _load()
     dev = tour.device
@@ -210,7 +216,8 @@ def split_eval(tour, Q, demands, *, coords=None, dist=None, preds=None, algo="au
         pred = torch.empty((S, n), dtype=torch.int16 if preds == "u16" else torch.int32,
                            device=dev)
     m = torch.empty((), dtype=torch.float64, device=dev) if mean else None
-    a = _split_struct(tour, Q, demands, coords, dist, cost, pred, pd, algo, m, warps, ring)
+    a = _split_struct(tour, Q, demands, coords, dist, cost, pred, pd, algo, m, warps, ring,
+                      overload_penalty)
     ws = _workspace(_load().sdp_split_workspace_bytes(ctypes.byref(a)), dev)
     a.workspace, a.workspace_bytes = ws.data_ptr(), ws.numel()
     _check(_load().sdp_split_eval(ctypes.byref(a), _stream(stream)))
@@ -286,12 +293,16 @@ class SplitMeanCost(torch.autograd.Function):
         return g, None, None, None, None
 
 
+REINSERT_ALGOS = {"auto": 0, "warp": 1, "lane": 2}
+
+
 def reinsert_eval(T, U, I0, h, p, unit_cost, fixed, consumption, *, table=None,
-                  policy=True, value0=False, mean=True, stream=None):
+                  policy=True, value0=False, mean=True, algo="auto", stream=None):
     """Backward DP of the OU reinsertion over S scenarios (Algorithm
     SolveBatchDP).  fixed fp32 [T] CUDA, consumption int32 [S, T] CUDA, table
-    (optional) fp32 [U+1].  Returns dict(value fp32 [S], policy uint8 [S, T],
-    value0 fp32 [S, U+1], mean fp64 0-d)."""
+    (optional) fp32 [U+1].  algo: "auto", "warp" (one warp per scenario) or
+    "lane" (one lane per scenario).  Returns dict(value fp32 [S], policy
+    uint8 [S, T], value0 fp32 [S, U+1], mean fp64 0-d)."""
     lib = _load()
     dev = consumption.device
     S = int(consumption.shape[0])
@@ -300,7 +311,7 @@ def reinsert_eval(T, U, I0, h, p, unit_cost, fixed, consumption, *, table=None,
     v0 = torch.empty((S, U + 1), dtype=torch.float32, device=dev) if value0 else None
     m = torch.empty((), dtype=torch.float64, device=dev) if mean else None
     a = ReinsertArgs()
-    a.T, a.U, a.I0, a.algo = int(T), int(U), int(I0), 0
+    a.T, a.U, a.I0, a.algo = int(T), int(U), int(I0), REINSERT_ALGOS[algo]
     a.h, a.p, a.unit_cost = float(h), float(p), float(unit_cost)
     a.S = S
     a.fixed = _dev_ptr(fixed, "fixed", torch.float32)

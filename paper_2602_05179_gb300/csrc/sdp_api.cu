@@ -1,5 +1,6 @@
 // sdp_api.cu -- the C ABI of libsdp (include/sdp.h): argument checks,
 // workspace carving, kernel dispatch and the per-device status word.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -153,9 +154,17 @@ struct SplitWs {
 // keeps 16 DP warps per SM whatever n is (measured at n = 600 / 1000:
 // 0.47 / 0.77 ms against 0.78 / 2.27 ms for DEQUE's shared-memory staging);
 // PLAIN where neither applies.
+// soft capacity runs on the TMEM-staged deque kernel only
+bool soft_deque_ok(const sdp_split_args* a) {
+  return deque_supported(a->n, a->Q) && a->warps_per_cta == 0 &&
+         (int64_t)a->n * (a->Q <= 254 ? 1 : 2) <= 512;
+}
+
 int resolve_algo(const sdp_split_args* a) {
   int algo = a->algo;
   if (algo != SDP_ALGO_AUTO) return algo;
+  if (a->capacity_mode == SDP_CAPACITY_SOFT)
+    return soft_deque_ok(a) ? SDP_ALGO_DEQUE : SDP_ALGO_PLAIN;
   if (!deque_supported(a->n, a->Q)) return SDP_ALGO_PLAIN;
   const int64_t row_bytes = (int64_t)a->n * (a->Q <= 254 ? 1 : 2);
   if (row_bytes > 512 && a->warps_per_cta == 0 && stream_supported(a->n, a->Q) &&
@@ -283,6 +292,17 @@ int check_split(const sdp_split_args* a, bool need_cost) {
     return fail(SDP_ERR_UNSUPPORTED, "STREAM needs 1 <= n <= %d and Q <= 32767", kStreamMaxN);
   if (a->algo == SDP_ALGO_STREAM && (reinterpret_cast<uintptr_t>(a->demands) & 15))
     return fail(SDP_ERR_UNSUPPORTED, "STREAM needs 16-byte aligned demands");
+  if (a->capacity_mode != SDP_CAPACITY_HARD && a->capacity_mode != SDP_CAPACITY_SOFT)
+    return fail(SDP_ERR_INVALID_ARG, "unknown capacity_mode %d", a->capacity_mode);
+  if (a->capacity_mode == SDP_CAPACITY_SOFT) {
+    if (!(a->overload_penalty >= 0.f) || a->overload_penalty == INFINITY)
+      return fail(SDP_ERR_INVALID_ARG, "overload_penalty must be finite and >= 0");
+    if (a->algo == SDP_ALGO_STREAM)
+      return fail(SDP_ERR_UNSUPPORTED, "soft capacity runs on PLAIN or DEQUE");
+    if (a->algo == SDP_ALGO_DEQUE && !soft_deque_ok(a))
+      return fail(SDP_ERR_UNSUPPORTED,
+                  "soft-capacity DEQUE needs rows of at most 512 bytes and warps_per_cta = 0");
+  }
   if (need_cost && a->S > 0 && !is_device_ptr(a->cost_out))
     return fail(SDP_ERR_INVALID_ARG, "cost_out must be a device pointer");
   if (a->n > 0 && a->S > 0) {
@@ -366,6 +386,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     d.rec = w.prep.rec; d.cols = w.prep.cols; d.Dn = w.prep.Dn;
     d.demands = a->demands; d.cost = cost; d.pred = pred; d.pred_dtype = a->pred_dtype;
     d.hist = hist; d.fb_list = w.fb_list; d.fb_count = w.fb_count; d.status = status;
+    d.soft = a->capacity_mode == SDP_CAPACITY_SOFT; d.beta = a->overload_penalty;
     prof_begin(st);
     e = launch_split_deque(d, cfg, grid, st);
     prof_end(st);
@@ -379,6 +400,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
   p.nslots = w.nslots; p.hist = hist;
   p.fb_list = algo != SDP_ALGO_PLAIN ? w.fb_list : nullptr;
   p.fb_count = w.fb_count; p.status = status;
+  p.soft = a->capacity_mode == SDP_CAPACITY_SOFT; p.beta = a->overload_penalty;
   const int grid = (int)((w.nslots + 255) / 256);
   if (algo == SDP_ALGO_PLAIN) prof_begin(st);
   launch_split_plain(p, grid, st);
@@ -581,6 +603,8 @@ int sdp_split_backward(const sdp_split_args* args, const void* pred, const float
   const sdp_split_args rd = with_readable_demands(args);
   const sdp_split_args* fwd = &rd;
   if (!fwd->dist) return fail(SDP_ERR_UNSUPPORTED, "the adjoint is taken with respect to dist: set dist, not coords");
+  if (fwd->capacity_mode != SDP_CAPACITY_HARD)
+    return fail(SDP_ERR_UNSUPPORTED, "the adjoint takes the hard capacity only");
   if (!is_device_ptr(grad_mean)) return fail(SDP_ERR_INVALID_ARG, "grad_mean must be a device pointer");
   if (!is_device_ptr(grad_dist)) return fail(SDP_ERR_INVALID_ARG, "grad_dist must be a device pointer");
   if (route_hist_out && !is_device_ptr(route_hist_out))

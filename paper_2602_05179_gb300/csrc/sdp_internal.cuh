@@ -60,6 +60,8 @@ struct SplitPlainArgs {
   const uint32_t* fb_list;   // NULL: all scenarios; else list of scenario ids
   const uint32_t* fb_count;  // [1] number of entries in fb_list
   uint32_t* status;
+  int soft;                  // soft capacity: every p, beta per unit above Q
+  float beta;
 };
 void launch_split_plain(const SplitPlainArgs& a, int grid, cudaStream_t st);
 int plain_grid(int device_sms);
@@ -78,6 +80,8 @@ struct SplitDequeArgs {
   uint32_t* fb_list;    // [S] scenario ids that need the per-scenario path
   uint32_t* fb_count;   // [1]
   uint32_t* status;
+  int soft;             // soft capacity: beta per unit of route load above Q
+  float beta;
 };
 struct DequeConfig {
   int warps;        // warps per CTA

@@ -403,6 +403,9 @@ struct DequeState {
   int head, tail, maxcnt, fidx;
   uint32_t L, fL;     // prefix load through the current position, at the front
   float K, bpsi, fpsi;
+  // soft capacity: the best expired entry, c = psi(p) - beta L(p) and its p
+  float cmin;
+  int cidx;
 
   __device__ __forceinline__ void init(uint2* ring_pl, uint16_t* ring_idx, int lane,
                                        float psi0) {
@@ -413,6 +416,8 @@ struct DequeState {
     K = 0.f;
     bpsi = -CUDART_INF_F;
     fpsi = psi0;  // entry p = 0, pushed by the first step
+    cmin = CUDART_INF_F;
+    cidx = -1;
   }
   __device__ __forceinline__ bool back_needed(float psi) const { return bpsi > psi; }
   __device__ __forceinline__ void pop_back() {
@@ -470,6 +475,42 @@ struct DequeState {
   }
   __device__ __forceinline__ void front_more(int Q) {
     while (front_needed<true>(Q)) pop_front();
+  }
+  // Soft capacity: every entry whose route p+1..i exceeds Q leaves the deque
+  // (the newest one too, when q_i > Q) and joins the expired set, whose
+  // candidate at position i is c(p) + beta (L(i) - Q); the best one is
+  // c(p) = psi(p) - beta L(p) minimal (entries expire in increasing p, so "<"
+  // keeps the smallest p on ties).  An emptied deque has fpsi = +inf.
+  __device__ __forceinline__ void front_soft(int q, int Q, float beta) {
+    L += (uint32_t)q;
+    while (tail > head && L - fL > (uint32_t)Q) {
+      const float c = __fsub_rn(fpsi, __fmul_rn(beta, (float)fL));
+      if (c < cmin) {
+        cmin = c;
+        cidx = fidx;
+      }
+      if (tail - head > 1) {
+        pop_front();
+      } else {
+        ++head;
+        fpsi = CUDART_INF_F;
+        bpsi = -CUDART_INF_F;
+      }
+    }
+  }
+  // min(window minimum, best expired candidate); ties go to the expired
+  // entry (the smaller p)
+  __device__ __forceinline__ float soft_best(int Q, float beta, int* idx) const {
+    float best = fpsi;
+    *idx = fidx;
+    if (cmin < CUDART_INF_F) {
+      const float c2 = __fadd_rn(__fmul_rn(beta, (float)(int)(L - (uint32_t)Q)), cmin);
+      if (c2 <= best) {
+        best = c2;
+        *idx = cidx;
+      }
+    }
+    return best;
   }
 };
 
@@ -535,11 +576,12 @@ __device__ __forceinline__ void flush_stage(const PT* stage, PT* pred_tile, int 
 // UNR: unroll factor of the position loop (1 where registers are tight).
 // PACKED: every prefix load of the tile is below 2^16 (see DequeState).
 template <int NS, typename QT, typename PT, int RING, int OUT, bool CHECK, bool REC_SHARED,
-          typename SRC, int UNR = 2, bool PACKED = false>
+          typename SRC, int UNR = 2, bool PACKED = false, bool SOFT = false>
 __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const StepRec* rec,
                                         uint2* ring_pl, uint16_t* ring_idx, int lane,
                                         PT* stage, PT* pred_tile, int rows, bool check_delta,
-                                        uint32_t* first_inf, bool* bad, float* K_out) {
+                                        uint32_t* first_inf, bool* bad, float* K_out,
+                                        float beta = 0.f) {
   constexpr int kP = stage_pitch<PT>();
   const uint32_t rec_s = REC_SHARED ? (uint32_t)__cvta_generic_to_shared(rec) : 0u;
   auto load_rec = [&](int k) -> StepRec {
@@ -577,12 +619,22 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       st[s].push(psi[s], i);
-      if (CHECK && q[s] > Q && first_inf[s] > (uint32_t)n) first_inf[s] = (uint32_t)i;
-      st[s].template front1<CHECK>(q[s], Q);
-      st[s].front_more(Q);
+      if (SOFT) {
+        st[s].front_soft(q[s], Q, beta);
+      } else {
+        if (CHECK && q[s] > Q && first_inf[s] > (uint32_t)n) first_inf[s] = (uint32_t)i;
+        st[s].template front1<CHECK>(q[s], Q);
+        st[s].front_more(Q);
+      }
     }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
+      if (SOFT) {
+        int idx;
+        st[s].K = __fadd_rn(st[s].soft_best(Q, beta, &idx), r.ce);
+        p[s] = idx;
+        continue;
+      }
       st[s].K = __fadd_rn(st[s].fpsi, r.ce);
       p[s] = (CHECK && (uint32_t)i >= first_inf[s]) ? -1 : st[s].fidx;
       if (OUT == kOutDelta) {
@@ -871,6 +923,89 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
   if (warp == 0) tmem_dealloc(tmem_base, 512);
 }
 
+// Soft-capacity Split with TMEM staging (16 warps per SM, as split_tmem_kernel
+// with XW = 0): every split is allowed and a route pays beta per unit of
+// load above Q.  Demands are staged exactly (no clamp to Q + 1); a row with a
+// demand the staging type cannot hold goes to the plain kernel.
+template <typename QT, typename PT, int OUT>
+__global__ void __launch_bounds__(512, 1) split_tmem_soft_kernel(SplitDequeArgs a, int64_t tiles) {
+  constexpr int RING = 16;
+  constexpr int cols_per_warp = 128;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t tmem_base;
+  const int n = a.n, Q = a.Q;
+  const float beta = a.beta;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  StepRec* rec = reinterpret_cast<StepRec*>(smem);
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
+  const size_t off = ((size_t)n + 1) * sizeof(StepRec);
+  const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, 1>() : 0;
+  const size_t per_warp = ring_bytes(RING) + stage_bytes;
+  unsigned char* wbase = smem + off + per_warp * warp;
+  uint2* ring_pl = reinterpret_cast<uint2*>(wbase);
+  uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + RING * 32);
+  PT* stage = reinterpret_cast<PT*>(ring_idx + RING * 32);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t taddr = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) +
+                         (uint32_t)((warp >> 2) * cols_per_warp);
+  // the largest demand the staging type holds exactly (one below its top, so
+  // the staging's own clamp never collides with a real value)
+  const int cap = (sizeof(QT) == 1 ? 255 : 65535) - 1;
+  const double Dn = *a.Dn;
+  bool neg = false;
+  uint32_t any_fb = 0;
+  const int64_t wstride = (int64_t)gridDim.x * nwarps;
+  for (int64_t tile = (int64_t)blockIdx.x * nwarps + warp; tile < tiles; tile += wstride) {
+    const int64_t s0 = tile * 32;
+    const int rows = (int)imin64(32, a.S - s0);
+    uint32_t first_inf = (uint32_t)n + 1;
+    bool bad = false;
+    float K;
+    PT* pred_tile = a.pred ? reinterpret_cast<PT*>(a.pred) + s0 * n : nullptr;
+    const int prow = pred_tile ? rows : 0;
+    using Src = TmemQ<QT>;
+    const TileFlags tf = ingest_tile_tmem<QT, 16>(a.demands + s0 * n, rows, n, cap, taddr, lane);
+    Src src{taddr, 0u};
+    if (tf.small_loads)
+      dp_rows<1, QT, PT, RING, OUT, false, true, Src, 2, true, true>(
+          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow, false,
+          &first_inf, &bad, &K, beta);
+    else
+      dp_rows<1, QT, PT, RING, OUT, false, true, Src, 2, false, true>(
+          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow, false,
+          &first_inf, &bad, &K, beta);
+    neg |= tf.neg;
+    const bool valid = lane < rows;
+    bad = (bad || ((tf.inf_rows >> lane) & 1u)) && valid;
+    if (valid) {
+      if (bad) {
+        const uint32_t k = atomicAdd(a.fb_count, 1u);
+        a.fb_list[k] = (uint32_t)(s0 + lane);
+      } else if (a.cost) {
+        a.cost[s0 + lane] = (float)((double)K + Dn);
+      }
+    }
+    any_fb |= __ballot_sync(0xffffffffu, bad);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (any_fb) atomicOr(a.status, SDP_FLAG_FALLBACK);
+    if (neg) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(tmem_base, 512);
+}
+
 // Batched Split: a persistent grid pulls work items (tour, 32-scenario tile)
 // from a global counter; items are ordered longest tour first, so the uneven
 // tours finish together.
@@ -1107,6 +1242,23 @@ namespace {
 template <typename QT, typename PT, int RING, int OUT>
 int launch_t(const SplitDequeArgs& a, const DequeConfig& c, int grid, cudaStream_t st,
              int* occ_out) {
+  if (a.soft) {  // soft capacity: TMEM staging only (checked by the caller)
+    if (OUT == kOutDelta || !c.tmem) return (int)cudaErrorInvalidValue;
+    const bool direct = OUT == kOutStream && (a.n & 3) == 0 &&
+                        (reinterpret_cast<uintptr_t>(a.pred) & 15) == 0;
+    auto k = direct ? split_tmem_soft_kernel<QT, PT, kOutDirect>
+                    : split_tmem_soft_kernel<QT, PT, OUT == kOutDelta ? kOutNone : OUT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)c.smem);
+    if (e != cudaSuccess) return (int)e;
+    if (occ_out) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_out, k, 512, c.smem);
+      if (*occ_out > 1) *occ_out = 1;
+      return (int)e;
+    }
+    k<<<grid, 512, c.smem, st>>>(a, (a.S + 31) / 32);
+    return (int)cudaGetLastError();
+  }
   if (OUT != kOutDelta && c.tmem) {
     // predecessors stored 4 per lane when every row segment is aligned
     const bool direct = OUT == kOutStream && (a.n & 3) == 0 &&

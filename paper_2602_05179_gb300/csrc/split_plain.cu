@@ -14,7 +14,9 @@
 
 namespace sdp {
 
-template <typename PT>
+// SOFT: every predecessor p is relaxed (the dense triangle of the penalised
+// recursion), with beta per unit of route load above Q added to W(p,i).
+template <typename PT, bool SOFT>
 __global__ void __launch_bounds__(256) split_plain_kernel(SplitPlainArgs a) {
   const int64_t nslots = a.nslots;
   const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -41,8 +43,9 @@ __global__ void __launch_bounds__(256) split_plain_kernel(SplitPlainArgs a) {
         int qp = __ldg(q + __ldg(&rec[p].col));  // customer at position p+1
         neg |= qp < 0;
         load += max(qp, 0);
-        if (load > Q) break;
-        const float psi = __fadd_rn(Kb[(int64_t)p * nslots], __ldg(&rec[p].a));
+        if (!SOFT && load > Q) break;
+        float psi = __fadd_rn(Kb[(int64_t)p * nslots], __ldg(&rec[p].a));
+        if (SOFT && load > Q) psi = __fadd_rn(psi, __fmul_rn(a.beta, (float)(load - Q)));
         if (psi <= best) {  // p descends: "<=" keeps the smallest p on ties
           best = psi;
           bp = p;
@@ -77,10 +80,14 @@ __global__ void __launch_bounds__(256) split_plain_kernel(SplitPlainArgs a) {
 int plain_grid(int device_sms) { return 2 * device_sms; }
 
 void launch_split_plain(const SplitPlainArgs& a, int grid, cudaStream_t st) {
-  if (a.pred && a.pred_dtype == SDP_PRED_U16)
-    split_plain_kernel<uint16_t><<<grid, 256, 0, st>>>(a);
-  else
-    split_plain_kernel<int32_t><<<grid, 256, 0, st>>>(a);
+  const bool u16 = a.pred && a.pred_dtype == SDP_PRED_U16;
+  if (a.soft) {
+    if (u16) split_plain_kernel<uint16_t, true><<<grid, 256, 0, st>>>(a);
+    else split_plain_kernel<int32_t, true><<<grid, 256, 0, st>>>(a);
+  } else {
+    if (u16) split_plain_kernel<uint16_t, false><<<grid, 256, 0, st>>>(a);
+    else split_plain_kernel<int32_t, false><<<grid, 256, 0, st>>>(a);
+  }
 }
 
 }  // namespace sdp
