@@ -67,6 +67,10 @@ def _load():
         lib.oracle_split_soft.argtypes = [ctypes.c_int, P, P, P, i32, f64, i64, P, P, P, P,
                                           P, P, ctypes.c_int]
         lib.oracle_split_soft.restype = ctypes.c_int
+        lib.oracle_reinsert_routes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, f64,
+                                               f64, f64, ctypes.c_int, P, P, P, i64, P, P, P,
+                                               P, P, P, ctypes.c_int]
+        lib.oracle_reinsert_routes.restype = ctypes.c_int
         lib.oracle_split_matrix.argtypes = [ctypes.c_int, P, P, P, i32, P, P, P]
         lib.oracle_split_matrix.restype = ctypes.c_int
         lib.oracle_split_route_counts.argtypes = [ctypes.c_int, i64, P, P, P, P]
@@ -244,3 +248,31 @@ def reinsert_forward(T, U, I0, h, p, unit_cost, fixed, consumption_row, H=None,
                                         float(unit_cost), _ptr(fixed), _ptr(H),
                                         _ptr(cons), _ptr(A), _ptr(Jh))
     return float(v), Jh, A
+
+
+def reinsert_routes(T, U, I0, h, p, unit_cost, rcost, cap, consumption, *, H=None,
+                    want_value0=False, want_margin=False, nthreads=0):
+    """Reinsertion with K route options per day: rcost float32 [T, K] (insertion
+    cost of route r on day t), cap int32 [S, T, K] (its residual capacity in
+    scenario s; a delivery of U - I rides route r only if cap >= U - I).
+    Returns value [S], policy uint8 [S, T] (0 = no delivery, r + 1 = route r),
+    optional value0 [S, U+1] and margin [S, T, U+1], and mean."""
+    cons = _c(consumption, np.int32).reshape(-1, T)
+    S = int(cons.shape[0])
+    rcost = _c(rcost, np.float32).reshape(T, -1)
+    K = int(rcost.shape[1])
+    cap = _c(cap, np.int32).reshape(S, T, K)
+    H = _c(H, np.float64)
+    value = np.empty(S, np.float64)
+    policy = np.empty((S, T), np.uint8)
+    value0 = np.empty((S, U + 1), np.float64) if want_value0 else None
+    margin = np.empty((S, T, U + 1), np.float64) if want_margin else None
+    mean = np.zeros(1, np.float64)
+    rc = _load().oracle_reinsert_routes(int(T), int(U), int(I0), float(h), float(p),
+                                        float(unit_cost), K, _ptr(rcost), _ptr(cap), _ptr(H),
+                                        S, _ptr(cons), _ptr(value), _ptr(policy),
+                                        _ptr(value0), _ptr(margin), _ptr(mean), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_reinsert_routes failed: {rc}")
+    return {"value": value, "policy": policy, "value0": value0, "margin": margin,
+            "mean": float(mean[0])}

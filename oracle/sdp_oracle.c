@@ -31,6 +31,8 @@
  *   - oracle_reinsert: backward DP of Algorithm "SolveBatchDP" (C[T]=0, then
  *       for t=T-1..0 compare no delivery with delivery up to U, record the
  *       decision) and the backtrack from the initial inventory.
+ *   - oracle_reinsert_routes: the same backward DP with several candidate
+ *       route options per day (an entry of A is a minimum over routes).
  *   - oracle_reinsert_forward: forward min-plus recursion of Eq. eqdp2 with
  *       the transition matrix A^{t}(I,J) of Sec. 2 "Instantiation B" built
  *       explicitly and multiplied with oracle_minplus_matvec.
@@ -501,6 +503,118 @@ int oracle_reinsert(int T, int U, int I0, double h, double p, double unit_cost,
       for (int64_t s = 0; s < S; ++s) {
         value_out[s] = reinsert_one(
             &m, I0, cons + s * T, C, dec,
+            margin_out ? margin_out + (size_t)s * T * W : NULL,
+            policy_out ? policy_out + s * T : NULL,
+            value0_out ? value0_out + (size_t)s * W : NULL);
+      }
+    }
+    free(C);
+    free(dec);
+  }
+  if (bad) return -2;
+  if (mean_out) {
+    double sum = 0.0;
+    for (int64_t s = 0; s < S; ++s) sum += value_out[s];
+    *mean_out = S > 0 ? sum / (double)S : 0.0;
+  }
+  return 0;
+}
+
+/* Reinsertion with route options (Sec. 2 Instantiation B: an entry of the
+ * transition matrix may itself be a minimum over candidate route options,
+ * A(I,J) = min_r A(I,J;r)).  Reading: on day t the delivery q = U - I can
+ * ride any route r in 0..K-1 whose residual capacity cap[s][t][r] is at least
+ * q, at insertion cost rcost[t][r] + unit_cost * q; no route, no delivery.
+ *   nd(I)   = e(I - d_t) + C_{t+1}(max(0, I - d_t))
+ *   dv_r(I) = rcost[t][r] + unit_cost (U-I) + e(U - d_t) + C_{t+1}(max(0, U - d_t))
+ *   C_t(I)  = min(nd, min over feasible r of dv_r), I < U (I = U: nd only)
+ * Decision: 0 = no delivery, r + 1 = route r; ties keep no delivery, then the
+ * smallest r.  marg = gap between the best and the second-best action over
+ * max(|best|, |second|) (+inf with a single action). */
+static double reinsert_routes_one(const inv_t* m, int K, const float* rcost,
+                                  const int32_t* cap, int I0, const int32_t* d, double* C,
+                                  uint8_t* dec, double* marg, uint8_t* policy,
+                                  double* value0) {
+  const int T = m->T, U = m->U, W = U + 1;
+  for (int I = 0; I < W; ++I) C[(size_t)T * W + I] = 0.0;
+  for (int t = T - 1; t >= 0; --t) {
+    const int64_t dt = d[t];
+    const double* Cn = C + (size_t)(t + 1) * W;
+    double* Ct = C + (size_t)t * W;
+    for (int I = 0; I < W; ++I) {
+      const int64_t x0 = (int64_t)I - dt;
+      const double nd = end_cost(m, x0) + Cn[x0 > 0 ? x0 : 0];
+      double best = nd, second = INFINITY;
+      uint8_t a = 0;
+      if (I < U) {
+        const int q = U - I;
+        const int64_t x1 = (int64_t)U - dt;
+        const double e1 = end_cost(m, x1), c1 = Cn[x1 > 0 ? x1 : 0];
+        for (int r = 0; r < K; ++r) {
+          if (cap[(size_t)t * K + r] < q) continue;
+          /* summed in the order of the two-action DP: F(q) + e + C */
+          const double dv = ((double)rcost[(size_t)t * K + r] + m->unit_cost * (double)q) + e1 + c1;
+          if (dv < best) {
+            second = best;
+            best = dv;
+            a = (uint8_t)(r + 1);
+          } else if (dv < second) {
+            second = dv;
+          }
+        }
+      }
+      Ct[I] = best;
+      dec[(size_t)t * W + I] = a;
+      if (marg) {
+        const double den = fmax(fabs(best), fabs(second));
+        marg[(size_t)t * W + I] =
+            isinf(second) ? INFINITY : (den > 0 ? (second - best) / den : 0.0);
+      }
+    }
+  }
+  if (value0)
+    for (int I = 0; I < W; ++I) value0[I] = C[I];
+  if (policy) {
+    int64_t I = I0;
+    for (int t = 0; t < T; ++t) {
+      const uint8_t a = dec[(size_t)t * W + I];
+      policy[t] = a;
+      const int64_t x = (a ? U : I) - d[t];
+      I = x > 0 ? x : 0;
+    }
+  }
+  return C[I0];
+}
+
+/* Route-option reinsertion over S scenarios: rcost[T*K] shared, cap[S*T*K]
+ * per scenario (cap[(s*T + t)*K + r]); other arguments as oracle_reinsert;
+ * policy_out holds 0 (no delivery) or r + 1. */
+int oracle_reinsert_routes(int T, int U, int I0, double h, double p, double unit_cost, int K,
+                           const float* rcost, const int32_t* cap, const double* H,
+                           int64_t S, const int32_t* cons, double* value_out,
+                           uint8_t* policy_out, double* value0_out, double* margin_out,
+                           double* mean_out, int nthreads) {
+  if (T <= 0 || U < 0 || I0 < 0 || I0 > U || S < 0 || K < 0 || K > 254 || !value_out ||
+      (K > 0 && (!rcost || !cap)))
+    return -1;
+  inv_t m = {T, U, h, p, unit_cost, NULL, H};
+  const size_t W = (size_t)U + 1;
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads) reduction(| : bad)
+#endif
+  {
+    double* C = (double*)malloc(sizeof(double) * (size_t)(T + 1) * W);
+    uint8_t* dec = (uint8_t*)malloc((size_t)T * W);
+    if (!C || !dec) bad = 1;
+    else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+      for (int64_t s = 0; s < S; ++s) {
+        value_out[s] = reinsert_routes_one(
+            &m, K, rcost, cap + (size_t)s * T * K, I0, cons + s * T, C, dec,
             margin_out ? margin_out + (size_t)s * T * W : NULL,
             policy_out ? policy_out + s * T : NULL,
             value0_out ? value0_out + (size_t)s * W : NULL);

@@ -99,3 +99,34 @@ def reinsert_brute(T, U, I0, h, p, unit_cost, fixed, cons, H=None):
         elif abs(total - best) <= tol:
             arg.append(seq)
     return best, arg
+
+
+def reinsert_routes_brute(T, U, I0, h, p, unit_cost, rcost, cap, cons, H=None):
+    """Min over every sequence of daily actions (0 = no delivery, r + 1 =
+    deliver up to U on route r, allowed when cap[t][r] >= U - I) of the
+    simulated total cost.  Returns (best value, list of optimal sequences)."""
+    K = len(rcost[0]) if T else 0
+    best, arg = math.inf, []
+    for seq in itertools.product(range(K + 1), repeat=T):
+        I, total, ok = I0, 0.0, True
+        for t, a in enumerate(seq):
+            q = (U - I) if a else 0
+            if a:
+                if q == 0 or cap[t][a - 1] < q:
+                    ok = False
+                    break
+                total += float(rcost[t][a - 1]) + unit_cost * q
+            x = I + q - int(cons[t])
+            if H is not None:
+                total += H[max(0, x)]
+            else:
+                total += h * x if x >= 0 else p * (-x)
+            I = max(0, x)
+        if not ok:
+            continue
+        tol = 1e-12 * max(1.0, abs(total))
+        if best == math.inf or total < best - tol:
+            best, arg = total, [seq]
+        elif abs(total - best) <= tol:
+            arg.append(seq)
+    return best, arg
