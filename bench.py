@@ -402,6 +402,22 @@ def operators(api, wl, dev, only="", steps=0):
                                  "frac": 2 * rel / (kms / 1e3) / p_alu,
                                  "peak_source": f"{sms} SMs x 128 lanes x sm_max_mhz ({src})"}}
     del cons
+    # ---- reinsertion with K = 4 route options per day (ALU bound)
+    rr = wl.REINSERT_ROUTES
+    cons = wl.reinsert_consumption_device(rr, dev)
+    cap = wl.reinsert_route_caps_device(rr, dev)
+    rcost = torch.from_numpy(wl.reinsert_route_costs(rr)).to(dev)
+    K = int(rcost.shape[1])
+    fn = lambda: api.reinsert_eval(rr.T, rr.U, rr.I0, rr.h, rr.p, rr.unit_cost, None, cons,
+                                   route_cost=rcost, route_cap=cap)
+    ms, kms = _timed(fn, steps or 10)
+    rel = float(rr.U + 1) * rr.T * (K + 1) * rr.S  # (state, action) pairs: no delivery + K routes
+    out[rr.name] = {"value": rel / (ms / 1e3), "unit": "relaxations/s",
+                    "scenarios_per_s": rr.S / (ms / 1e3), "ms_per_step": ms, "kernel_ms": kms,
+                    "roofline": {"bound": "alu", "achieved": 2 * rel / (kms / 1e3),
+                                 "peak": p_alu, "unit": "ops/s",
+                                 "frac": 2 * rel / (kms / 1e3) / p_alu}}
+    del cons, cap
     if only:
         return out
     return _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm)

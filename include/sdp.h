@@ -318,6 +318,20 @@ typedef struct sdp_reinsert_args {
   double* mean_out;           /* [1] or NULL */
   void* workspace;
   size_t workspace_bytes;
+  int32_t n_routes;           /* K route options per day (0: the single route
+                                 of `fixed`).  With K > 0 a delivery of
+                                 q = U - I on day t may ride route r only if
+                                 route_cap[(s*T + t)*K + r] >= q, at cost
+                                 route_cost[t*K + r] (+ unit_cost * q); the
+                                 cheapest such route is taken, none -> no
+                                 delivery (an entry of the transition matrix
+                                 is a minimum over route options, Sec. 2
+                                 "Instantiation B").  policy_out then holds
+                                 0 (no delivery) or r + 1; `fixed` is not
+                                 read.  Needs U <= 255, K <= 64, no
+                                 end_cost_table, algo AUTO or WARP. */
+  const float* route_cost;    /* [T*K] */
+  const int32_t* route_cap;   /* [S*T*K] */
 } sdp_reinsert_args;
 
 size_t sdp_reinsert_args_size(void);

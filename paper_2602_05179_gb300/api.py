@@ -44,7 +44,8 @@ class ReinsertArgs(ctypes.Structure):
                 ("unit_cost", ctypes.c_float), ("S", ctypes.c_int64), ("fixed", P),
                 ("end_cost_table", P), ("consumption", P), ("value_out", P),
                 ("policy_out", P), ("value0_out", P), ("mean_out", P), ("workspace", P),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("n_routes", ctypes.c_int32),
+                ("route_cost", P), ("route_cap", P)]
 
 
 class BatchDesc(ctypes.Structure):
@@ -297,12 +298,15 @@ REINSERT_ALGOS = {"auto": 0, "warp": 1, "lane": 2}
 
 
 def reinsert_eval(T, U, I0, h, p, unit_cost, fixed, consumption, *, table=None,
-                  policy=True, value0=False, mean=True, algo="auto", stream=None):
+                  policy=True, value0=False, mean=True, algo="auto", route_cost=None,
+                  route_cap=None, stream=None):
     """Backward DP of the OU reinsertion over S scenarios (Algorithm
     SolveBatchDP).  fixed fp32 [T] CUDA, consumption int32 [S, T] CUDA, table
     (optional) fp32 [U+1].  algo: "auto", "warp" (one warp per scenario) or
-    "lane" (one lane per scenario).  Returns dict(value fp32 [S], policy
-    uint8 [S, T], value0 fp32 [S, U+1], mean fp64 0-d)."""
+    "lane" (one lane per scenario).  Route options: route_cost fp32 CUDA
+    [T, K] and route_cap int32 CUDA [S, T, K] (fixed may then be None); the
+    policy holds 0 (no delivery) or r + 1.  Returns dict(value fp32 [S],
+    policy uint8 [S, T], value0 fp32 [S, U+1], mean fp64 0-d)."""
     lib = _load()
     dev = consumption.device
     S = int(consumption.shape[0])
@@ -315,6 +319,10 @@ def reinsert_eval(T, U, I0, h, p, unit_cost, fixed, consumption, *, table=None,
     a.h, a.p, a.unit_cost = float(h), float(p), float(unit_cost)
     a.S = S
     a.fixed = _dev_ptr(fixed, "fixed", torch.float32)
+    if route_cost is not None:
+        a.n_routes = int(route_cost.shape[-1])
+        a.route_cost = _dev_ptr(route_cost, "route_cost", torch.float32)
+        a.route_cap = _dev_ptr(route_cap, "route_cap", torch.int32)
     a.end_cost_table = _dev_ptr(table, "table", torch.float32)
     a.consumption = _dev_ptr(consumption, "consumption", torch.int32)
     a.value_out = _dev_ptr(val, "value")

@@ -175,6 +175,159 @@ __global__ void __launch_bounds__(512) reinsert_kernel(ReinsertArgs a) {
   if (__any_sync(0xffffffffu, neg) && lane == 0) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
 }
 
+// ----------------------------------------------------------- route options
+// reinsert_routes_kernel: the warp-per-scenario recursion with K candidate
+// routes per day (an entry of the transition matrix is a minimum over route
+// options).  Route r on day t costs rcost[t][r] and carries the delivery
+// q = U - I only if its residual capacity in this scenario, cap[s][t][r], is
+// at least q.  Per state the delivery costs F(q) = min over those routes, so
+//     dv(I) = F(U - I) + G_{t+1}(U - d_t) (+ c (U - I)),
+// +inf when no route fits; the two-action recursion of reinsert_kernel is
+// the case K = 1 with a roomy route (same FP32 operations, same bits).
+// Decisions stay ballot bits (deliver or not); the backtrack recomputes the
+// route that carried each delivery (the cheapest feasible one, the first on
+// ties) and writes r + 1 to the policy.  Linear end-of-day costs only.
+template <int KC, bool UNIT>
+__global__ void __launch_bounds__(512) reinsert_routes_kernel(ReinsertArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int T = a.T, U = a.U, K = a.n_routes;
+  constexpr int GW = kPad + 32 * KC;
+  constexpr int BS = bits_stride(KC);
+  // CTA-shared route costs [T*K]; per warp: G double buffer, decision words,
+  // consumption and route capacities of the current scenario
+  float* rcost_sm = reinterpret_cast<float*>(smem);
+  const size_t rc_bytes = ((size_t)T * K * 4 + 15) & ~(size_t)15;
+  const size_t per_warp =
+      (((size_t)2 * GW + (size_t)T * BS + (size_t)T + (size_t)T * K) * 4 + 15) & ~(size_t)15;
+  unsigned char* wb = smem + rc_bytes + per_warp * warp;
+  float* G0 = reinterpret_cast<float*>(wb);
+  float* G1 = G0 + GW;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(G1 + GW);
+  int32_t* dsm = reinterpret_cast<int32_t*>(bits + (size_t)T * BS);
+  int32_t* capsm = dsm + T;
+  for (int i = threadIdx.x; i < T * K; i += blockDim.x) rcost_sm[i] = __ldg(a.route_cost + i);
+  __syncthreads();
+
+  const float h = a.h, p = a.p, c = a.c;
+  float eI[KC], cq[KC];
+  int qk[KC];  // q = U - I of each slot
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    const int I = lane + 32 * k;
+    eI[k] = __fmul_rn(h, (float)min(I, U));
+    cq[k] = UNIT ? __fmul_rn(c, (float)(U - I)) : 0.f;
+    qk[k] = U - I;
+  }
+  const float eneg = __fmul_rn(p, (float)(kPad - lane));
+  bool neg = false;
+
+  for (int64_t s = (int64_t)blockIdx.x * nw + warp; s < a.S; s += (int64_t)gridDim.x * nw) {
+    for (int t = lane; t < T; t += 32) {
+      const int d = a.cons[s * T + t];
+      neg |= d < 0;
+      dsm[t] = max(d, 0);
+    }
+    const int32_t* capg = a.route_cap + s * (int64_t)T * K;
+    for (int i = lane; i < T * K; i += 32) capsm[i] = __ldg(capg + i);
+    float* Gn = G0;
+    float* Gc = G1;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) Gn[kPad + lane + 32 * k] = eI[k];
+    Gn[lane] = eneg;
+    __syncwarp();
+    float C[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) C[k] = 0.f;
+
+    for (int t = T - 1; t >= 0; --t) {
+      const int d = dsm[t];
+      const float C0n = Gn[kPad];  // C_{t+1}(0) (e(0) = 0)
+      auto gat = [&](int j) -> float {
+        if (j >= -kPad) return Gn[j + kPad];
+        return __fadd_rn(C0n, __fmul_rn(p, (float)(-j)));
+      };
+      const float gUd = gat(U - d);
+      // cheapest route that holds q (q >= 1; +inf when none does)
+      float fb[KC];
+#pragma unroll
+      for (int k = 0; k < KC; ++k) fb[k] = CUDART_INF_F;
+      for (int r = 0; r < K; ++r) {
+        const float fr = rcost_sm[t * K + r];
+        const int cr = capsm[t * K + r];
+#pragma unroll
+        for (int k = 0; k < KC; ++k)
+          if (qk[k] >= 1 && cr >= qk[k]) fb[k] = fminf(fb[k], fr);
+      }
+      uint32_t w[KC];
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const float nd = d <= kPad ? Gn[lane + 32 * k - d + kPad] : gat(lane + 32 * k - d);
+        float dv = __fadd_rn(fb[k], gUd);
+        if (UNIT) dv = __fadd_rn(dv, cq[k]);
+        const bool dec = dv < nd;
+        C[k] = dec ? dv : nd;
+        w[k] = __ballot_sync(0xffffffffu, dec);
+      }
+      if (lane == 0) {
+        uint32_t* row = bits + t * BS;
+#pragma unroll
+        for (int k0 = 0; k0 < BS; k0 += 4) {
+          uint4 v;
+          v.x = k0 + 0 < KC ? w[k0 + 0] : 0u;
+          v.y = k0 + 1 < KC ? w[k0 + 1] : 0u;
+          v.z = k0 + 2 < KC ? w[k0 + 2] : 0u;
+          v.w = k0 + 3 < KC ? w[k0 + 3] : 0u;
+          *reinterpret_cast<uint4*>(row + k0) = v;
+        }
+      }
+      const float C0 = __shfl_sync(0xffffffffu, C[0], 0);
+#pragma unroll
+      for (int k = 0; k < KC; ++k) Gc[kPad + lane + 32 * k] = __fadd_rn(eI[k], C[k]);
+      Gc[lane] = __fadd_rn(C0, eneg);
+      __syncwarp();
+      float* tmp = Gn; Gn = Gc; Gc = tmp;
+    }
+
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k == (a.I0 >> 5)) v = C[k];
+    v = __shfl_sync(0xffffffffu, v, a.I0 & 31);
+    if (lane == 0) a.value[s] = v;
+    if (a.value0) {
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const int I = lane + 32 * k;
+        if (I <= U) a.value0[s * (U + 1) + I] = C[k];
+      }
+    }
+    if (a.policy) {
+      int I = a.I0;
+      for (int t = 0; t < T; ++t) {
+        const uint32_t wd = bits[t * BS + (I >> 5)];
+        const bool dec = (wd >> (I & 31)) & 1u;
+        int route = 0;
+        if (dec) {  // the cheapest route that holds U - I, the first on ties
+          const int q = U - I;
+          float best = CUDART_INF_F;
+          for (int r = 0; r < K; ++r) {
+            const float fr = rcost_sm[t * K + r];
+            if (capsm[t * K + r] >= q && fr < best) {
+              best = fr;
+              route = r + 1;
+            }
+          }
+        }
+        if ((t & 31) == lane) a.policy[s * T + t] = (uint8_t)route;
+        I = max((dec ? U : I) - dsm[t], 0);
+      }
+    }
+    __syncwarp();
+  }
+  if (__any_sync(0xffffffffu, neg) && lane == 0) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
+}
+
 // ------------------------------------------------------- one scenario per lane
 // reinsert_lane_kernel: the same recursion with lane l of a warp running
 // scenario s0 + l on its own (no ballots, shuffles or per-warp decision
@@ -376,6 +529,43 @@ int launch_lane_kc(const ReinsertArgs& a, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
+template <int KC, bool UNIT>
+int launch_routes_kc(const ReinsertArgs& a, cudaStream_t st) {
+  auto k = reinsert_routes_kernel<KC, UNIT>;
+  constexpr int GW = kPad + 32 * KC;
+  const size_t per_warp = (((size_t)2 * GW + (size_t)a.T * bits_stride(KC) + (size_t)a.T +
+                            (size_t)a.T * a.n_routes) * 4 + 15) & ~(size_t)15;
+  const size_t rc_bytes = ((size_t)a.T * a.n_routes * 4 + 15) & ~(size_t)15;
+  int warps = 16;
+  while (warps > 1 && rc_bytes + per_warp * warps > 100 * 1024) warps >>= 1;
+  const size_t smem = rc_bytes + per_warp * warps;
+  if (smem > 200 * 1024) return (int)cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, warps * 32, smem);
+  if (e != cudaSuccess) return (int)e;
+  if (occ < 1) occ = 1;
+  const int64_t need = (a.S + warps - 1) / warps;
+  const int grid = (int)imin64(need, (int64_t)occ * num_sms());
+  if (grid > 0) k<<<grid, warps * 32, smem, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <bool UNIT>
+int routes_by_kc(const ReinsertArgs& a, cudaStream_t st) {
+  switch ((a.U + 1 + 31) / 32) {
+    case 1: return launch_routes_kc<1, UNIT>(a, st);
+    case 2: return launch_routes_kc<2, UNIT>(a, st);
+    case 3: return launch_routes_kc<3, UNIT>(a, st);
+    case 4: return launch_routes_kc<4, UNIT>(a, st);
+    case 5: return launch_routes_kc<5, UNIT>(a, st);
+    case 6: return launch_routes_kc<6, UNIT>(a, st);
+    case 7: return launch_routes_kc<7, UNIT>(a, st);
+    default: return launch_routes_kc<8, UNIT>(a, st);
+  }
+}
+
 template <bool TABLE, bool UNIT>
 int lane_by_kc(const ReinsertArgs& a, cudaStream_t st) {
   switch ((a.U + 1 + 31) / 32) {
@@ -410,6 +600,10 @@ size_t reinsert_lane_scratch_bytes(int T, int U) {
 int launch_reinsert(const ReinsertArgs& a, cudaStream_t st) {
   if (a.S <= 0) return 0;
   const bool unit = a.c != 0.f;
+  if (a.n_routes > 0) {  // route options: U <= 255, linear end costs (checked by the caller)
+    if (a.U > 255 || a.table) return (int)cudaErrorInvalidValue;
+    return unit ? routes_by_kc<true>(a, st) : routes_by_kc<false>(a, st);
+  }
   // AUTO takes WARP: at T = 60, U = 200, S = 10^6 it runs in 6.16 ms against
   // 7.09 ms for LANE (fewer instructions, but only 7 warps per SM to hide them)
   if (a.algo == SDP_REINSERT_LANE && reinsert_lane_supported(a.T, a.U)) {

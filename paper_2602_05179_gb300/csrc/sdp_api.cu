@@ -642,7 +642,7 @@ namespace {
 // the lane kernel keeps its decision bits in the workspace when the policy
 // is wanted
 bool reinsert_uses_lane(const sdp_reinsert_args* a) {
-  return a->algo == SDP_REINSERT_LANE && reinsert_lane_supported(a->T, a->U);
+  return a->algo == SDP_REINSERT_LANE && a->n_routes == 0 && reinsert_lane_supported(a->T, a->U);
 }
 size_t reinsert_scratch_bytes(const sdp_reinsert_args* a) {
   return (reinsert_uses_lane(a) && a->policy_out && a->S > 0)
@@ -663,6 +663,16 @@ int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
   if (a->S < 0) return fail(SDP_ERR_INVALID_ARG, "S < 0");
   if (a->algo < SDP_REINSERT_AUTO || a->algo > SDP_REINSERT_LANE)
     return fail(SDP_ERR_INVALID_ARG, "unknown reinsertion algo %d", a->algo);
+  if (a->n_routes < 0 || a->n_routes > 64)
+    return fail(SDP_ERR_INVALID_ARG, "n_routes = %d outside 0..64", a->n_routes);
+  if (a->n_routes > 0) {
+    if (a->U > 255) return fail(SDP_ERR_UNSUPPORTED, "route options need U <= 255");
+    if (a->end_cost_table) return fail(SDP_ERR_UNSUPPORTED, "route options take linear end costs");
+    if (a->algo == SDP_REINSERT_LANE)
+      return fail(SDP_ERR_UNSUPPORTED, "route options run on the warp kernel");
+    if (a->S > 0 && (!is_device_ptr(a->route_cost) || !is_device_ptr(a->route_cap)))
+      return fail(SDP_ERR_INVALID_ARG, "route_cost / route_cap must be device pointers");
+  }
   if (a->algo == SDP_REINSERT_LANE && !reinsert_lane_supported(a->T, a->U))
     return fail(SDP_ERR_UNSUPPORTED, "SDP_REINSERT_LANE needs U <= 255 and its shared memory to fit");
   const int kc = a->U + 1 <= 256 ? (a->U + 1 + 31) / 32 : (a->U + 1 <= 512 ? 16 : 32);
@@ -672,7 +682,8 @@ int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
                 "T = %d with U = %d needs %lld decision words per scenario, above 4096 "
                 "(decision bits are kept on chip)", a->T, a->U, (long long)words);
   if (a->S > 0) {
-    if (!is_device_ptr(a->fixed)) return fail(SDP_ERR_INVALID_ARG, "fixed must be a device pointer");
+    if (a->n_routes == 0 && !is_device_ptr(a->fixed))
+      return fail(SDP_ERR_INVALID_ARG, "fixed must be a device pointer");
     if (!is_device_ptr(a->consumption)) return fail(SDP_ERR_INVALID_ARG, "consumption must be a device pointer");
     if (!is_device_ptr(a->value_out)) return fail(SDP_ERR_INVALID_ARG, "value_out must be a device pointer");
     if (a->end_cost_table && !is_device_ptr(a->end_cost_table))
@@ -692,7 +703,8 @@ int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ReinsertArgs r{};
-  r.algo = a->algo; r.T = a->T; r.U = a->U; r.I0 = a->I0; r.h = a->h; r.p = a->p; r.c = a->unit_cost;
+  r.algo = a->algo; r.T = a->T; r.U = a->U; r.I0 = a->I0;
+  r.n_routes = a->n_routes; r.route_cost = a->route_cost; r.route_cap = a->route_cap; r.h = a->h; r.p = a->p; r.c = a->unit_cost;
   r.S = a->S; r.fixed = a->fixed; r.table = a->end_cost_table; r.cons = a->consumption;
   r.value = a->value_out; r.policy = a->policy_out; r.value0 = a->value0_out; r.status = status;
   r.dscratch = scratch ? reinterpret_cast<uint32_t*>(

@@ -245,6 +245,9 @@ struct ReinsertArgs {
   float* value0;
   uint32_t* status;
   uint32_t* dscratch;  // lane kernel with a policy: reinsert_lane_scratch_bytes
+  int n_routes;               // route options per day (0: the two-action DP)
+  const float* route_cost;    // [T * n_routes]
+  const int32_t* route_cap;   // [S * T * n_routes]
 };
 int launch_reinsert(const ReinsertArgs& a, cudaStream_t st);
 // one-scenario-per-lane kernel: shapes it runs, its shared memory and the

@@ -45,6 +45,7 @@ MASK = (1 << 64) - 1
 
 # stream ids (fixed: changing them changes every workload)
 ST_COORDS, ST_TOUR, ST_DEMAND, ST_CONS, ST_FIXED, ST_NB = 1, 2, 3, 4, 5, 6
+ST_RCOST, ST_RCAP = 7, 8  # route-option reinsertion: route costs, residual capacities
 ST_BATCH0 = 64  # batched tours: stream = ST_BATCH0 + 4*b + {0: coords, 1: tour, 2: demand}
 
 _U64 = np.uint64
@@ -218,6 +219,28 @@ def reinsert_consumption(spec: ReinsertSpec, s0: int = 0, s1: int | None = None)
     return q.reshape(s1 - s0, spec.T)
 
 
+# Route-option reinsertion: the reinsertion workload with K routes per day;
+# route r on day t costs U[5,50) fp32 (shared by the scenarios) and has a
+# residual capacity U{0..250} in each scenario (it carries a refill of q only
+# if the capacity is at least q).
+REINSERT_ROUTES = ReinsertSpec("reinsert_routes_T60_U200_K4_S1e6", 60, 200, 100, 1.0, 20.0, 0.0,
+                               1_000_000, 5, 8.0, 5.0, 50.0)
+ROUTES_K, ROUTES_CAP_LO, ROUTES_CAP_HI = 4, 0, 250
+
+
+def reinsert_route_costs(spec: ReinsertSpec, K: int = ROUTES_K) -> np.ndarray:
+    return uniform_f32(spec.seed, ST_RCOST, 0, spec.T * K, spec.f_lo, spec.f_hi).reshape(spec.T, K)
+
+
+def reinsert_route_caps(spec: ReinsertSpec, s0: int = 0, s1: int | None = None,
+                        K: int = ROUTES_K) -> np.ndarray:
+    """Rows s0..s1-1 of the residual capacities [S, T, K] (int32)."""
+    s1 = spec.S if s1 is None else s1
+    c = uniform_int(spec.seed, ST_RCAP, s0 * spec.T * K, (s1 - s0) * spec.T * K,
+                    ROUTES_CAP_LO, ROUTES_CAP_HI)
+    return c.reshape(s1 - s0, spec.T, K)
+
+
 @dataclass
 class BatchSpec:
     name: str
@@ -321,3 +344,12 @@ def batch_demands_device(spec: BatchSpec, b: int, n_b: int, out):
     """Fill out (int32 [S, n_b] CUDA view) with tour b's demands."""
     st = ST_BATCH0 + 4 * b + 2
     return device_poisson_clip(out, spec.seed, st, 0, spec.lam, 1, spec.Q)
+
+
+def reinsert_route_caps_device(spec: ReinsertSpec, device="cuda", s0=0, s1=None,
+                               K: int = ROUTES_K):
+    import torch
+    s1 = spec.S if s1 is None else s1
+    out = torch.empty((s1 - s0, spec.T, K), dtype=torch.int32, device=device)
+    return device_uniform_int(out, spec.seed, ST_RCAP, s0 * spec.T * K, ROUTES_CAP_LO,
+                              ROUTES_CAP_HI)
