@@ -1,0 +1,128 @@
+"""GPU parity of the Split adjoint (d mean / d dist = scenario-averaged
+arc-usage counts of the optimal splits) through the C ABI and the autograd
+binding: the fused forward + on-chip backtrack and the backtrack of stored
+predecessors against the FP64 oracle's backtrack."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_05179_gb300 import workloads as wl
+from tests.gpu_util import check_split, preds_to_i64
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def sdp():
+    from paper_2602_05179_gb300 import api
+    return api
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _case(seed, n, S, Q, lam):
+    spec = wl.SplitSpec(f"adj{seed}", n, Q, S, seed, "poisson", lam=lam, lo=1, hi=Q,
+                        dist_mode=True)
+    tour, _, dist = wl.split_tour(spec)
+    return tour, dist, wl.split_demands(spec)
+
+
+def _gpu_preds(tour, Q, q, dist):
+    r = sdp().split_eval(_cuda(tour), Q, _cuda(q), dist=_cuda(dist), preds="i32")
+    torch.cuda.synchronize()
+    return r, preds_to_i64(r["pred"]).astype(np.int32)
+
+
+@pytest.mark.parametrize("case", [(1, 17, 70, 40, 8.0), (2, 60, 500, 80, 10.0),
+                                  (3, 300, 2000, 120, 10.0), (4, 513, 96, 150, 12.0)])
+@pytest.mark.parametrize("mode", ["fused", "pred_u16", "pred_i32"])
+def test_adjoint_vs_oracle_backtrack(case, mode):
+    seed, n, S, Q, lam = case
+    tour, dist, q = _case(seed, n, S, Q, lam)
+    orc = oracle.split(tour, Q, q, dist=dist, want_margin=True)
+    r, gp = _gpu_preds(tour, Q, q, dist)
+    check_split(r["cost"], r["pred"], orc, min_checked=0.0)   # preds = oracle's where unique
+    # the oracle's backtrack of the GPU's own optimal splits: exact counts
+    g_ref = oracle.split_mean_grad(tour, gp)
+    start, end, skipped = oracle.split_route_counts(gp)
+    assert skipped == 0
+    gm = torch.tensor(1.0, device="cuda")
+    if mode == "fused":
+        g, hist = sdp().split_backward(_cuda(tour), Q, _cuda(q), _cuda(dist), gm, want_hist=True)
+    else:
+        dt = mode.split("_")[1]
+        p = sdp().split_eval(_cuda(tour), Q, _cuda(q), dist=_cuda(dist), preds=dt)["pred"]
+        g, hist = sdp().split_backward(_cuda(tour), Q, _cuda(q), _cuda(dist), gm, pred=p,
+                                       pred_dtype=dt, want_hist=True)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy()
+    np.testing.assert_array_equal(h[:n], start)
+    np.testing.assert_array_equal(h[n:], end)
+    np.testing.assert_allclose(g.cpu().double().numpy(), g_ref, rtol=1e-6, atol=1e-9)
+    # against the oracle's own splits: only scenarios with a near-tie may differ
+    g_orc = oracle.split_mean_grad(tour, orc["pred"])
+    differ = int((gp != orc["pred"]).any(axis=1).sum())
+    assert np.abs(g.cpu().double().numpy() - g_orc).max() <= 2.0 * differ / S + 1e-6
+
+
+def test_adjoint_autograd_and_upstream_gradient():
+    """SplitMeanCost.backward (stored predecessors and fused) equals the C ABI
+    call, scaled by the upstream gradient."""
+    tour, dist, q = _case(5, 80, 400, 60, 9.0)
+    d = _cuda(dist).requires_grad_(True)
+    t, qd = _cuda(tour), _cuda(q)
+    for keep in (False, True):
+        d.grad = None
+        m = sdp().SplitMeanCost.apply(d, t, qd, 60, keep)
+        (3.0 * m).backward()
+        g, _ = sdp().split_backward(t, 60, qd, d.detach(), torch.tensor(3.0, device="cuda"))
+        torch.cuda.synchronize()
+        assert torch.equal(d.grad, g)
+    r = sdp().split_eval(t, 60, qd, dist=d.detach())
+    assert abs(float(m) - float(r["mean"])) == 0.0
+
+
+def test_adjoint_skips_infeasible_scenarios():
+    """A scenario with a demand above Q is infeasible (cost +inf) and
+    contributes no arc; the others are averaged over all S."""
+    tour, dist, q = _case(6, 40, 200, 50, 8.0)
+    q[3, 5] = 51
+    q[77, 0] = 999
+    r, gp = _gpu_preds(tour, 50, q, dist)
+    assert np.isinf(r["cost"][3].item()) and np.isinf(r["cost"][77].item())
+    g_ref = oracle.split_mean_grad(tour, gp)
+    g, hist = sdp().split_backward(_cuda(tour), 50, _cuda(q), _cuda(dist),
+                                   torch.tensor(1.0, device="cuda"), want_hist=True)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(g.cpu().double().numpy(), g_ref, rtol=1e-6, atol=1e-9)
+    start, _, skipped = oracle.split_route_counts(gp)
+    assert skipped == 2
+    np.testing.assert_array_equal(hist.cpu().numpy()[:40], start)
+    sdp().status()
+
+
+def test_adjoint_full_size():
+    """n=300, S=10^5 (the adjoint workload) with the fused kernel: counts equal
+    the oracle's backtrack of the GPU's predecessors."""
+    spec = wl.ADJOINT_C5
+    tour, _, dist = wl.split_tour(spec)
+    qd = wl.split_demands_device(spec)
+    t, dd = _cuda(tour), _cuda(dist)
+    r = sdp().split_eval(t, spec.Q, qd, dist=dd, preds="i32")
+    g, hist = sdp().split_backward(t, spec.Q, qd, dd, torch.tensor(1.0, device="cuda"),
+                                   want_hist=True)
+    torch.cuda.synchronize()
+    gp = preds_to_i64(r["pred"]).astype(np.int32)
+    start, end, skipped = oracle.split_route_counts(gp)
+    assert skipped == 0
+    h = hist.cpu().numpy()
+    np.testing.assert_array_equal(h[:spec.n], start)
+    np.testing.assert_array_equal(h[spec.n:], end)
+    np.testing.assert_allclose(g.cpu().double().numpy(), oracle.split_mean_grad(tour, gp),
+                               rtol=1e-6, atol=1e-9)
+    rows = np.random.default_rng(4).choice(spec.S, 500, replace=False)
+    qs = np.concatenate([wl.split_demands(spec, int(s), int(s) + 1) for s in rows])
+    orc = oracle.split(tour, spec.Q, qs, dist=dist, want_margin=True)
+    check_split(r["cost"], r["pred"], orc, rows=rows, margin=1e-5, min_checked=0.5)
