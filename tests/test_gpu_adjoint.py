@@ -81,7 +81,7 @@ def test_adjoint_autograd_and_upstream_gradient():
         torch.cuda.synchronize()
         assert torch.equal(d.grad, g)
     r = sdp().split_eval(t, 60, qd, dist=d.detach())
-    assert abs(float(m) - float(r["mean"])) == 0.0
+    assert abs(float(m.detach()) - float(r["mean"])) == 0.0
 
 
 def test_adjoint_skips_infeasible_scenarios():
