@@ -243,10 +243,11 @@ def split_count_arcs(tour, Q, demands, *, coords=None, dist=None, per_scenario=T
 
 
 def split_backward(tour, Q, demands, dist, grad_mean, *, pred=None, pred_dtype=None,
-                   algo="auto", want_hist=False, stream=None):
+                   algo="auto", want_hist=False, warps=0, ring=0, stream=None):
     """d mean / d dist (fp32 [n+1, n+1]) as scenario-averaged arc-usage counts
     times grad_mean (device fp32 scalar).  pred: the forward's predecessors,
-    or None to recompute them in the fused forward + backtrack kernel."""
+    or None to recompute them in the fused forward + backtrack kernel
+    (warps / ring: the DEQUE launch shape, as in split_eval; 0 = default)."""
     _load()
     dev = tour.device
     n = int(tour.numel())
@@ -255,7 +256,7 @@ def split_backward(tour, Q, demands, dist, grad_mean, *, pred=None, pred_dtype=N
     pd = 0
     if pred is not None:
         pd = PRED_DTYPES[pred_dtype or ("u16" if pred.element_size() == 2 else "i32")]
-    a = _split_struct(tour, Q, demands, None, dist, None, None, pd, algo, None, 0, 0)
+    a = _split_struct(tour, Q, demands, None, dist, None, None, pd, algo, None, warps, ring)
     ws = _workspace(_load().sdp_split_backward_workspace_bytes(ctypes.byref(a)), dev)
     a.workspace, a.workspace_bytes = ws.data_ptr(), ws.numel()
     gm = grad_mean.reshape(()).to(device=dev, dtype=torch.float32).contiguous()

@@ -146,6 +146,7 @@ struct SplitWs {
   unsigned long long* hist;
   unsigned char* qt;   // STREAM: narrowed demands in tour order
   uint32_t* tflags;    // STREAM: per-tile rows with a demand above Q
+  uint32_t* dscratch;  // fused adjoint on TMEM: i - pred(i) per [word][lane]
   size_t bytes;
 };
 
@@ -158,6 +159,17 @@ struct SplitWs {
 bool soft_deque_ok(const sdp_split_args* a) {
   return deque_supported(a->n, a->Q) && a->warps_per_cta == 0 &&
          (int64_t)a->n * (a->Q <= 254 ? 1 : 2) <= 512;
+}
+
+int resolve_algo(const sdp_split_args* a);
+
+// The fused adjoint runs on the TMEM-staged deque kernel when the forward
+// would take DEQUE in its default shape and a row fits the tensor memory.
+int adjoint_tmem_warps(const sdp_split_args* a) {
+  const int algo = resolve_algo(a);
+  if (algo != SDP_ALGO_DEQUE && algo != SDP_ALGO_STREAM) return 0;
+  if (a->warps_per_cta != 0 || (a->ring != 0 && a->ring != 16)) return 0;
+  return split_tmem_adj_warps(a->n, a->Q, a->S, num_sms());
 }
 
 int resolve_algo(const sdp_split_args* a) {
@@ -194,6 +206,9 @@ SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
   w.kscratch = c.take<float>((size_t)(n + 1) * w.nslots);
   w.pscratch = backward ? c.take<int32_t>((size_t)n * w.nslots) : nullptr;
   w.hist = backward ? c.take<unsigned long long>(2 * (size_t)n + 1) : nullptr;
+  w.dscratch = (backward && adjoint_tmem_warps(a) > 0)
+                   ? c.take<uint32_t>(split_tmem_adj_scratch_bytes(n, a->Q, num_sms()) / 4)
+                   : nullptr;
   w.qt = nullptr;
   w.tflags = nullptr;
   if (algo == SDP_ALGO_STREAM && !backward && n > 0) {
@@ -364,7 +379,18 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     prof_end(st);
     if (e) return cuda_fail((cudaError_t)e, "split_stream launch");
   }
-  if (algo == SDP_ALGO_DEQUE) {
+  const int adj_warps = (hist && w.dscratch) ? adjoint_tmem_warps(a) : 0;
+  if (algo == SDP_ALGO_DEQUE && adj_warps > 0) {
+    SplitDequeArgs d{};
+    d.n = a->n; d.Q = a->Q; d.S = a->S;
+    d.rec = w.prep.rec; d.cols = w.prep.cols; d.Dn = w.prep.Dn;
+    d.demands = a->demands; d.cost = nullptr; d.pred = nullptr; d.pred_dtype = a->pred_dtype;
+    d.hist = hist; d.fb_list = w.fb_list; d.fb_count = w.fb_count; d.status = status;
+    prof_begin(st);
+    const int e = launch_split_tmem_adj(d, adj_warps, w.dscratch, sms, st);
+    prof_end(st);
+    if (e) return cuda_fail((cudaError_t)e, "split_tmem_adj launch");
+  } else if (algo == SDP_ALGO_DEQUE) {
     const int ring = a->ring > 0 ? a->ring : 16;
     const int pbytes = pred ? (a->pred_dtype == SDP_PRED_U16 ? 2 : 4) : 0;
     // warps_per_cta == 0: default launch, TMEM staging when the rows fit;

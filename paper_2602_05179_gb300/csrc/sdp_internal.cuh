@@ -102,6 +102,13 @@ int launch_split_deque(const SplitDequeArgs& a, const DequeConfig& c, int grid,
                        cudaStream_t st);
 int deque_max_ctas_per_sm(const DequeConfig& c, bool hist, int pred_dtype,
                           bool want_pred, int* out);
+// Fused adjoint with TMEM-staged rows: warps per CTA (16..24) for S
+// scenarios on sms SMs, 0 where rows do not fit; the [word][lane] delta
+// scratch it needs; the launch (hist set, cost / pred unused).
+int split_tmem_adj_warps(int n, int Q, int64_t S, int sms);
+size_t split_tmem_adj_scratch_bytes(int n, int Q, int sms);
+int launch_split_tmem_adj(const SplitDequeArgs& a, int warps, uint32_t* dscratch, int sms,
+                          cudaStream_t st);
 
 // batched Split (persistent work queue over (tour, 32-scenario tile) items)
 struct BatchKernelArgs {

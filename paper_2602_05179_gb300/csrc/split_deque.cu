@@ -376,6 +376,8 @@ constexpr int kOutStream = 1;  // predecessors streamed out every 16 positions
 constexpr int kOutDirect = 3;  // predecessors stored by each lane, 4 per store
 constexpr int kOutDelta = 2;   // i - pred(i) written in place over the consumed
                                // demand byte (on-chip backtrack of the adjoint)
+constexpr int kOutDeltaLane = 4;  // i - pred(i) packed 4 (uint8) or 2 (uint16)
+                                  // per word into a [word][lane] scratch
 
 // Ring bytes per warp: RING entries x 32 lanes of an 8-byte (psi, prefix load)
 // pair and a 16-bit position.
@@ -581,8 +583,10 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
                                         uint2* ring_pl, uint16_t* ring_idx, int lane,
                                         PT* stage, PT* pred_tile, int rows, bool check_delta,
                                         uint32_t* first_inf, bool* bad, float* K_out,
-                                        float beta = 0.f) {
+                                        float beta = 0.f, uint32_t* dout = nullptr) {
   constexpr int kP = stage_pitch<PT>();
+  constexpr int kPer = 4 / (int)sizeof(QT);  // deltas per word (kOutDeltaLane)
+  uint32_t dacc = 0u;
   const uint32_t rec_s = REC_SHARED ? (uint32_t)__cvta_generic_to_shared(rec) : 0u;
   auto load_rec = [&](int k) -> StepRec {
     if (REC_SHARED) return ld_rec_shared(rec_s + 16u * (uint32_t)k);
@@ -641,6 +645,17 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
         const uint32_t delta = (uint32_t)(i - st[s].fidx);
         if (check_delta && delta > (sizeof(QT) == 1 ? 255u : 65535u)) bad[s] = true;
         row[r.col] = (QT)delta;
+      }
+      if (OUT == kOutDeltaLane) {
+        // NS = 1: position j sits in word (j - 1) / kPer at slot (j - 1) % kPer
+        const uint32_t delta = (uint32_t)(i - st[s].fidx);
+        if (check_delta && delta > (sizeof(QT) == 1 ? 255u : 65535u)) bad[s] = true;
+        dacc = sizeof(QT) == 1 ? (dacc >> 8) | (delta << 24) : (dacc >> 16) | (delta << 16);
+        if (i % kPer == 0) {
+          dout[((i - 1) / kPer) * 32] = dacc;
+        } else if (i == n) {
+          dout[((i - 1) / kPer) * 32] = dacc >> (8 * (int)sizeof(QT) * (kPer - i % kPer));
+        }
       }
     }
   };
@@ -921,6 +936,115 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
   __syncthreads();
   tmem_fence_after();
   if (warp == 0) tmem_dealloc(tmem_base, 512);
+}
+
+// Fused adjoint with TMEM staging: the forward DP of split_tmem_kernel
+// (cost not stored), i - pred(i) of each position packed into the warp's
+// slot of a [word][lane] global scratch (one coalesced 128-byte store every
+// 4 uint8 / 2 uint16 positions), then each lane walks its own scenario's
+// optimal routes back from position n and counts route starts / ends in
+// shared-memory histograms.  The CTA holds blockDim.x / 32 = 16..24 warps:
+// a launch chooses the count that takes every tile in the fewest rounds
+// (the DP is bound by dependent latencies, so a fuller SM costs little and a
+// second, partly empty round costs a whole row's time).  Warp w holds its
+// tile in TMEM lane quadrant w % 4, column block w / 4 of cols_per_warp.
+template <typename QT, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) split_tmem_adj_kernel(SplitDequeArgs a,
+                                                                 int64_t tiles,
+                                                                 int cols_per_warp,
+                                                                 uint32_t* dscratch) {
+  constexpr int RING = 16;
+  constexpr int kPer = 4 / (int)sizeof(QT);
+  constexpr int UNR = MAXT <= 512 ? 2 : 1;  // 21..24 warps leave 80 registers
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t tmem_base;
+  const int n = a.n, Q = a.Q;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int dwords = (n + kPer - 1) / kPer;
+
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  StepRec* rec = reinterpret_cast<StepRec*>(smem);
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
+  size_t off = ((size_t)n + 1) * sizeof(StepRec);
+  unsigned int* hist_sm = reinterpret_cast<unsigned int*>(smem + off);
+  off += ((size_t)(2 * n + 1) * 4 + 15) & ~(size_t)15;
+  for (int k = threadIdx.x; k < 2 * n + 1; k += blockDim.x) hist_sm[k] = 0u;
+  uint2* ring_pl = reinterpret_cast<uint2*>(smem + off + ring_bytes(RING) * warp);
+  uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + RING * 32);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t taddr = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) +
+                         (uint32_t)((warp >> 2) * cols_per_warp);
+  uint32_t* dl = dscratch + ((int64_t)blockIdx.x * nwarps + warp) * dwords * 32 + lane;
+
+  bool neg = false;
+  uint32_t any_inf = 0, any_fb = 0;
+  const int64_t wstride = (int64_t)gridDim.x * nwarps;
+  for (int64_t tile = (int64_t)blockIdx.x * nwarps + warp; tile < tiles; tile += wstride) {
+    const int64_t s0 = tile * 32;
+    const int rows = (int)imin64(32, a.S - s0);
+    uint32_t first_inf = (uint32_t)n + 1;
+    bool bad = false;
+    float K;
+    using Src = TmemQ<QT>;
+    const TileFlags tf =
+        ingest_tile_tmem<QT, MAXT <= 512 ? 16 : 8>(a.demands + s0 * n, rows, n, Q, taddr, lane);
+    Src src{taddr, 0u};
+    if (tf.inf_rows)
+      dp_rows<1, QT, int32_t, RING, kOutDeltaLane, true, true, Src, UNR>(
+          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, nullptr, nullptr, 0, tf.zero,
+          &first_inf, &bad, &K, 0.f, dl);
+    else if (tf.small_loads)
+      dp_rows<1, QT, int32_t, RING, kOutDeltaLane, false, true, Src, UNR, true>(
+          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, nullptr, nullptr, 0, tf.zero,
+          &first_inf, &bad, &K, 0.f, dl);
+    else
+      dp_rows<1, QT, int32_t, RING, kOutDeltaLane, false, true, Src, UNR>(
+          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, nullptr, nullptr, 0, tf.zero,
+          &first_inf, &bad, &K, 0.f, dl);
+    neg |= tf.neg;
+    const bool valid = lane < rows;
+    bad = bad && valid;
+    if (bad) {
+      const uint32_t k = atomicAdd(a.fb_count, 1u);
+      a.fb_list[k] = (uint32_t)(s0 + lane);
+    }
+    any_inf |= tf.inf_rows;
+    any_fb |= __ballot_sync(0xffffffffu, bad);
+    // backtrack of this lane's scenario through its own deltas (written by
+    // this thread above: program order makes them visible)
+    if (valid && !bad && first_inf > (uint32_t)n) {
+      for (int i = n; i > 0;) {
+        const uint32_t w = dl[((i - 1) / kPer) * 32];
+        const int sh = 8 * (int)sizeof(QT) * ((i - 1) % kPer);
+        const int d = (int)((w >> sh) & (sizeof(QT) == 1 ? 0xFFu : 0xFFFFu));
+        if (d < 1 || d > i) break;  // 1 <= i - pred(i) <= i; keeps the walk bounded
+        const int p = i - d;
+        atomicAdd(&hist_sm[p], 1u);
+        atomicAdd(&hist_sm[n + i - 1], 1u);
+        i = p;
+      }
+      atomicAdd(&hist_sm[2 * n], 1u);
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (any_inf) atomicOr(a.status, SDP_FLAG_INFEASIBLE);
+    if (any_fb) atomicOr(a.status, SDP_FLAG_FALLBACK);
+    if (neg) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(tmem_base, 512);
+  for (int k = threadIdx.x; k < 2 * n + 1; k += blockDim.x)
+    if (hist_sm[k]) atomicAdd(&a.hist[k], (unsigned long long)hist_sm[k]);
 }
 
 // Soft-capacity Split with TMEM staging (16 warps per SM, as split_tmem_kernel
@@ -1388,6 +1512,64 @@ int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int grid, 
                        int* occ_out) {
   if (a.Q <= 254) return batch_ring<uint8_t>(a, warps, ring, grid, st, occ_out);
   return batch_ring<uint16_t>(a, warps, ring, grid, st, occ_out);
+}
+
+// ---- fused adjoint with TMEM staging
+namespace {
+constexpr int kAdjMaxWarps = 24;
+// TMEM columns of each warp when nw warps share the 512 (nw / 4 rounded up
+// warps per lane quadrant), in whole 4-column stores
+int adj_cols_per_warp(int nw) { return (512 / ((nw + 3) / 4)) & ~3; }
+}  // namespace
+
+int split_tmem_adj_warps(int n, int Q, int64_t S, int sms) {
+  if (n < 1 || S < 1 || sms < 1 || !deque_supported(n, Q)) return 0;
+  const int words = tmem_row_words(n, Q <= 254 ? 1 : 2);
+  if (words > adj_cols_per_warp(16)) return 0;
+  const int64_t tiles = (S + 31) / 32;
+  // fewest rounds of tiles over the SMs; the smallest such warp count
+  int best = 16;
+  int64_t best_rounds = (tiles + 16LL * sms - 1) / (16LL * sms);
+  for (int nw = 17; nw <= kAdjMaxWarps; ++nw) {
+    if (words > adj_cols_per_warp(nw)) break;
+    const int64_t r = (tiles + (int64_t)nw * sms - 1) / ((int64_t)nw * sms);
+    if (r < best_rounds) {
+      best_rounds = r;
+      best = nw;
+    }
+  }
+  return best;
+}
+
+size_t split_tmem_adj_scratch_bytes(int n, int Q, int sms) {
+  const int per = Q <= 254 ? 4 : 2;
+  return (size_t)sms * kAdjMaxWarps * (size_t)((n + per - 1) / per) * 32 * sizeof(uint32_t);
+}
+
+namespace {
+template <typename QT>
+int launch_adj_t(const SplitDequeArgs& a, int nw, uint32_t* dscratch, int sms,
+                 cudaStream_t st) {
+  auto k = nw <= 16 ? split_tmem_adj_kernel<QT, 512> : split_tmem_adj_kernel<QT, 32 * kAdjMaxWarps>;
+  size_t smem = ((size_t)a.n + 1) * sizeof(StepRec) + (((size_t)(2 * a.n + 1) * 4 + 15) & ~(size_t)15) +
+                (size_t)nw * ring_bytes(16);
+  if (smem < kOneCtaPerSmSmem) smem = kOneCtaPerSmSmem;  // one TMEM owner per SM
+  if (smem > kMaxSmemPerCta) return (int)cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  const int64_t tiles = (a.S + 31) / 32;
+  const int64_t ctas = (tiles + nw - 1) / nw;
+  const int grid = (int)(ctas < sms ? ctas : sms);
+  k<<<grid, 32 * nw, smem, st>>>(a, tiles, adj_cols_per_warp(nw), dscratch);
+  return (int)cudaGetLastError();
+}
+}  // namespace
+
+int launch_split_tmem_adj(const SplitDequeArgs& a, int warps, uint32_t* dscratch, int sms,
+                          cudaStream_t st) {
+  if (warps < 16 || warps > kAdjMaxWarps || !a.hist || !dscratch) return (int)cudaErrorInvalidValue;
+  if (a.Q <= 254) return launch_adj_t<uint8_t>(a, warps, dscratch, sms, st);
+  return launch_adj_t<uint16_t>(a, warps, dscratch, sms, st);
 }
 
 int deque_max_ctas_per_sm(const DequeConfig& c, bool hist, int pred_dtype,

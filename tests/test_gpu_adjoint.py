@@ -126,3 +126,71 @@ def test_adjoint_full_size():
     qs = np.concatenate([wl.split_demands(spec, int(s), int(s) + 1) for s in rows])
     orc = oracle.split(tour, spec.Q, qs, dist=dist, want_margin=True)
     check_split(r["cost"], r["pred"], orc, rows=rows, margin=1e-5, min_checked=0.5)
+
+
+def _sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("case", [
+    # (seed, n, Q, tiles per SM): the TMEM adjoint takes 16 warps per SM up to
+    # 16 tiles per SM, else as many (up to 24, as the row fits) as finish in
+    # the fewest rounds
+    (7, 17, 40, 0.5),      # n % 4 = 1, under one round
+    (8, 300, 120, 20.6),   # 21 warps, one round
+    (9, 300, 120, 24.0),   # 24 warps, exactly one round
+    (10, 350, 120, 18.0),  # 88-word rows: at most 20 warps
+    (11, 200, 300, 19.5),  # uint16 rows (Q >= 255), 100 words
+    (12, 450, 150, 17.0),  # 113-word rows: 16 warps, two rounds
+    (13, 301, 120, 49.3),  # several rounds at 17..24 warps
+])
+def test_adjoint_tmem_equals_shared_staging(case):
+    """The TMEM adjoint (default shape) and the shared-memory one (4 warps
+    per CTA) take the same DP steps: identical counts, identical gradient,
+    and both equal to the oracle's backtrack of the GPU's predecessors."""
+    seed, n, Q, tps = case
+    S = max(1, int(tps * _sms() * 32) - 5)   # a ragged last tile
+    tour, dist, q = _case(seed, n, S, Q, 10.0 if Q < 255 else 25.0)
+    t, qd, dd = _cuda(tour), _cuda(q), _cuda(dist)
+    gm = torch.tensor(1.0, device="cuda")
+    g0, h0 = sdp().split_backward(t, Q, qd, dd, gm, want_hist=True)
+    g1, h1 = sdp().split_backward(t, Q, qd, dd, gm, want_hist=True, warps=4)
+    torch.cuda.synchronize()
+    assert sdp().status() & sdp().FLAG_FALLBACK == 0
+    assert torch.equal(h0, h1)
+    assert torch.equal(g0, g1)
+    assert int(h0[:n].sum()) >= S  # every scenario has at least one route
+    if S <= 60000:
+        r, gp = _gpu_preds(tour, Q, q, dist)
+        start, end, skipped = oracle.split_route_counts(gp)
+        assert skipped == 0
+        h = h0.cpu().numpy()
+        np.testing.assert_array_equal(h[:n], start)
+        np.testing.assert_array_equal(h[n:], end)
+
+
+def test_adjoint_tmem_route_longer_than_255_falls_back():
+    """uint8 deltas hold routes of at most 255 customers: with zero demands a
+    route may be longer, and such scenarios are recomputed (with their
+    backtrack) by the plain kernel.  Counts equal the oracle's backtrack."""
+    rng = np.random.default_rng(14)
+    n, S, Q = 400, 200, 60
+    spec = wl.SplitSpec("adj_zero", n, Q, S, 14, "poisson", lam=1.0, lo=1, hi=Q, dist_mode=True)
+    tour, _, dist = wl.split_tour(spec)
+    q = (rng.random((S, n)) < 0.05).astype(np.int32) * rng.integers(1, 30, (S, n)).astype(np.int32)
+    q[:100] = 0                   # one route of all 400 customers
+    q[100:105, 200] = Q           # a full customer splits it into three
+    orc = oracle.split(tour, Q, q, dist=dist, want_margin=True)
+    r, gp = _gpu_preds(tour, Q, q, dist)
+    check_split(r["cost"], r["pred"], orc, min_checked=0.0)
+    g, hist = sdp().split_backward(_cuda(tour), Q, _cuda(q), _cuda(dist),
+                                   torch.tensor(1.0, device="cuda"), want_hist=True)
+    torch.cuda.synchronize()
+    assert sdp().status() & sdp().FLAG_FALLBACK
+    start, end, skipped = oracle.split_route_counts(gp)
+    assert skipped == 0
+    h = hist.cpu().numpy()
+    np.testing.assert_array_equal(h[:n], start)
+    np.testing.assert_array_equal(h[n:], end)
+    np.testing.assert_allclose(g.cpu().double().numpy(), oracle.split_mean_grad(tour, gp),
+                               rtol=1e-6, atol=1e-9)
