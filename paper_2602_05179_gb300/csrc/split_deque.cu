@@ -295,14 +295,17 @@ __device__ __forceinline__ TileFlags ingest_tile_tmem(const int32_t* src, int ro
     // Fast pass: pack without clamping, tracking each row's minimum and
     // maximum; a tile with a demand outside [0, Q] is packed again below with
     // the clamp and the per-row flags.
+    // Padding (columns past n, rows past the tile) packs as demand 1: no DP
+    // step reads it, and the tile minimum then tells whether a real demand
+    // is zero.
     constexpr int LOADS = WPI * PER / 4;
-    int mn = 0, mx = 0;  // the zero padding is inside [0, Q] anyway
+    int mn = 1, mx = 0;
     for (int w0 = 0; w0 < words; w0 += WPI) {
       int4 x[LOADS];
 #pragma unroll
       for (int k = 0; k < LOADS; ++k) {
         const int c = w0 * PER + 4 * k;
-        x[k] = (live && c < n) ? ld_v4(row + c) : make_int4(0, 0, 0, 0);
+        x[k] = (live && c < n) ? ld_v4(row + c) : make_int4(1, 1, 1, 1);
       }
 #pragma unroll
       for (int k = 0; k < LOADS; ++k) {
@@ -323,7 +326,7 @@ __device__ __forceinline__ TileFlags ingest_tile_tmem(const int32_t* src, int ro
     if (!__any_sync(0xffffffffu, mn < 0 || mx > Q)) {
       TileFlags t;
       t.inf_rows = 0u;
-      t.zero = true;  // conservative (the TMEM kernels write no in-place deltas)
+      t.zero = __any_sync(0xffffffffu, mn <= 0);
       t.neg = false;
       t.small_loads = !__any_sync(0xffffffffu, n * mx >= 65536);  // n <= 512, mx <= Q
       return t;
@@ -586,7 +589,7 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
                                         float beta = 0.f, uint32_t* dout = nullptr) {
   constexpr int kP = stage_pitch<PT>();
   constexpr int kPer = 4 / (int)sizeof(QT);  // deltas per word (kOutDeltaLane)
-  uint32_t dacc = 0u;
+  uint32_t dlast = 0u;
   const uint32_t rec_s = REC_SHARED ? (uint32_t)__cvta_generic_to_shared(rec) : 0u;
   auto load_rec = [&](int k) -> StepRec {
     if (REC_SHARED) return ld_rec_shared(rec_s + 16u * (uint32_t)k);
@@ -646,21 +649,39 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
         if (check_delta && delta > (sizeof(QT) == 1 ? 255u : 65535u)) bad[s] = true;
         row[r.col] = (QT)delta;
       }
-      if (OUT == kOutDeltaLane) {
-        // NS = 1: position j sits in word (j - 1) / kPer at slot (j - 1) % kPer
-        const uint32_t delta = (uint32_t)(i - st[s].fidx);
-        if (check_delta && delta > (sizeof(QT) == 1 ? 255u : 65535u)) bad[s] = true;
-        dacc = sizeof(QT) == 1 ? (dacc >> 8) | (delta << 24) : (dacc >> 16) | (delta << 16);
-        if (i % kPer == 0) {
-          dout[((i - 1) / kPer) * 32] = dacc;
-        } else if (i == n) {
-          dout[((i - 1) / kPer) * 32] = dacc >> (8 * (int)sizeof(QT) * (kPer - i % kPer));
-        }
-      }
+      if (OUT == kOutDeltaLane) dlast = (uint32_t)(i - st[s].fidx);  // NS = 1
     }
   };
 
-  if (OUT == kOutDirect) {
+  if (OUT == kOutDeltaLane) {
+    // position j's delta sits in word (j - 1) / kPer at slot (j - 1) % kPer;
+    // whole words first (static slots), then the last partial word
+    constexpr int kBits = 8 * (int)sizeof(QT);
+    uint32_t any = 0u;  // OR of the deltas: one range test per row
+    int i = 1;
+    for (; i + kPer - 1 <= n; i += kPer) {
+      uint32_t w = 0u;
+      int p;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        step(i + u, &p);
+        any |= dlast;
+        w |= dlast << (kBits * u);
+      }
+      dout[((i - 1) / kPer) * 32] = w;
+    }
+    if (i <= n) {
+      uint32_t w = 0u;
+      int p;
+      for (int u = 0; i + u <= n; ++u) {
+        step(i + u, &p);
+        any |= dlast;
+        w |= dlast << (kBits * u);
+      }
+      dout[((i - 1) / kPer) * 32] = w;
+    }
+    if (check_delta && any > (sizeof(QT) == 1 ? 255u : 65535u)) bad[0] = true;
+  } else if (OUT == kOutDirect) {
     PT* prow[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) prow[s] = pred_tile + (int64_t)(s * 32 + lane) * n;
