@@ -196,7 +196,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--only", default="", choices=["", "reinsert", "batch", "adjoint", "soft"],
+    ap.add_argument("--only", default="",
+                    choices=["", "reinsert", "batch", "adjoint", "soft", "saa"],
                     help="run one operator line alone (profiling)")
     ap.add_argument("--preds", default="u16", choices=["u16", "i32", "none"])
     ap.add_argument("--no-operators", action="store_true",
@@ -461,7 +462,9 @@ def _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm):
     import torch
     if only == "soft":
         return _operator_soft(api, wl, dev, steps, out, hbm)
-    if only and only != "adjoint":
+    if only == "saa":
+        return _operator_saa(api, wl, dev, steps, out, p_alu)
+    if only == "batch":
         return _operator_batch(api, wl, dev, steps, out, p_alu, hbm)
     # ---- adjoint n=300, S=10^5 (fused forward + on-chip backtrack)
     ad = wl.ADJOINT_C5
@@ -488,7 +491,48 @@ def _operators_rest(api, wl, dev, only, steps, out, p_alu, hbm):
     if only:
         return out
     _operator_soft(api, wl, dev, steps, out, hbm)
-    return _operator_batch(api, wl, dev, steps, out, p_alu, hbm)
+    _operator_batch(api, wl, dev, steps, out, p_alu, hbm)
+    return _operator_saa(api, wl, dev, steps, out, p_alu)
+
+
+def _operator_saa(api, wl, dev, steps, out, p_alu):
+    """SAA candidate search on one CVRPSD instance (n=100, Q=100, Poisson(10)
+    demands, S=10^4): every iteration scores the current tour and 1024
+    neighbours in one batched-plan replay and takes the best strict
+    improvement on the device."""
+    import tempfile
+    import torch
+    spec = wl.SAA_C6
+    tour, xy, _ = wl.split_tour(spec)
+    t = torch.from_numpy(tour).to(dev)
+    c = torch.from_numpy(xy).to(dev)
+    q = wl.split_demands_device(spec, dev)
+    s = api.SaaSearch(t, c, q, spec.Q, wl.SAA_B, seed=spec.seed)
+    s.autotune(os.path.join(tempfile.gettempdir(), "sdp_autotune_cache.txt"))
+    s.run(3)  # warm-up: graph capture, first moves
+    torch.cuda.synchronize()
+    iters = steps or 20
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    trace, acc = s.run(iters)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    _, tot = api.split_count_arcs(t, spec.Q, q, coords=c, per_scenario=False)
+    evals = iters * (wl.SAA_B + 1)
+    arcs = int(tot) * evals  # estimate: every candidate at the start tour's arc count
+    tr = trace.cpu().numpy()
+    out[f"saa_n{spec.n}_S1e4_B{wl.SAA_B}"] = {
+        "value": iters * wl.SAA_B / (ms / 1e3), "unit": "candidates/s",
+        "ms_per_iteration": ms / iters, "iterations": iters,
+        "scenario_evaluations_per_s": evals * spec.S / (ms / 1e3),
+        "arcs_per_s_est": arcs / (ms / 1e3), "alu_frac_est": 2 * arcs / (ms / 1e3) / p_alu,
+        "best_mean_first": float(tr[0]), "best_mean_last": float(tr[-1]),
+        "improving_iterations": int((acc >= 0).sum())}
+    s.close()
+    del q
+    return out
 
 
 def _operator_batch(api, wl, dev, steps, out, p_alu, hbm):

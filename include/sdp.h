@@ -287,6 +287,73 @@ int sdp_plan_info(const sdp_plan* p, int32_t* warps_per_cta, int32_t* ring,
 int sdp_plan_count_arcs(sdp_plan* p, void* stream, uint64_t* total_host);
 void sdp_plan_destroy(sdp_plan* p);
 
+/* ------------------------------------------------- SAA candidate search */
+/* Sample-average-approximation search over first-stage giant tours (the
+ * candidate loop of Sec. "Decision Quality under Fixed Time Budgets" and
+ * Tables tab:gpu_dsirp / tab:cand_cvrp, where a genetic algorithm proposes
+ * candidates and each is scored by the SAA mean of its second-stage Split
+ * over the scenario set).  Here a local search proposes them: every
+ * iteration evaluates the current tour and B neighbours of it over the same
+ * S demand scenarios in one replay of a batched plan (B + 1 tours sharing
+ * one demand array and one coordinate array), then moves to the neighbour
+ * with the lowest scenario mean if that mean is strictly below the current
+ * tour's (ties between neighbours go to the smaller index).  Candidates are
+ * built and chosen on the device; the host only enqueues.
+ *
+ * Neighbour k (0-based) of iteration t draws z = SplitMix64 output number
+ * c = t*B + k of the stream `seed` (z = mix(seed + (c+1)*0x9E3779B97F4A7C15),
+ * mix = the finaliser of Steele, Lea and Flood's SplittableRandom with
+ * Stafford's constants), then
+ *     a = (z mod 2^32) mod n,  b = (z >> 40) mod (n-1),  b += (b >= a),
+ *     kind = enabled[((z >> 32) & 255) mod #enabled]
+ * with the enabled kinds listed in the order 2-opt, relocate, swap:
+ *     2-opt:    reverse positions min(a,b) .. max(a,b) of the tour;
+ *     relocate: take the customer at position a out and reinsert it so that
+ *               it ends at position b;
+ *     swap:     exchange the customers at positions a and b.
+ * Positions are 0-based indices into the tour array. */
+#define SDP_MOVE_2OPT 1
+#define SDP_MOVE_RELOCATE 2
+#define SDP_MOVE_SWAP 4
+
+typedef struct sdp_saa_search_desc {
+  int32_t n;               /* customers, 2 <= n <= 2048 */
+  const float* coords;     /* device [(n+1)*2], node 0 = depot */
+  int32_t Q;               /* capacity, 1 <= Q <= 32767 */
+  int64_t S;               /* scenarios, S >= 1 */
+  const int32_t* demands;  /* device [S*n], demands[s*n + (c-1)] = demand of
+                              customer c; one scenario set for every candidate */
+  int32_t B;               /* neighbours per iteration, 1 <= B <= 2^20 */
+  uint64_t seed;           /* move stream */
+  int32_t moves;           /* nonzero OR of SDP_MOVE_* */
+  const int32_t* tour0;    /* device [n]: the starting tour, a permutation of
+                              1..n (copied at create) */
+} sdp_saa_search_desc;
+
+typedef struct sdp_saa_search sdp_saa_search;
+/* Allocates the search (its batched plan, B + 1 candidate tours, their costs
+ * and means, the current tour); SDP_ERR_OOM if that fails.  The caller's
+ * coords and demands must stay valid until destroy.  Uses the current
+ * device; later calls must run with that device current. */
+int sdp_saa_search_create(const sdp_saa_search_desc* d, sdp_saa_search** out);
+/* Runs `iters` iterations on `stream` (continuing the move stream where the
+ * previous run stopped).  trace_out: device [iters] fp64 or NULL: the best
+ * mean after each iteration; accepted_out: device [iters] int32 or NULL: the
+ * neighbour taken (0..B-1), or -1 if none improved. */
+int sdp_saa_search_run(sdp_saa_search* s, int32_t iters, double* trace_out,
+                       int32_t* accepted_out, void* stream);
+/* Current tour (device [n] int32) and, if means_out (device [B+1] fp64) is
+ * set, the means of the last iteration: [0] the tour it started from, [1+k]
+ * neighbour k.  Before any iteration the means are not defined. */
+int sdp_saa_search_state(sdp_saa_search* s, int32_t* tour_out, double* means_out,
+                         void* stream);
+/* sdp_plan_autotune on the search's plan, deque rings of 16 entries only:
+ * the tours change as the search goes, and a ring sized on the first ones can
+ * overflow on later, better tours (longer monotone runs in the deque), whose
+ * scenarios then go to the plain fallback.  Overwrites the last means. */
+int sdp_saa_search_autotune(sdp_saa_search* s, void* stream, const char* cache_path);
+void sdp_saa_search_destroy(sdp_saa_search* s);
+
 /* ------------------------------------------------------------ Reinsertion */
 /* One customer, order-up-to level U, days t = 0..T-1, S scenarios.
  * State: start-of-day inventory I in 0..U.  Actions q in {0, U-I}; delivery

@@ -276,3 +276,6 @@ def reinsert_routes(T, U, I0, h, p, unit_cost, rcost, cap, consumption, *, H=Non
         raise ValueError(f"oracle_reinsert_routes failed: {rc}")
     return {"value": value, "policy": policy, "value0": value0, "margin": margin,
             "mean": float(mean[0])}
+
+
+from .saa import apply_move, draw_move, saa_search, splitmix64  # noqa: E402,F401

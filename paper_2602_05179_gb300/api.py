@@ -55,6 +55,12 @@ class BatchDesc(ctypes.Structure):
                 ("means_out", P)]
 
 
+class SaaSearchDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("coords", P), ("Q", ctypes.c_int32),
+                ("S", ctypes.c_int64), ("demands", P), ("B", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("moves", ctypes.c_int32), ("tour0", P)]
+
+
 class SdpError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libsdp error {code}: {msg}")
@@ -96,6 +102,11 @@ def _load():
             "sdp_plan_info": ([P, P, P, P, P], i32),
             "sdp_plan_count_arcs": ([P, P, P], i32),
             "sdp_plan_destroy": ([P], None),
+            "sdp_saa_search_create": ([P, P], i32),
+            "sdp_saa_search_run": ([P, i32, P, P, P], i32),
+            "sdp_saa_search_state": ([P, P, P, P], i32),
+            "sdp_saa_search_autotune": ([P, P, ctypes.c_char_p], i32),
+            "sdp_saa_search_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -411,6 +422,70 @@ class SplitPlan:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self._lib.sdp_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MOVES = {"2opt": 1, "relocate": 2, "swap": 4}
+
+
+class SaaSearch:
+    """SAA local search over giant tours: every iteration scores the current
+    tour and B neighbours (2-opt / relocate / swap moves drawn from a
+    SplitMix64 stream) by their Split mean over the same scenario set, in one
+    batched-plan replay, and keeps the best neighbour if it is strictly
+    better.  tour0: int32 CUDA [n]; coords fp32 CUDA [n+1, 2]; demands int32
+    CUDA [S, n] (16-byte aligned; shared by every candidate)."""
+
+    def __init__(self, tour0, coords, demands, Q, B, *, seed=0,
+                 moves=("2opt", "relocate", "swap")):
+        lib = _load()
+        self._lib = lib
+        self.n = int(tour0.numel())
+        self.S = int(demands.shape[0])
+        self.B, self.Q = int(B), int(Q)
+        self.coords, self.demands = coords, demands  # kept alive for the search
+        d = SaaSearchDesc()
+        d.n, d.Q, d.S, d.B = self.n, self.Q, self.S, self.B
+        d.coords = _dev_ptr(coords, "coords", torch.float32)
+        d.demands = _dev_ptr(demands, "demands", torch.int32)
+        d.tour0 = _dev_ptr(tour0, "tour0", torch.int32)
+        d.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        d.moves = sum(MOVES[m] for m in moves)
+        self._dev = demands.device
+        self._h = ctypes.c_void_p()
+        _check(lib.sdp_saa_search_create(ctypes.byref(d), ctypes.byref(self._h)))
+
+    def run(self, iters, stream=None):
+        """(trace fp64 [iters]: best mean after each iteration, accepted int32
+        [iters]: neighbour taken or -1), on the device."""
+        trace = torch.empty(max(int(iters), 0), dtype=torch.float64, device=self._dev)
+        acc = torch.empty(max(int(iters), 0), dtype=torch.int32, device=self._dev)
+        _check(self._lib.sdp_saa_search_run(self._h, int(iters), _dev_ptr(trace, "trace"),
+                                            _dev_ptr(acc, "accepted"), _stream(stream)))
+        return trace, acc
+
+    def state(self, stream=None):
+        """(current tour int32 [n], means fp64 [B+1] of the last iteration:
+        [0] the tour it started from, [1+k] neighbour k)."""
+        tour = torch.empty(self.n, dtype=torch.int32, device=self._dev)
+        means = torch.empty(self.B + 1, dtype=torch.float64, device=self._dev)
+        _check(self._lib.sdp_saa_search_state(self._h, _dev_ptr(tour, "tour"),
+                                              _dev_ptr(means, "means"), _stream(stream)))
+        return tour, means
+
+    def autotune(self, cache_path=None, stream=None):
+        cp = cache_path.encode() if cache_path else None
+        _check(self._lib.sdp_saa_search_autotune(self._h, _stream(stream), cp))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.sdp_saa_search_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -442,6 +442,8 @@ int status_word(uint32_t** out) { return status_ptr(out); }
 
 int api_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
+bool api_device_ptr(const void* p) { return is_device_ptr(p); }
+
 int num_sms() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;

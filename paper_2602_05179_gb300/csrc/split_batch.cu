@@ -319,10 +319,17 @@ int sdp_plan_info(const sdp_plan* p, int32_t* warps_per_cta, int32_t* ring, int3
   return SDP_OK;
 }
 
-int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
+}  // extern "C"
+
+namespace sdp {
+// min_ring: the smallest deque ring timed.  Plans whose tours change between
+// runs (the SAA search) take 16: a ring sized on the tours it was timed on can
+// overflow on later ones, and overflowed scenarios go to the plain fallback.
+int plan_autotune(sdp_plan* p, void* stream, const char* cache_path, int min_ring) {
   if (!p) return pfail(SDP_ERR_INVALID_ARG, "plan is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const std::string key = cache_key(p);
+  std::string key = cache_key(p);
+  if (min_ring > 8) key += "|ring>=" + std::to_string(min_ring);
   if (cache_path) {
     FILE* f = fopen(cache_path, "r");
     if (f) {
@@ -353,6 +360,7 @@ int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
   for (int w : warps_c)
     for (int r : ring_c) {
       if (w < 0 && r != 16) continue;  // the streaming kernel has one ring size
+      if (r < min_ring) continue;
       if (configure(p, w, r)) continue;
       float tsum = 0.f;
       bool ok = true;
@@ -380,6 +388,13 @@ int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
     }
   }
   return SDP_OK;
+}
+}  // namespace sdp
+
+extern "C" {
+
+int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
+  return plan_autotune(p, stream, cache_path, 8);
 }
 
 int sdp_plan_count_arcs(sdp_plan* p, void* stream, uint64_t* total_host) {

@@ -164,6 +164,10 @@ SPLIT_C1 = SplitSpec("split_n50_S1e3", 50, 100, 1000, 0, "poisson", lam=10.0, lo
 SPLIT_C2 = SplitSpec("split_n500_S1e6", 500, 200, 1_000_000, 1, "uniform", lo=1, hi=30)
 ADJOINT_C5 = SplitSpec("adjoint_n300_S1e5", 300, 120, 100_000, 4, "poisson", lam=10.0,
                        lo=1, hi=120, dist_mode=True)
+# SAA candidate search: one CVRPSD instance (n = 100 customers, Q = 100,
+# Poisson(10) demands, 10^4 scenarios), 1024 neighbours per iteration
+SAA_C6 = SplitSpec("saa_n100_S1e4", 100, 100, 10_000, 6, "poisson", lam=10.0, lo=1, hi=100)
+SAA_B = 1024
 
 
 def split_tour(spec: SplitSpec):
