@@ -334,7 +334,9 @@ typedef struct sdp_saa_search sdp_saa_search;
 /* Allocates the search (its batched plan, B + 1 candidate tours, their costs
  * and means, the current tour); SDP_ERR_OOM if that fails.  The caller's
  * coords and demands must stay valid until destroy.  Uses the current
- * device; later calls must run with that device current. */
+ * device; later calls must run with that device current.  A search is used
+ * from one thread at a time (like a plan); its calls are ordered on the
+ * stream they are given. */
 int sdp_saa_search_create(const sdp_saa_search_desc* d, sdp_saa_search** out);
 /* Runs `iters` iterations on `stream` (continuing the move stream where the
  * previous run stopped).  trace_out: device [iters] fp64 or NULL: the best

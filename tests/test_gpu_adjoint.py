@@ -194,3 +194,26 @@ def test_adjoint_tmem_route_longer_than_255_falls_back():
     np.testing.assert_array_equal(h[n:], end)
     np.testing.assert_allclose(g.cpu().double().numpy(), oracle.split_mean_grad(tour, gp),
                                rtol=1e-6, atol=1e-9)
+
+
+def test_adjoint_tmem_uint16_rows_with_over_capacity_demands():
+    """Q >= 255 stages uint16 rows; demands above Q make their scenarios
+    infeasible (no arc counted).  The TMEM adjoint, the shared-memory one and
+    the oracle's backtrack of the GPU's predecessors agree."""
+    n, S, Q = 180, 3000, 400
+    tour, dist, q = _case(15, n, S, Q, 40.0)
+    q[7, 3] = Q + 1
+    q[2999, 179] = 5000
+    t, qd, dd = _cuda(tour), _cuda(q), _cuda(dist)
+    gm = torch.tensor(1.0, device="cuda")
+    g0, h0 = sdp().split_backward(t, Q, qd, dd, gm, want_hist=True)
+    g1, h1 = sdp().split_backward(t, Q, qd, dd, gm, want_hist=True, warps=4)
+    torch.cuda.synchronize()
+    assert sdp().status() & sdp().FLAG_INFEASIBLE
+    assert torch.equal(h0, h1) and torch.equal(g0, g1)
+    r, gp = _gpu_preds(tour, Q, q, dist)
+    start, end, skipped = oracle.split_route_counts(gp)
+    assert skipped == 2
+    h = h0.cpu().numpy()
+    np.testing.assert_array_equal(h[:n], start)
+    np.testing.assert_array_equal(h[n:], end)
