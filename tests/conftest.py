@@ -24,3 +24,16 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _clear_device_status(request):
+    """The library's device status word is sticky across calls: clear it
+    before every GPU test so that each test reads only its own flags."""
+    if "gpu" in request.keywords:
+        import torch
+        if torch.cuda.is_available():
+            from paper_2602_05179_gb300 import api
+            torch.cuda.synchronize()
+            api.status()
+    yield

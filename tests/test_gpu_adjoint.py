@@ -217,3 +217,4 @@ def test_adjoint_tmem_uint16_rows_with_over_capacity_demands():
     h = h0.cpu().numpy()
     np.testing.assert_array_equal(h[:n], start)
     np.testing.assert_array_equal(h[n:], end)
+    sdp().status()  # the forward above flags the same infeasible scenarios
