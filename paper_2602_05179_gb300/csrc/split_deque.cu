@@ -570,8 +570,10 @@ __device__ __forceinline__ void flush_stage(const PT* stage, PT* pred_tile, int 
 // Scenario s of the lane is tile row s * 32 + lane.
 // CHECK: the tile holds a scenario with a demand above Q; first_inf records
 // the first such position of each scenario.
-// REC_SHARED: rec points to shared memory (loaded as LDS.128) and holds a copy
-// of position n after it.
+// REC_SHARED: rec points to shared memory (loaded as LDS.128) and holds copies
+// of position n at indices n and n + 1.  Records are loaded two positions
+// ahead, so the TMEM load of the next demand reads a column loaded a step
+// earlier instead of waiting for this step's shared load.
 // OUT == kOutStream: predecessors through the shared-memory stage (any n);
 // OUT == kOutDirect: each lane stores its own row, 4 positions per 8-byte
 // (uint16) or 16-byte (int32) store, when n % 4 == 0 and the rows are aligned
@@ -596,6 +598,7 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
     return ld_rec_any(rec + k);
   };
   StepRec rn = load_rec(0);
+  StepRec rn2 = load_rec(REC_SHARED ? 1 : min(1, n - 1));
   DequeState<RING, PACKED> st[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -609,8 +612,9 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
     int q[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) q[s] = src[s].take(r);
-    // next position's record and demand
-    rn = load_rec(REC_SHARED ? i : min(i, n - 1));
+    // next position's demand (its record came a step ago), the record after it
+    rn = rn2;
+    rn2 = load_rec(REC_SHARED ? i + 1 : min(i + 1, n - 1));
 #pragma unroll
     for (int s = 0; s < NS; ++s) src[s].prefetch(rn);
     // Each lane pops on its own: warp votes that skipped the pop phases when
@@ -869,8 +873,8 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
   // tour records in shared memory (a row that fits a warp's TMEM columns has
   // n <= 512), plus a copy of position n after them
   StepRec* rec = reinterpret_cast<StepRec*>(smem);
-  for (int k = threadIdx.x; k <= n; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
-  const size_t off = ((size_t)n + 1) * sizeof(StepRec);
+  for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
+  const size_t off = ((size_t)n + 2) * sizeof(StepRec);
   const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, 1>() : 0;
   const size_t per_warp = ring_bytes(RING) + stage_bytes;
   unsigned char* wbase = smem + off + per_warp * warp;
@@ -990,8 +994,8 @@ __global__ void __launch_bounds__(MAXT, 1) split_tmem_adj_kernel(SplitDequeArgs 
     tmem_relinquish();
   }
   StepRec* rec = reinterpret_cast<StepRec*>(smem);
-  for (int k = threadIdx.x; k <= n; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
-  size_t off = ((size_t)n + 1) * sizeof(StepRec);
+  for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
+  size_t off = ((size_t)n + 2) * sizeof(StepRec);
   unsigned int* hist_sm = reinterpret_cast<unsigned int*>(smem + off);
   off += ((size_t)(2 * n + 1) * 4 + 15) & ~(size_t)15;
   for (int k = threadIdx.x; k < 2 * n + 1; k += blockDim.x) hist_sm[k] = 0u;
@@ -1088,8 +1092,8 @@ __global__ void __launch_bounds__(512, 1) split_tmem_soft_kernel(SplitDequeArgs 
     tmem_relinquish();
   }
   StepRec* rec = reinterpret_cast<StepRec*>(smem);
-  for (int k = threadIdx.x; k <= n; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
-  const size_t off = ((size_t)n + 1) * sizeof(StepRec);
+  for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
+  const size_t off = ((size_t)n + 2) * sizeof(StepRec);
   const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, 1>() : 0;
   const size_t per_warp = ring_bytes(RING) + stage_bytes;
   unsigned char* wbase = smem + off + per_warp * warp;
@@ -1242,7 +1246,7 @@ __global__ void __launch_bounds__(512, 1) split_batch_tmem_kernel(BatchKernelArg
     tmem_alloc(&tmem_base, 512);
     tmem_relinquish();
   }
-  const size_t rec_bytes = ((size_t)a.n_max + 1) * sizeof(StepRec);
+  const size_t rec_bytes = ((size_t)a.n_max + 2) * sizeof(StepRec);
   const size_t per_warp = ring_bytes(RING) + rec_bytes;
   unsigned char* wbase = smem + per_warp * warp;
   uint2* ring_pl = reinterpret_cast<uint2*>(wbase);
@@ -1273,7 +1277,7 @@ __global__ void __launch_bounds__(512, 1) split_batch_tmem_kernel(BatchKernelArg
     if (b != cur_b) {  // this tour's records into the warp's slice
       __syncwarp();
       const StepRec* src = a.rec + a.rec_off[b];
-      for (int k = lane; k <= n; k += 32) rec_sm[k] = tmem_rec<QT>(ld_rec_any(src + min(k, n - 1)));
+      for (int k = lane; k <= n + 1; k += 32) rec_sm[k] = tmem_rec<QT>(ld_rec_any(src + min(k, n - 1)));
       __syncwarp();
       cur_b = b;
     }
@@ -1357,7 +1361,7 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
   // needed.
   c.tmem = allow_tmem && !hist && tmem_row_words(n, c.qbytes) <= kTmemColsPerWarp;
   if (c.tmem) {
-    const size_t base = ((size_t)n + 1) * sizeof(StepRec);
+    const size_t base = ((size_t)n + 2) * sizeof(StepRec);
     const size_t per_warp = ring_bytes(ring) + stage_bytes_for(pred_bytes, 1);
     c.warps = 16 + kTmemExtraWarps;
     size_t need = base + (size_t)c.warps * per_warp +
@@ -1482,7 +1486,7 @@ size_t batch_smem(int n_max, int Q, int warps, int ring) {
   const int qbytes = Q <= 254 ? 1 : 2;
   if (warps == 0) {
     const int tw = batch_tmem_warps(n_max, Q);
-    const size_t need = (size_t)tw * (ring_bytes(ring) + ((size_t)n_max + 1) * sizeof(StepRec));
+    const size_t need = (size_t)tw * (ring_bytes(ring) + ((size_t)n_max + 2) * sizeof(StepRec));
     return need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
   }
   return (size_t)warps * ((size_t)32 * staged_row_stride(n_max, qbytes) + ring_bytes(ring));
@@ -1572,7 +1576,7 @@ template <typename QT>
 int launch_adj_t(const SplitDequeArgs& a, int nw, uint32_t* dscratch, int sms,
                  cudaStream_t st) {
   auto k = nw <= 16 ? split_tmem_adj_kernel<QT, 512> : split_tmem_adj_kernel<QT, 32 * kAdjMaxWarps>;
-  size_t smem = ((size_t)a.n + 1) * sizeof(StepRec) + (((size_t)(2 * a.n + 1) * 4 + 15) & ~(size_t)15) +
+  size_t smem = ((size_t)a.n + 2) * sizeof(StepRec) + (((size_t)(2 * a.n + 1) * 4 + 15) & ~(size_t)15) +
                 (size_t)nw * ring_bytes(16);
   if (smem < kOneCtaPerSmSmem) smem = kOneCtaPerSmSmem;  // one TMEM owner per SM
   if (smem > kMaxSmemPerCta) return (int)cudaErrorInvalidValue;
