@@ -573,7 +573,9 @@ __device__ __forceinline__ void flush_stage(const PT* stage, PT* pred_tile, int 
 // REC_SHARED: rec points to shared memory (loaded as LDS.128) and holds copies
 // of position n at indices n and n + 1.  Records are loaded two positions
 // ahead, so the TMEM load of the next demand reads a column loaded a step
-// earlier instead of waiting for this step's shared load.
+// earlier instead of waiting for this step's shared load (1.603 -> 1.589 ms
+// at n = 500, S = 10^6).  Records read from global memory stay one position
+// ahead: two ahead slowed the batched shared-memory kernel by 4%.
 // OUT == kOutStream: predecessors through the shared-memory stage (any n);
 // OUT == kOutDirect: each lane stores its own row, 4 positions per 8-byte
 // (uint16) or 16-byte (int32) store, when n % 4 == 0 and the rows are aligned
@@ -598,7 +600,7 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
     return ld_rec_any(rec + k);
   };
   StepRec rn = load_rec(0);
-  StepRec rn2 = load_rec(REC_SHARED ? 1 : min(1, n - 1));
+  StepRec rn2 = REC_SHARED ? load_rec(1) : rn;
   DequeState<RING, PACKED> st[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -613,8 +615,12 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
 #pragma unroll
     for (int s = 0; s < NS; ++s) q[s] = src[s].take(r);
     // next position's demand (its record came a step ago), the record after it
-    rn = rn2;
-    rn2 = load_rec(REC_SHARED ? i + 1 : min(i + 1, n - 1));
+    if (REC_SHARED) {
+      rn = rn2;
+      rn2 = load_rec(i + 1);
+    } else {
+      rn = load_rec(min(i, n - 1));
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s) src[s].prefetch(rn);
     // Each lane pops on its own: warp votes that skipped the pop phases when
