@@ -232,5 +232,5 @@ def test_split_workload_c1_smoke():
     r = oracle.split(tour, spec.Q, q, coords=xy)
     assert np.all(np.isfinite(r["cost"]))
     assert abs(r["mean"] - r["cost"].mean()) <= 1e-9 * r["mean"]
-    # survey estimate: ~439 feasible arcs per scenario
+    # a seeded estimate over 200 scenarios gives about 439 feasible arcs each
     assert 300 < r["arcs"].mean() < 600
