@@ -226,9 +226,9 @@ int sdp_split_count_arcs(const sdp_split_args* a, int64_t* arcs_out,
  * Infeasible scenarios contribute no arc (the mean is +inf there).
  * Fused pass, default shape (warps_per_cta = 0, ring 0 or 16) and rows that
  * fit the tensor memory (n bytes of uint8 or 2n of uint16 within 512): the
- * deque kernel with TMEM-staged rows and 16..24 warps per SM, as many as
- * take all 32-scenario tiles in the fewest rounds, keeping i - pred(i) in a
- * workspace scratch; otherwise the shared-memory DEQUE kernel keeps them in
+ * deque kernel with TMEM-staged rows and 16 warps per SM (17..24 when that
+ * many take every 32-scenario tile in one round where 16 would need two),
+ * keeping i - pred(i) in a workspace scratch; otherwise the shared-memory DEQUE kernel keeps them in
  * its staged rows. */
 size_t sdp_split_backward_workspace_bytes(const sdp_split_args* fwd);
 int sdp_split_backward(const sdp_split_args* fwd, const void* pred,

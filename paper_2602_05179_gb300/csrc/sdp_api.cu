@@ -397,6 +397,10 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     // an explicit warp count selects shared-memory staging with that shape.
     DequeConfig cfg = deque_config(a->n, a->Q, a->warps_per_cta, ring, hist != nullptr, pbytes,
                                    a->warps_per_cta == 0);
+    if (a->warps_per_cta == 0 && !hist && a->capacity_mode != SDP_CAPACITY_SOFT) {
+      const bool direct_ok = !pred || ((a->n & 3) == 0 && (reinterpret_cast<uintptr_t>(pred) & 15) == 0);
+      cfg = deque_config_wide(cfg, a->n, a->Q, a->S, direct_ok, sms);
+    }
     const int warps = cfg.warps;
     if (cfg.smem > 227 * 1024)
       return fail(SDP_ERR_UNSUPPORTED, "DEQUE tile needs %zu B of shared memory; lower warps_per_cta", cfg.smem);

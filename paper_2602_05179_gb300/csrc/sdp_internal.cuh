@@ -102,8 +102,15 @@ int launch_split_deque(const SplitDequeArgs& a, const DequeConfig& c, int grid,
                        cudaStream_t st);
 int deque_max_ctas_per_sm(const DequeConfig& c, bool hist, int pred_dtype,
                           bool want_pred, int* out);
-// Fused adjoint with TMEM-staged rows: warps per CTA (16..24) for S
-// scenarios on sms SMs, 0 where rows do not fit; the [word][lane] delta
+// The default TMEM launch c made wide (17..24 warps, every one staging its
+// tile in TMEM) when that many take every tile in one round where 16 would
+// need two, and the rows fit; direct_ok: no predecessors, or predecessors stored 4 per lane
+// (n % 4 == 0, 16-byte aligned rows).  Returns c itself otherwise.
+DequeConfig deque_config_wide(const DequeConfig& c, int n, int Q, int64_t S, bool direct_ok,
+                              int sms);
+// Fused adjoint and forward with TMEM-staged rows: warps per CTA (16..24)
+// for S scenarios on sms SMs (more than 16 only for a single round), 0 where
+// rows do not fit 16 warps' columns; the [word][lane] delta
 // scratch it needs; the launch (hist set, cost / pred unused).
 int split_tmem_adj_warps(int n, int Q, int64_t S, int sms);
 size_t split_tmem_adj_scratch_bytes(int n, int Q, int sms);

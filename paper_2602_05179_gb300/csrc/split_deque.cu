@@ -854,23 +854,25 @@ __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
 
 // Single tour, TMEM staging (cost + streamed predecessors).  One CTA per SM
 // (its dynamic shared memory request guarantees it) allocates all 512 TMEM
-// columns; warp w < 16 holds its tile in lane quadrant w % 4, column block
-// w / 4 of cols_per_warp columns.  XW more warps stage their tiles in shared
-// memory (rows of row_stride bytes) with the same records: more warps per SM
-// hide more of the deque's dependent latencies, and the TMEM alone holds 16
-// tiles.
+// columns; warp w < tmem_warps holds its tile in lane quadrant w % 4, column
+// block w / 4 of cols_per_warp columns.  Any further warps stage their tiles
+// in shared memory (rows of row_stride bytes) with the same records.  XW
+// sizes the launch bounds (512 + 32 XW threads): the default launch has 16
+// TMEM warps; the wide one 17..24 (XW = 8, every warp in TMEM, fewer
+// columns each), taken when that many finish every tile in one round.
 template <typename QT, typename PT, int RING, int OUT, int XW>
 __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDequeArgs a,
                                                                      int64_t tiles,
                                                                      int cols_per_warp,
-                                                                     int row_stride) {
+                                                                     int row_stride,
+                                                                     int tmem_warps) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t tmem_base;
   const int n = a.n, Q = a.Q;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const bool in_tmem = warp < 16;
+  const bool in_tmem = warp < tmem_warps;
 
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
@@ -975,10 +977,10 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
 // 4 uint8 / 2 uint16 positions), then each lane walks its own scenario's
 // optimal routes back from position n and counts route starts / ends in
 // shared-memory histograms.  The CTA holds blockDim.x / 32 = 16..24 warps:
-// a launch chooses the count that takes every tile in the fewest rounds
-// (the DP is bound by dependent latencies, so a fuller SM costs little and a
-// second, partly empty round costs a whole row's time).  Warp w holds its
-// tile in TMEM lane quadrant w % 4, column block w / 4 of cols_per_warp.
+// more than 16 when that many take every tile in one round where 16 would
+// need two (a second, partly empty round costs a whole row's time).  Warp w
+// holds its tile in TMEM lane quadrant w % 4, column block w / 4 of
+// cols_per_warp.
 template <typename QT, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) split_tmem_adj_kernel(SplitDequeArgs a,
                                                                  int64_t tiles,
@@ -1345,14 +1347,21 @@ size_t stage_bytes_for(int pred_bytes, int ns) {
   const int pitch = pred_bytes == 2 ? stage_pitch<uint16_t>() : stage_pitch<int32_t>();
   return (((size_t)ns * 32 * pitch * pred_bytes) + 15) & ~(size_t)15;
 }
-// TMEM single-tour launch: 16 warps with 128 TMEM columns each, plus
-// kTmemExtraWarps warps staging in shared memory when their rows fit.
-// Measured at n = 500, S = 10^6: one scenario per lane with 16 warps (2.07 ms)
-// beats two per lane with 8 warps (2.72 ms) -- the DP is bound by dependent
-// latencies, which more warps hide better than two chains per thread.
+// TMEM single-tour launch: 16 warps with 128 TMEM columns each.  Measured at
+// n = 500, S = 10^6: one scenario per lane with 16 warps (2.07 ms) beats two
+// per lane with 8 warps (2.72 ms) -- the DP is bound by dependent latencies,
+// which more warps hide better than two chains per thread -- and 4 more warps
+// staging in shared memory (96 registers each) gained nothing.  When 17..24
+// warps take every tile in one round where 16 would need two (16 to 24 tiles
+// per SM) and the rows fit their share of the columns, the launch is that
+// wide instead.
 constexpr int kTmemColsPerWarp = 128;
-constexpr int kTmemExtraWarps = 0;
+constexpr int kTmemMaxWarps = 24;
+constexpr int kWideXW = kTmemMaxWarps - 16;  // launch bounds of the wide kernels
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
+// TMEM columns of each warp when nw warps share the 512 (nw / 4 rounded up
+// warps per lane quadrant), in whole 4-column stores
+int tmem_cols_per_warp(int nw) { return nw <= 16 ? kTmemColsPerWarp : (512 / ((nw + 3) / 4)) & ~3; }
 }  // namespace
 
 DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_bytes,
@@ -1369,13 +1378,8 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
   if (c.tmem) {
     const size_t base = ((size_t)n + 2) * sizeof(StepRec);
     const size_t per_warp = ring_bytes(ring) + stage_bytes_for(pred_bytes, 1);
-    c.warps = 16 + kTmemExtraWarps;
-    size_t need = base + (size_t)c.warps * per_warp +
-                  (size_t)kTmemExtraWarps * 32 * c.row_stride;
-    if (need > kMaxSmemPerCta) {
-      c.warps = 16;
-      need = base + (size_t)c.warps * per_warp;
-    }
+    c.warps = 16;
+    const size_t need = base + (size_t)c.warps * per_warp;
     c.smem = need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
     return c;
   }
@@ -1391,6 +1395,18 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
   while (warps == 0 && c.warps > 1 && off + (size_t)c.warps * per_warp > kMaxSmemPerCta) --c.warps;
   c.smem = off + (size_t)c.warps * per_warp;
   return c;
+}
+
+DequeConfig deque_config_wide(const DequeConfig& c, int n, int Q, int64_t S, bool direct_ok,
+                              int sms) {
+  if (!c.tmem || c.ring != 16 || !direct_ok) return c;
+  const int nw = split_tmem_adj_warps(n, Q, S, sms);
+  if (nw <= 16) return c;
+  DequeConfig w = c;
+  w.warps = nw;
+  const size_t need = ((size_t)n + 2) * sizeof(StepRec) + (size_t)nw * ring_bytes(16);
+  w.smem = need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
+  return w;
 }
 
 namespace {
@@ -1418,10 +1434,14 @@ int launch_t(const SplitDequeArgs& a, const DequeConfig& c, int grid, cudaStream
     // predecessors stored 4 per lane when every row segment is aligned
     const bool direct = OUT == kOutStream && (a.n & 3) == 0 &&
                         (reinterpret_cast<uintptr_t>(a.pred) & 15) == 0;
-    auto k = direct ? (c.warps > 16 ? split_tmem_kernel<QT, PT, RING, kOutDirect, kTmemExtraWarps>
-                                    : split_tmem_kernel<QT, PT, RING, kOutDirect, 0>)
-                    : (c.warps > 16 ? split_tmem_kernel<QT, PT, RING, OUT, kTmemExtraWarps>
-                                    : split_tmem_kernel<QT, PT, RING, OUT, 0>);
+    // wide launch (17..24 warps, deque_config_wide): 16-entry rings, direct
+    // or no predecessors
+    const bool wide = c.warps > 16;
+    if (wide && (RING != 16 || (OUT == kOutStream && !direct))) return (int)cudaErrorInvalidValue;
+    auto k = wide ? (direct ? split_tmem_kernel<QT, PT, 16, kOutDirect, kWideXW>
+                            : split_tmem_kernel<QT, int32_t, 16, kOutNone, kWideXW>)
+                  : (direct ? split_tmem_kernel<QT, PT, RING, kOutDirect, 0>
+                            : split_tmem_kernel<QT, PT, RING, OUT, 0>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)c.smem);
     if (e != cudaSuccess) return (int)e;
@@ -1431,7 +1451,8 @@ int launch_t(const SplitDequeArgs& a, const DequeConfig& c, int grid, cudaStream
       return (int)e;
     }
     const int64_t tiles = (a.S + 31) / 32;
-    k<<<grid, c.warps * 32, c.smem, st>>>(a, tiles, kTmemColsPerWarp, c.row_stride);
+    k<<<grid, c.warps * 32, c.smem, st>>>(a, tiles, tmem_cols_per_warp(c.warps), c.row_stride,
+                                          c.warps);
     return (int)cudaGetLastError();
   }
   const int64_t tiles = (a.S + 31) / 32;
@@ -1546,42 +1567,32 @@ int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int grid, 
 }
 
 // ---- fused adjoint with TMEM staging
-namespace {
-constexpr int kAdjMaxWarps = 24;
-// TMEM columns of each warp when nw warps share the 512 (nw / 4 rounded up
-// warps per lane quadrant), in whole 4-column stores
-int adj_cols_per_warp(int nw) { return (512 / ((nw + 3) / 4)) & ~3; }
-}  // namespace
 
 int split_tmem_adj_warps(int n, int Q, int64_t S, int sms) {
   if (n < 1 || S < 1 || sms < 1 || !deque_supported(n, Q)) return 0;
   const int words = tmem_row_words(n, Q <= 254 ? 1 : 2);
-  if (words > adj_cols_per_warp(16)) return 0;
+  if (words > tmem_cols_per_warp(16)) return 0;
   const int64_t tiles = (S + 31) / 32;
-  // fewest rounds of tiles over the SMs; the smallest such warp count
-  int best = 16;
-  int64_t best_rounds = (tiles + 16LL * sms - 1) / (16LL * sms);
-  for (int nw = 17; nw <= kAdjMaxWarps; ++nw) {
-    if (words > adj_cols_per_warp(nw)) break;
-    const int64_t r = (tiles + (int64_t)nw * sms - 1) / ((int64_t)nw * sms);
-    if (r < best_rounds) {
-      best_rounds = r;
-      best = nw;
-    }
-  }
-  return best;
+  // 17..24 warps only when they take every tile in one round where 16 need
+  // two: a wide round (80 registers a thread) costs more than a 16-warp one,
+  // so over several rounds fewer of them did not pay (n = 300 forward: 0.148
+  // -> 0.125 ms at 10^5 scenarios, one round; 0.240 -> 0.249 ms at 2 10^5
+  // and 0.99 -> 1.10 ms at 10^6, fewest rounds at 21..23 warps)
+  const int64_t nw = (tiles + sms - 1) / sms;
+  if (nw <= 16 || nw > kTmemMaxWarps || words > tmem_cols_per_warp((int)nw)) return 16;
+  return (int)nw;
 }
 
 size_t split_tmem_adj_scratch_bytes(int n, int Q, int sms) {
   const int per = Q <= 254 ? 4 : 2;
-  return (size_t)sms * kAdjMaxWarps * (size_t)((n + per - 1) / per) * 32 * sizeof(uint32_t);
+  return (size_t)sms * kTmemMaxWarps * (size_t)((n + per - 1) / per) * 32 * sizeof(uint32_t);
 }
 
 namespace {
 template <typename QT>
 int launch_adj_t(const SplitDequeArgs& a, int nw, uint32_t* dscratch, int sms,
                  cudaStream_t st) {
-  auto k = nw <= 16 ? split_tmem_adj_kernel<QT, 512> : split_tmem_adj_kernel<QT, 32 * kAdjMaxWarps>;
+  auto k = nw <= 16 ? split_tmem_adj_kernel<QT, 512> : split_tmem_adj_kernel<QT, 32 * kTmemMaxWarps>;
   size_t smem = ((size_t)a.n + 2) * sizeof(StepRec) + (((size_t)(2 * a.n + 1) * 4 + 15) & ~(size_t)15) +
                 (size_t)nw * ring_bytes(16);
   if (smem < kOneCtaPerSmSmem) smem = kOneCtaPerSmSmem;  // one TMEM owner per SM
@@ -1591,14 +1602,14 @@ int launch_adj_t(const SplitDequeArgs& a, int nw, uint32_t* dscratch, int sms,
   const int64_t tiles = (a.S + 31) / 32;
   const int64_t ctas = (tiles + nw - 1) / nw;
   const int grid = (int)(ctas < sms ? ctas : sms);
-  k<<<grid, 32 * nw, smem, st>>>(a, tiles, adj_cols_per_warp(nw), dscratch);
+  k<<<grid, 32 * nw, smem, st>>>(a, tiles, tmem_cols_per_warp(nw), dscratch);
   return (int)cudaGetLastError();
 }
 }  // namespace
 
 int launch_split_tmem_adj(const SplitDequeArgs& a, int warps, uint32_t* dscratch, int sms,
                           cudaStream_t st) {
-  if (warps < 16 || warps > kAdjMaxWarps || !a.hist || !dscratch) return (int)cudaErrorInvalidValue;
+  if (warps < 16 || warps > kTmemMaxWarps || !a.hist || !dscratch) return (int)cudaErrorInvalidValue;
   if (a.Q <= 254) return launch_adj_t<uint8_t>(a, warps, dscratch, sms, st);
   return launch_adj_t<uint16_t>(a, warps, dscratch, sms, st);
 }

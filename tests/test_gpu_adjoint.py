@@ -133,16 +133,15 @@ def _sms():
 
 
 @pytest.mark.parametrize("case", [
-    # (seed, n, Q, tiles per SM): the TMEM adjoint takes 16 warps per SM up to
-    # 16 tiles per SM, else as many (up to 24, as the row fits) as finish in
-    # the fewest rounds
+    # (seed, n, Q, tiles per SM): the TMEM adjoint takes 16 warps per SM,
+    # 17..24 when that many (as the row fits) finish every tile in one round
     (7, 17, 40, 0.5),      # n % 4 = 1, under one round
     (8, 300, 120, 20.6),   # 21 warps, one round
     (9, 300, 120, 24.0),   # 24 warps, exactly one round
     (10, 350, 120, 18.0),  # 88-word rows: at most 20 warps
     (11, 200, 300, 19.5),  # uint16 rows (Q >= 255), 100 words
     (12, 450, 150, 17.0),  # 113-word rows: 16 warps, two rounds
-    (13, 301, 120, 49.3),  # several rounds at 17..24 warps
+    (13, 301, 120, 49.3),  # beyond one round of 24: 16 warps, four rounds
 ])
 def test_adjoint_tmem_equals_shared_staging(case):
     """The TMEM adjoint (default shape) and the shared-memory one (4 warps

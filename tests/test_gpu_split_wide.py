@@ -1,0 +1,84 @@
+"""GPU parity of the wide TMEM Split launch: below a few 10^5 scenarios the
+default DEQUE launch takes 17..24 warps per SM (every one staging its tile in
+tensor memory, fewer columns each) when that finishes every 32-scenario tile
+in one round where 16 warps would need two.  Same DP steps as the shared-memory launch
+(bit-identical costs and predecessors) and the oracle's results on sampled
+scenarios."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_05179_gb300 import workloads as wl
+from tests.gpu_util import check_split
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def sdp():
+    from paper_2602_05179_gb300 import api
+    return api
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("case", [
+    # (seed, n, Q, tiles per SM, preds): warps per SM the launch takes
+    (1, 300, 120, 20.6, "u16"),   # 21, uint8 rows, predecessors 4 per lane
+    (2, 336, 120, 24.0, "i32"),   # 24, the longest uint8 row 24 warps hold
+    (3, 350, 120, 18.0, "none"),  # 18 (88-word rows: at most 20 warps)
+    (4, 200, 300, 19.5, "u16"),   # 20, uint16 rows
+    (5, 301, 120, 20.0, "u16"),   # n % 4 = 1 with predecessors: 16 warps, two rounds
+    (6, 301, 120, 20.0, "none"),  # n % 4 = 1 without: 20 warps
+    (7, 64, 80, 50.0, "u16"),     # beyond one round of 24: 16 warps
+])
+def test_wide_launch_equals_shared_staging_and_oracle(case):
+    seed, n, Q, tps, preds = case
+    S = int(tps * _sms() * 32) - 7
+    spec = wl.SplitSpec(f"wide{seed}", n, Q, S, seed, "poisson", lam=10.0 if Q < 255 else 25.0,
+                        lo=1, hi=Q)
+    tour, xy, _ = wl.split_tour(spec)
+    qd = wl.split_demands_device(spec)
+    t, c = _cuda(tour), _cuda(xy)
+    pk = {} if preds == "none" else {"preds": preds}
+    a = sdp().split_eval(t, Q, qd, coords=c, algo="deque", **pk)
+    b = sdp().split_eval(t, Q, qd, coords=c, algo="deque", warps=4, **pk)
+    torch.cuda.synchronize()
+    assert torch.equal(a["cost"], b["cost"])
+    if preds != "none":
+        assert torch.equal(a["pred"], b["pred"])
+    assert sdp().status() & (sdp().FLAG_FALLBACK | sdp().FLAG_INFEASIBLE) == 0
+    rows = np.sort(np.random.default_rng(seed).choice(S, 200, replace=False))
+    rows = np.concatenate([rows, [0, S - 1]])
+    q = np.concatenate([wl.split_demands(spec, int(s), int(s) + 1) for s in rows])
+    orc = oracle.split(tour, Q, q, coords=xy, want_margin=True)
+    check_split(a["cost"], a.get("pred"), orc, rows=rows, min_checked=0.0)
+
+
+def test_wide_launch_with_over_capacity_and_zero_demands():
+    """Tiles with a demand above Q (clamped staging, infeasible scenarios) and
+    with zero demands take the wide launch's general paths."""
+    n, Q = 240, 100
+    S = int(21.5 * _sms() * 32)
+    rng = np.random.default_rng(8)
+    xy = np.vstack([[50.0, 50.0], rng.uniform(0, 100, (n, 2))]).astype(np.float32)
+    tour = (rng.permutation(n) + 1).astype(np.int32)
+    q = rng.integers(0, 25, size=(S, n)).astype(np.int32)
+    q[5, 17] = Q + 1
+    q[S - 1, 0] = 900
+    t, c, qd = _cuda(tour), _cuda(xy), _cuda(q)
+    a = sdp().split_eval(t, Q, qd, coords=c, algo="deque", preds="u16")
+    b = sdp().split_eval(t, Q, qd, coords=c, algo="deque", preds="u16", warps=4)
+    torch.cuda.synchronize()
+    assert torch.equal(a["cost"], b["cost"]) and torch.equal(a["pred"], b["pred"])
+    assert np.isinf(a["cost"][5].item()) and np.isinf(a["cost"][S - 1].item())
+    rows = np.array([0, 5, 77, S // 2, S - 1])
+    orc = oracle.split(tour, Q, q[rows], coords=xy, want_margin=True)
+    check_split(a["cost"], a["pred"], orc, rows=rows, min_checked=0.0)
+    sdp().status()
