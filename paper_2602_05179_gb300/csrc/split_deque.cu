@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const bool in_tmem = warp < tmem_warps;
+  const bool in_tmem = XW == 0 || warp < tmem_warps;  // the 16-warp launch: every warp
 
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
