@@ -17,6 +17,8 @@
 // j in [-P, U] (P = 32; for j < -P the linear tail e(j) = p (-j) is evaluated
 // directly).  Decisions are warp ballots, one 32-bit word per (t, k), kept in
 // shared memory for the backtrack.
+#include <climits>
+
 #include <math_constants.h>
 
 #include "sdp_internal.cuh"
@@ -187,6 +189,8 @@ __global__ void __launch_bounds__(512) reinsert_kernel(ReinsertArgs a) {
 // Decisions stay ballot bits (deliver or not); the backtrack recomputes the
 // route that carried each delivery (the cheapest feasible one, the first on
 // ties) and writes r + 1 to the policy.  Linear end-of-day costs only.
+constexpr int kUnrolledRoutes = 8;
+
 template <int KC, bool UNIT>
 __global__ void __launch_bounds__(512) reinsert_routes_kernel(ReinsertArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -211,13 +215,16 @@ __global__ void __launch_bounds__(512) reinsert_routes_kernel(ReinsertArgs a) {
 
   const float h = a.h, p = a.p, c = a.c;
   float eI[KC], cq[KC];
-  int qk[KC];  // q = U - I of each slot
+  // route r carries the refill q = U - I of slot k iff its capacity is at
+  // least qmin[k]: q itself, or INT_MAX where there is nothing to deliver
+  // (q <= 0), so one compare per (route, slot) decides
+  int qmin[KC];
 #pragma unroll
   for (int k = 0; k < KC; ++k) {
     const int I = lane + 32 * k;
     eI[k] = __fmul_rn(h, (float)min(I, U));
     cq[k] = UNIT ? __fmul_rn(c, (float)(U - I)) : 0.f;
-    qk[k] = U - I;
+    qmin[k] = U - I >= 1 ? U - I : INT_MAX;
   }
   const float eneg = __fmul_rn(p, (float)(kPad - lane));
   bool neg = false;
@@ -248,16 +255,33 @@ __global__ void __launch_bounds__(512) reinsert_routes_kernel(ReinsertArgs a) {
         return __fadd_rn(C0n, __fmul_rn(p, (float)(-j)));
       };
       const float gUd = gat(U - d);
-      // cheapest route that holds q (q >= 1; +inf when none does)
+      // cheapest route that holds q (q >= 1; +inf when none does).  Up to
+      // kUnrolledRoutes routes the loop is unrolled: a compare and a
+      // predicated min per route and slot.
       float fb[KC];
 #pragma unroll
       for (int k = 0; k < KC; ++k) fb[k] = CUDART_INF_F;
-      for (int r = 0; r < K; ++r) {
-        const float fr = rcost_sm[t * K + r];
-        const int cr = capsm[t * K + r];
+      const float* frow = rcost_sm + t * K;
+      const int* crow = capsm + t * K;
+      if (K <= kUnrolledRoutes) {
 #pragma unroll
-        for (int k = 0; k < KC; ++k)
-          if (qk[k] >= 1 && cr >= qk[k]) fb[k] = fminf(fb[k], fr);
+        for (int r = 0; r < kUnrolledRoutes; ++r) {
+          if (r < K) {
+            const float fr = frow[r];
+            const int cr = crow[r];
+#pragma unroll
+            for (int k = 0; k < KC; ++k)
+              if (cr >= qmin[k]) fb[k] = fminf(fb[k], fr);
+          }
+        }
+      } else {
+        for (int r = 0; r < K; ++r) {
+          const float fr = frow[r];
+          const int cr = crow[r];
+#pragma unroll
+          for (int k = 0; k < KC; ++k)
+            if (cr >= qmin[k]) fb[k] = fminf(fb[k], fr);
+        }
       }
       uint32_t w[KC];
 #pragma unroll
