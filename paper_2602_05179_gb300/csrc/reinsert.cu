@@ -284,14 +284,28 @@ __global__ void __launch_bounds__(512) reinsert_routes_kernel(ReinsertArgs a) {
         }
       }
       uint32_t w[KC];
+      // one branch per day (d is warp-uniform): the direct shared loads when
+      // every state's I - d stays inside the buffer's negative margin
+      if (d <= kPad) {
 #pragma unroll
-      for (int k = 0; k < KC; ++k) {
-        const float nd = d <= kPad ? Gn[lane + 32 * k - d + kPad] : gat(lane + 32 * k - d);
-        float dv = __fadd_rn(fb[k], gUd);
-        if (UNIT) dv = __fadd_rn(dv, cq[k]);
-        const bool dec = dv < nd;
-        C[k] = dec ? dv : nd;
-        w[k] = __ballot_sync(0xffffffffu, dec);
+        for (int k = 0; k < KC; ++k) {
+          const float nd = Gn[lane + 32 * k - d + kPad];
+          float dv = __fadd_rn(fb[k], gUd);
+          if (UNIT) dv = __fadd_rn(dv, cq[k]);
+          const bool dec = dv < nd;
+          C[k] = dec ? dv : nd;
+          w[k] = __ballot_sync(0xffffffffu, dec);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+          const float nd = gat(lane + 32 * k - d);
+          float dv = __fadd_rn(fb[k], gUd);
+          if (UNIT) dv = __fadd_rn(dv, cq[k]);
+          const bool dec = dv < nd;
+          C[k] = dec ? dv : nd;
+          w[k] = __ballot_sync(0xffffffffu, dec);
+        }
       }
       if (lane == 0) {
         uint32_t* row = bits + t * BS;
