@@ -349,6 +349,8 @@ int sdp_saa_search_run(sdp_saa_search* s, int32_t iters, double* trace_out,
  * neighbour k.  Before any iteration the means are not defined. */
 int sdp_saa_search_state(sdp_saa_search* s, int32_t* tour_out, double* means_out,
                          void* stream);
+/* sizeof(sdp_saa_search_desc) as compiled into the library (binding checks). */
+size_t sdp_saa_search_desc_size(void);
 /* sdp_plan_autotune on the search's plan, deque rings of 16 entries only:
  * the tours change as the search goes, and a ring sized on the first ones can
  * overflow on later, better tours (longer monotone runs in the deque), whose

@@ -290,6 +290,8 @@ int sdp_saa_search_state(sdp_saa_search* s, int32_t* tour_out, double* means_out
   return SDP_OK;
 }
 
+size_t sdp_saa_search_desc_size(void) { return sizeof(sdp_saa_search_desc); }
+
 int sdp_saa_search_autotune(sdp_saa_search* s, void* stream, const char* cache_path) {
   if (!s) return sfail(SDP_ERR_INVALID_ARG, "search is NULL");
   return plan_autotune(s->plan, stream, cache_path, 16);

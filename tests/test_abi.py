@@ -33,7 +33,8 @@ def test_header_declares_the_operators():
     d = declared()
     for must in ("sdp_split_eval", "sdp_split_backward", "sdp_reinsert_eval",
                  "sdp_split_plan_create", "sdp_plan_run", "sdp_plan_autotune",
-                 "sdp_split_count_arcs", "sdp_device_status"):
+                 "sdp_split_count_arcs", "sdp_device_status", "sdp_saa_search_create",
+                 "sdp_saa_search_run", "sdp_saa_search_state", "sdp_saa_search_destroy"):
         assert must in d
 
 
@@ -48,8 +49,39 @@ def test_struct_layouts(lib):
     lib.sdp_reinsert_args_size.restype = ctypes.c_size_t
     assert lib.sdp_split_args_size() == ctypes.sizeof(api.SplitArgs)
     assert lib.sdp_reinsert_args_size() == ctypes.sizeof(api.ReinsertArgs)
+    lib.sdp_saa_search_desc_size.restype = ctypes.c_size_t
+    assert lib.sdp_saa_search_desc_size() == ctypes.sizeof(api.SaaSearchDesc)
     lib.sdp_version.restype = ctypes.c_int
     assert lib.sdp_version() == 1
+
+
+def test_search_argument_checks_on_the_host(lib):
+    """sdp_saa_search_create rejects bad descriptors before touching a
+    device; host pointers are not device pointers."""
+    from paper_2602_05179_gb300 import api
+    lib.sdp_saa_search_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.sdp_saa_search_create.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    assert lib.sdp_saa_search_create(None, ctypes.byref(h)) == -1
+    buf = (ctypes.c_int32 * 64)()
+
+    def desc(**kw):
+        d = api.SaaSearchDesc()
+        d.n, d.Q, d.S, d.B, d.moves, d.seed = 10, 30, 4, 8, 7, 1
+        d.coords = d.demands = d.tour0 = ctypes.addressof(buf)
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+    for kw, code in ((dict(n=1), -5), (dict(n=4096), -5), (dict(B=0), -1), (dict(S=0), -1),
+                     (dict(moves=0), -1), (dict(moves=8), -1), ({}, -1)):
+        assert lib.sdp_saa_search_create(ctypes.byref(desc(**kw)), ctypes.byref(h)) == code, kw
+        assert not h.value
+    lib.sdp_saa_search_run.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+    lib.sdp_saa_search_run.restype = ctypes.c_int
+    assert lib.sdp_saa_search_run(None, 1, None, None, None) == -1
+    lib.sdp_saa_search_destroy.argtypes = [ctypes.c_void_p]
+    lib.sdp_saa_search_destroy(None)
 
 
 def test_workspace_query_is_host_only(lib):
