@@ -145,18 +145,6 @@ struct TmemQ {
   }
 };
 
-// Shared-memory row read through the TMEM records (col = 32-bit word, pad =
-// byte-permute selector), for the extra shared-memory warps of the TMEM kernel.
-template <typename QT>
-struct SmemWordQ {
-  const uint32_t* row;
-  uint32_t word;
-  __device__ __forceinline__ void prefetch(const StepRec& r) { word = row[r.col]; }
-  __device__ __forceinline__ int take(const StepRec& r) {
-    return (int)__byte_perm(word, 0u, r.pad);
-  }
-};
-
 struct TileFlags {
   uint32_t inf_rows;  // rows with a demand above Q
   bool zero;          // some demand <= 0 in the tile (routes may exceed 255)
@@ -854,25 +842,22 @@ __global__ void __launch_bounds__(256, 1) split_deque_kernel(SplitDequeArgs a,
 
 // Single tour, TMEM staging (cost + streamed predecessors).  One CTA per SM
 // (its dynamic shared memory request guarantees it) allocates all 512 TMEM
-// columns; warp w < tmem_warps holds its tile in lane quadrant w % 4, column
-// block w / 4 of cols_per_warp columns.  Any further warps stage their tiles
-// in shared memory (rows of row_stride bytes) with the same records.  XW
-// sizes the launch bounds (512 + 32 XW threads): the default launch has 16
-// TMEM warps; the wide one 17..24 (XW = 8, every warp in TMEM, fewer
-// columns each), taken when that many finish every tile in one round.
+// columns; warp w holds its tile in lane quadrant w % 4, column block w / 4
+// of cols_per_warp columns.  XW sizes the launch bounds (512 + 32 XW
+// threads): the default launch has 16 warps (XW = 0, two steps per loop
+// iteration); the wide one 17..24 (XW = 8, fewer columns each, 80 registers a
+// thread: one step per iteration, smaller ingest batches), taken when that
+// many finish every tile in one round.
 template <typename QT, typename PT, int RING, int OUT, int XW>
 __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDequeArgs a,
                                                                      int64_t tiles,
-                                                                     int cols_per_warp,
-                                                                     int row_stride,
-                                                                     int tmem_warps) {
+                                                                     int cols_per_warp) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t tmem_base;
   const int n = a.n, Q = a.Q;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const bool in_tmem = XW == 0 || warp < tmem_warps;  // the 16-warp launch: every warp
 
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
@@ -889,10 +874,6 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
   uint2* ring_pl = reinterpret_cast<uint2*>(wbase);
   uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + RING * 32);
   PT* stage = reinterpret_cast<PT*>(ring_idx + RING * 32);
-  QT* qb = in_tmem ? nullptr
-                   : reinterpret_cast<QT*>(smem + off + per_warp * nwarps +
-                                           (size_t)(warp - 16) * 32 * row_stride);
-  const int rs_elems = row_stride / (int)sizeof(QT);
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
@@ -912,39 +893,22 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
     float K;
     PT* pred_tile = a.pred ? reinterpret_cast<PT*>(a.pred) + s0 * n : nullptr;
     const int prow = pred_tile ? rows : 0;
-    TileFlags tf;
-    // 20 warps leave 96 registers per thread: no unrolling, fewer loads in flight
     constexpr int UNR = XW == 0 ? 2 : 1;
-    if (XW == 0 || in_tmem) {
-      using Src = TmemQ<QT>;
-      tf = ingest_tile_tmem<QT, XW == 0 ? 16 : 8>(tsrc, rows, n, Q, taddr, lane);
-      Src src{taddr, 0u};
-      if (tf.inf_rows)
-        dp_rows<1, QT, PT, RING, OUT, true, true, Src, UNR>(
-            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
-            false, &first_inf, &bad, &K);
-      else if (tf.small_loads)
-        dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR, true>(
-            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
-            false, &first_inf, &bad, &K);
-      else
-        dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR>(
-            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
-            false, &first_inf, &bad, &K);
-    } else {
-      using Src = SmemWordQ<QT>;
-      tf = ingest_tile<QT>(tsrc, rows, n, rs_elems, Q, qb, lane);
-      __syncwarp();
-      Src src{reinterpret_cast<const uint32_t*>(qb + lane * rs_elems), 0u};
-      if (tf.inf_rows)
-        dp_rows<1, QT, PT, RING, OUT, true, true, Src, UNR>(
-            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
-            false, &first_inf, &bad, &K);
-      else
-        dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR>(
-            &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
-            false, &first_inf, &bad, &K);
-    }
+    using Src = TmemQ<QT>;
+    const TileFlags tf = ingest_tile_tmem<QT, XW == 0 ? 16 : 8>(tsrc, rows, n, Q, taddr, lane);
+    Src src{taddr, 0u};
+    if (tf.inf_rows)
+      dp_rows<1, QT, PT, RING, OUT, true, true, Src, UNR>(
+          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
+          false, &first_inf, &bad, &K);
+    else if (tf.small_loads)
+      dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR, true>(
+          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
+          false, &first_inf, &bad, &K);
+    else
+      dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR>(
+          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
+          false, &first_inf, &bad, &K);
     neg |= tf.neg;
     const bool valid = lane < rows;
     bad = bad && valid;
@@ -1451,8 +1415,7 @@ int launch_t(const SplitDequeArgs& a, const DequeConfig& c, int grid, cudaStream
       return (int)e;
     }
     const int64_t tiles = (a.S + 31) / 32;
-    k<<<grid, c.warps * 32, c.smem, st>>>(a, tiles, tmem_cols_per_warp(c.warps), c.row_stride,
-                                          c.warps);
+    k<<<grid, c.warps * 32, c.smem, st>>>(a, tiles, tmem_cols_per_warp(c.warps));
     return (int)cudaGetLastError();
   }
   const int64_t tiles = (a.S + 31) / 32;
