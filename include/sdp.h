@@ -332,7 +332,13 @@ typedef struct sdp_saa_search_desc {
 
 typedef struct sdp_saa_search sdp_saa_search;
 /* Allocates the search (its batched plan, B + 1 candidate tours, their costs
- * and means, the current tour); SDP_ERR_OOM if that fails.  The caller's
+ * and means, the current tour); SDP_ERR_OOM if that fails.  Errors:
+ * SDP_ERR_INVALID_ARG for a NULL desc / out, B, S or moves out of range, or
+ * coords / demands / tour0 not in device memory; SDP_ERR_UNSUPPORTED for n
+ * outside 2..2048 or Q outside 1..32767.  tour0 is not checked here: a
+ * customer id outside 1..n is read as customer 1 and raises
+ * SDP_FLAG_DEVICE_CHECK in the status word at the first run (a repeated id
+ * is not detected and scores a different tour).  The caller's
  * coords and demands must stay valid until destroy.  Uses the current
  * device; later calls must run with that device current.  A search is used
  * from one thread at a time (like a plan); its calls are ordered on the
