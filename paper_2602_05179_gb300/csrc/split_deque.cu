@@ -30,16 +30,20 @@
 //   demands per 32-bit column; the column of customer s_i is warp-uniform, so
 //   one tcgen05.ld.32x32b per step (issued a step ahead) delivers all 32
 //   demands.  Shared memory then holds only the deque rings, so 16 warps fit
-//   per SM instead of 8.
+//   per SM instead of 8 -- or 17..24 with fewer columns each when that many
+//   finish every tile in one round where 16 would need two.
 // (A bulk L2 prefetch of the next tile was measured: it raised DRAM reads from
 // 2.2 to 3.8 GB per launch at n = 500, S = 10^6 -- prefetched lines were
 // evicted before use -- for 3% less time, so tiles are read on demand, with
 // 16 loads in flight per lane in the tensor-memory ingest.)
 //
-// Outputs.  Predecessors are staged per 16 positions in a small shared buffer
-// and written as coalesced row segments.  The fused adjoint instead writes the
-// predecessor distance i - pred(i) in place over the consumed demand byte and
-// backtracks it on chip into shared-memory route start / end histograms.
+// Outputs.  Each lane stores its own predecessors 4 positions per store when
+// n % 4 == 0 and the rows are aligned; otherwise they are staged per 16
+// positions in a small shared buffer and written as coalesced row segments.
+// The fused adjoint keeps the predecessor distance i - pred(i) instead -- in
+// place over the consumed demand byte with shared-memory staging, in a
+// lane-interleaved global scratch with TMEM staging -- and backtracks it on
+// chip into shared-memory route start / end histograms.
 #include <math_constants.h>
 
 #include "sdp_internal.cuh"
