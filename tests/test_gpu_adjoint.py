@@ -217,3 +217,104 @@ def test_adjoint_tmem_uint16_rows_with_over_capacity_demands():
     np.testing.assert_array_equal(h[:n], start)
     np.testing.assert_array_equal(h[n:], end)
     sdp().status()  # the forward above flags the same infeasible scenarios
+
+
+def _path_positions(pred, n):
+    """Positions i visited by the backtrack from n (where pred(i) decides the
+    routes), per scenario."""
+    out = []
+    for row in pred:
+        i, pos = n, []
+        while i > 0:
+            pos.append(i)
+            i = int(row[i - 1])
+        out.append(pos)
+    return out
+
+
+def _tie_free(orc, n, margin=1e-4):
+    """Scenarios whose optimal routes are unique by more than `margin`
+    relative at every position the oracle's backtrack visits."""
+    keep = []
+    for s, pos in enumerate(_path_positions(orc["pred"], n)):
+        if all(orc["margin"][s, i - 1] > margin for i in pos):
+            keep.append(s)
+    return np.asarray(keep, np.int64)
+
+
+@pytest.mark.parametrize("case", [(21, 60, 4000, 80, 1e-4), (23, 300, 3000, 120, 1e-6)])
+@pytest.mark.parametrize("mode", ["fused", "pred_u16"])
+def test_adjoint_equals_oracle_splits_where_tie_free(case, mode):
+    """On the scenarios whose optimal routes are unique by more than `margin`
+    relative along the oracle's backtrack, the GPU adjoint's route start /
+    end counts equal those of the oracle's OWN optimal splits exactly, and
+    its gradient equals the oracle's arc-usage gradient to FP32 rounding.
+    1e-4 is the uniqueness the predecessor parity uses; at n = 300 no
+    scenario is unique by 1e-4 at every visited position (J(i) reaches 10^4,
+    so 1e-4 relative is about one distance unit), so that case takes 1e-6."""
+    seed, n, S, Q, margin = case
+    tour, dist, q = _case(seed, n, S, Q, 10.0)
+    orc = oracle.split(tour, Q, q, dist=dist, want_margin=True)
+    keep = _tie_free(orc, n, margin)
+    assert keep.size >= S // 8
+    qs = np.ascontiguousarray(q[keep])
+    op = np.ascontiguousarray(orc["pred"][keep])
+    start, end, skipped = oracle.split_route_counts(op)
+    assert skipped == 0
+    t, qd, dd = _cuda(tour), _cuda(qs), _cuda(dist)
+    gm = torch.tensor(1.0, device="cuda")
+    if mode == "fused":
+        g, hist = sdp().split_backward(t, Q, qd, dd, gm, want_hist=True)
+    else:
+        p = sdp().split_eval(t, Q, qd, dist=dd, preds="u16")["pred"]
+        g, hist = sdp().split_backward(t, Q, qd, dd, gm, pred=p, pred_dtype="u16",
+                                       want_hist=True)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy()
+    np.testing.assert_array_equal(h[:n], start)
+    np.testing.assert_array_equal(h[n:], end)
+    np.testing.assert_allclose(g.cpu().double().numpy(), oracle.split_mean_grad(tour, op),
+                               rtol=1e-6, atol=1e-9)
+
+
+def test_adjoint_equals_central_differences_of_the_oracle_mean():
+    """The GPU gradient (SplitMeanCost.backward) equals the central finite
+    difference, h = 1e-3 in FP32, of the FP64 oracle's scenario mean at every
+    checked entry of dist: the 3n structurally nonzero ones and 40 random
+    zero ones, where every scenario's optimal routes at +h and -h are those
+    at 0 (the mean is piecewise linear in dist, so the difference is exact
+    there up to rounding).  Scenarios are those whose optimal routes are
+    unique by more than 1e-4 relative, so the GPU's splits are the oracle's."""
+    n, S, Q = 60, 2000, 80
+    tour, dist, q = _case(22, n, S, Q, 10.0)
+    orc = oracle.split(tour, Q, q, dist=dist, want_margin=True)
+    keep = _tie_free(orc, n)
+    assert keep.size >= S // 8
+    q = np.ascontiguousarray(q[keep])
+    base = oracle.split(tour, Q, q, dist=dist)
+    routes0 = _path_positions(base["pred"], n)
+    d = _cuda(dist).requires_grad_(True)
+    m = sdp().SplitMeanCost.apply(d, _cuda(tour), _cuda(q), Q)
+    m.backward()
+    torch.cuda.synchronize()
+    g = d.grad.cpu().double().numpy()
+    assert abs(float(m.detach()) - base["mean"]) <= 1e-5 * abs(base["mean"])
+    rng = np.random.default_rng(22)
+    entries = [(0, int(c)) for c in tour] + [(int(c), 0) for c in tour]
+    entries += [(int(a), int(b)) for a, b in zip(tour[:-1], tour[1:])]
+    entries += [tuple(int(v) for v in rng.integers(1, n + 1, 2)) for _ in range(40)]
+    h = np.float32(1e-3)
+    checked = 0
+    for (a, b) in entries:
+        dp = dist.copy(); dp[a, b] += h
+        dm = dist.copy(); dm[a, b] -= h
+        rp = oracle.split(tour, Q, q, dist=dp)
+        rm = oracle.split(tour, Q, q, dist=dm)
+        if not (_path_positions(rp["pred"], n) == routes0 and
+                _path_positions(rm["pred"], n) == routes0):
+            continue  # a tie within h: the gradient is not defined there
+        step = float(dp[a, b]) - float(dm[a, b])  # the FP32 perturbation applied
+        fd = (rp["mean"] - rm["mean"]) / step
+        assert g[a, b] == pytest.approx(fd, rel=1e-6, abs=1e-7), (a, b)
+        checked += 1
+    assert checked >= 0.9 * len(entries)

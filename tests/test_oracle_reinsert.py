@@ -131,3 +131,29 @@ def test_reinsert_forward_equals_backward_on_workload_sample():
         assert v == pytest.approx(r["value"][s], rel=1e-12)
     assert np.all(np.isfinite(r["value0"]))
     assert abs(r["mean"] - r["value"].mean()) <= 1e-12 * r["mean"]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_reinsert_margin_by_brute_force(seed):
+    """The margin at (t, I) -- the relative gap between the two actions,
+    which decides where the GPU's policy is compared bit for bit -- equals
+    |v1 - v0| / max(|v0|, |v1|) for the values of delivering (v1) and not
+    delivering (v0) at (t, I) with every later day optimal, both found by
+    simulating every continuation; +inf where only one action exists (I = U)."""
+    rng = np.random.default_rng(2600 + seed)
+    T = int(rng.integers(1, 6))
+    U = int(rng.integers(1, 9))
+    h, p, c, fixed = _rand_params(rng, T, U)
+    H = rng.uniform(0.5, 20, size=U + 1) if seed % 3 == 2 else None
+    cons = rng.integers(0, U + 3, size=T).astype(np.int32)
+    r = oracle.reinsert(T, U, 0, h, p, c, fixed, cons[None, :], H=H, want_margin=True)
+    mg = r["margin"][0]
+    for t in range(T):
+        for I in range(U + 1):
+            v = brute.reinsert_action_values(T, U, h, p, c, fixed, cons, t, I, H=H)
+            if I == U:
+                assert list(v) == [0] and math.isinf(mg[t, I])
+                continue
+            den = max(abs(v[0]), abs(v[1]))
+            expect = abs(v[1] - v[0]) / den if den > 0 else 0.0
+            assert mg[t, I] == pytest.approx(expect, rel=1e-9, abs=1e-12), (t, I)

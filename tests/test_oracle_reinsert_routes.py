@@ -92,3 +92,31 @@ def test_more_routes_never_cost_more_and_ties_take_the_first():
     np.testing.assert_array_equal(a["value"], b["value"])
     np.testing.assert_array_equal(a["policy"], b["policy"])
     assert not math.isnan(float(b["mean"]))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_routes_margin_by_brute_force(seed):
+    """The margin at (t, I) equals (second - best) / max(|best|, |second|)
+    over the values of every allowed action at (t, I) -- no delivery, or a
+    route whose capacity holds U - I -- with every later day optimal, found
+    by simulating every continuation; +inf where a single action exists."""
+    rng = np.random.default_rng(760 + seed)
+    T = int(rng.integers(1, 5))
+    U = int(rng.integers(1, 8))
+    K = int(rng.integers(1, 4))
+    uc = float(rng.choice([0.0, 0.6]))
+    cons, rcost, cap = _case(rng, 1, T, U, K, lam=float(rng.uniform(0.5, 5)))
+    H = rng.uniform(0.5, 9, U + 1) if seed % 3 == 0 else None
+    o = oracle.reinsert_routes(T, U, 0, 1.0, 7.0, uc, rcost, cap, cons, H=H, want_margin=True)
+    mg = o["margin"][0]
+    for t in range(T):
+        for I in range(U + 1):
+            v = brute.reinsert_action_values(T, U, 1.0, 7.0, uc, None, cons[0], t, I, H=H,
+                                             rcost=rcost, cap=cap[0])
+            vals = sorted(v.values())
+            if len(vals) < 2:
+                assert math.isinf(mg[t, I]), (t, I)
+                continue
+            den = max(abs(vals[0]), abs(vals[1]))
+            expect = (vals[1] - vals[0]) / den if den > 0 else 0.0
+            assert mg[t, I] == pytest.approx(expect, rel=1e-9, abs=1e-12), (t, I)

@@ -121,3 +121,26 @@ def test_soft_split_large_penalty_reaches_hard_optimum():
     h = oracle.split(tour, Q, q, coords=xy)
     s = oracle.split_soft(tour, Q, beta, q, coords=xy)
     np.testing.assert_allclose(s["cost"], h["cost"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_soft_split_margin_by_brute_force(seed):
+    """The margin of each position (relative gap between the best and the
+    second-best predecessor, which decides where the GPU's predecessors are
+    compared bit for bit) equals the gap between the two smallest candidate
+    values of J(i), each built by brute force over the prefix splits."""
+    rng = np.random.default_rng(5600 + seed)
+    n = int(rng.integers(2, 9))
+    Q = int(rng.integers(3, 30))
+    beta = float(rng.choice([0.0, 0.7, 4.0, 50.0]))
+    dist_mode = bool(seed % 2)
+    tour, xy, d, q = _instance(rng, n, qmax=Q + 5, dist_mode=dist_mode)
+    cost = (lambda a, b: float(d[a, b])) if dist_mode else (lambda a, b: brute.euclid(xy, a, b))
+    r = oracle.split_soft(tour, Q, beta, q[None, :], coords=xy, dist=d, want_margin=True)
+    for i in range(1, n + 1):
+        vals = sorted(v for v, _ in brute.split_candidates(list(tour), list(q), Q, cost, i, beta))
+        m = r["margin"][0][i - 1]
+        if len(vals) < 2:
+            assert math.isinf(m)
+        else:
+            assert m == pytest.approx((vals[1] - vals[0]) / abs(vals[0]), rel=1e-9, abs=1e-12), i
