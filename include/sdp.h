@@ -100,6 +100,14 @@ const char* sdp_last_error(void);
  * SDP_ERR_INVALID_ARG if exactly one is NULL. */
 int sdp_set_profile_events(void* start, void* stop);
 
+/* Launch shape of the DP kernel of the calling thread's last sdp_split_eval
+ * or sdp_split_backward call: warps per CTA and CTAs (0, 0 for the STREAM
+ * path, whose CTAs mix producer and DP warps; 0, 0 before any call).  The
+ * shape is chosen from n, Q, S and the SM count, so a test can check that
+ * the launch it means to exercise is the one that ran.  Host-side only;
+ * always SDP_OK. */
+int sdp_last_launch(int32_t* warps_per_cta_out, int32_t* ctas_out);
+
 /* Reads (and with clear != 0 resets) the status word of the current device.
  * Synchronises the device.  *flags_out receives SDP_FLAG_* bits. */
 int sdp_device_status(int clear, uint32_t* flags_out);
@@ -194,9 +202,22 @@ int sdp_split_eval(const sdp_split_args* a, void* stream);
  *   - Calls whose workspace (sdp_split_workspace_bytes) exceeds that size are
  *     rejected with SDP_ERR_UNSUPPORTED and nothing is launched (at n = 500,
  *     algo DEQUE, about 2 million scenarios fit; algo PLAIN needs more).
+ *     The scratch holds the workspace of sdp_split_workspace_bytes, whose
+ *     large terms are: the plain kernel's fallback rows, (n+1) * min(S,4096)
+ *     * 4 bytes (above 16 MiB from n = 1023 on, so DEQUE calls with
+ *     S >= 4096 and long rows are rejected there); 4 * S bytes of fallback
+ *     list; STREAM's tour-ordered rows, S * (n + 48) bytes or so (AUTO takes
+ *     STREAM for n > 512); and with demands in page-locked host memory two
+ *     staging buffers of min(S, 65536) * n * 4 bytes each (rejected from
+ *     n = 32 on at S >= 65536).  Give such calls a workspace through
+ *     sdp_split_eval instead.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture.
+ *     (cudaGetSymbolAddress, with that device current) and caches it for
+ *     the life of the process; make that first call before any stream
+ *     capture.  The cached address belongs to the device's primary context:
+ *     after cudaDeviceReset on that device the next call would pass a stale
+ *     address, so do not use this entry point across a device reset (the
+ *     status word that every entry point uses is cached the same way).
  *   - All calls share the one array and it keeps the last call's contents;
  *     each call resets what must start at zero (the fallback counter).  Calls
  *     that overlap on the GPU (other streams, other host threads) race on it:
@@ -340,7 +361,8 @@ typedef struct sdp_saa_search sdp_saa_search;
  * SDP_FLAG_DEVICE_CHECK in the status word at the first run (a repeated id
  * is not detected and scores a different tour).  The caller's
  * coords and demands must stay valid until destroy.  Uses the current
- * device; later calls must run with that device current.  A search is used
+ * device; later calls must run with that device current (run and state
+ * return SDP_ERR_INVALID_ARG otherwise, launching nothing).  A search is used
  * from one thread at a time (like a plan); its calls are ordered on the
  * stream they are given. */
 int sdp_saa_search_create(const sdp_saa_search_desc* d, sdp_saa_search** out);

@@ -95,6 +95,7 @@ def _load():
             "sdp_reinsert_workspace_bytes": ([P], sz),
             "sdp_reinsert_eval": ([P, P], i32),
             "sdp_set_profile_events": ([P, P], i32),
+            "sdp_last_launch": ([P, P], i32),
             "sdp_split_plan_create": ([P, P], i32),
             "sdp_plan_autotune": ([P, P, ctypes.c_char_p], i32),
             "sdp_plan_run": ([P, P], i32),
@@ -170,6 +171,14 @@ def set_profile_events(start, stop):
     sp = None if start is None else start.cuda_event
     ep = None if stop is None else stop.cuda_event
     _check(_load().sdp_set_profile_events(sp, ep))
+
+
+def last_launch():
+    """(warps per CTA, CTAs) of the DP kernel of this thread's last Split
+    evaluation or adjoint call; (0, 0) for the streaming path."""
+    w, c = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(_load().sdp_last_launch(ctypes.byref(w), ctypes.byref(c)))
+    return int(w.value), int(c.value)
 
 
 def status(clear: bool = True) -> int:

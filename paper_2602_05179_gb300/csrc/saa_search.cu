@@ -40,6 +40,13 @@ namespace {
 
 bool is_device_ptr(const void* p) { return api_device_ptr(p); }
 
+// The search's buffers and the caller's stream belong to the device that was
+// current at creation; run and state need it current again.
+bool on_own_device(const sdp_saa_search* s) {
+  int d = -1;
+  return cudaGetDevice(&d) == cudaSuccess && d == s->device;
+}
+
 int sfail(int code, const char* msg) { return api_fail(code, msg); }
 
 int scuda(cudaError_t e, const char* what) {
@@ -251,6 +258,7 @@ int sdp_saa_search_create(const sdp_saa_search_desc* d, sdp_saa_search** out) {
 int sdp_saa_search_run(sdp_saa_search* s, int32_t iters, double* trace_out,
                        int32_t* accepted_out, void* stream) {
   if (!s) return sfail(SDP_ERR_INVALID_ARG, "search is NULL");
+  if (!on_own_device(s)) return sfail(SDP_ERR_INVALID_ARG, "the search's device is not current");
   if (iters < 0) return sfail(SDP_ERR_INVALID_ARG, "iters < 0");
   if (trace_out && !is_device_ptr(trace_out))
     return sfail(SDP_ERR_INVALID_ARG, "trace_out must be a device pointer");
@@ -276,6 +284,7 @@ int sdp_saa_search_run(sdp_saa_search* s, int32_t iters, double* trace_out,
 int sdp_saa_search_state(sdp_saa_search* s, int32_t* tour_out, double* means_out,
                          void* stream) {
   if (!s) return sfail(SDP_ERR_INVALID_ARG, "search is NULL");
+  if (!on_own_device(s)) return sfail(SDP_ERR_INVALID_ARG, "the search's device is not current");
   if (!tour_out || !is_device_ptr(tour_out))
     return sfail(SDP_ERR_INVALID_ARG, "tour_out must be a device pointer");
   if (means_out && !is_device_ptr(means_out))

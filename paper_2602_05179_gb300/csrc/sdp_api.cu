@@ -28,6 +28,13 @@ void prof_end(cudaStream_t st) {
   if (g_prof_stop) cudaEventRecord(g_prof_stop, st);
   g_prof_start = g_prof_stop = nullptr;
 }
+// Launch shape of the dominant kernel of the calling thread's last operator
+// call (sdp_last_launch).
+thread_local int32_t g_last_warps = 0, g_last_ctas = 0;
+void note_launch(int warps, int ctas) {
+  g_last_warps = warps;
+  g_last_ctas = ctas;
+}
 
 int fail(int code, const char* fmt, ...) {
   va_list ap;
@@ -374,6 +381,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     sa.tflags = w.tflags; sa.cost = cost; sa.pred = pred; sa.pred_dtype = a->pred_dtype;
     sa.fb_list = w.fb_list; sa.fb_count = w.fb_count; sa.status = status;
     sa.ctas_per_sm = 0;
+    note_launch(0, 0);
     prof_begin(st);  // both kernels of the path: pre-pass + DP
     const int e = launch_split_stream(sa, st);
     prof_end(st);
@@ -386,6 +394,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     d.rec = w.prep.rec; d.cols = w.prep.cols; d.Dn = w.prep.Dn;
     d.demands = a->demands; d.cost = nullptr; d.pred = nullptr; d.pred_dtype = a->pred_dtype;
     d.hist = hist; d.fb_list = w.fb_list; d.fb_count = w.fb_count; d.status = status;
+    note_launch(adj_warps, sms);
     prof_begin(st);
     const int e = launch_split_tmem_adj(d, adj_warps, w.dscratch, sms, st);
     prof_end(st);
@@ -417,6 +426,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     d.demands = a->demands; d.cost = cost; d.pred = pred; d.pred_dtype = a->pred_dtype;
     d.hist = hist; d.fb_list = w.fb_list; d.fb_count = w.fb_count; d.status = status;
     d.soft = a->capacity_mode == SDP_CAPACITY_SOFT; d.beta = a->overload_penalty;
+    note_launch(warps, grid);
     prof_begin(st);
     e = launch_split_deque(d, cfg, grid, st);
     prof_end(st);
@@ -432,7 +442,10 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
   p.fb_count = w.fb_count; p.status = status;
   p.soft = a->capacity_mode == SDP_CAPACITY_SOFT; p.beta = a->overload_penalty;
   const int grid = (int)((w.nslots + 255) / 256);
-  if (algo == SDP_ALGO_PLAIN) prof_begin(st);
+  if (algo == SDP_ALGO_PLAIN) {
+    note_launch(8, grid);
+    prof_begin(st);
+  }
   launch_split_plain(p, grid, st);
   if (algo == SDP_ALGO_PLAIN) prof_end(st);
   cudaError_t e = cudaGetLastError();
@@ -476,6 +489,11 @@ int sdp_set_profile_events(void* start, void* stop) {
     return fail(SDP_ERR_INVALID_ARG, "give both events or neither");
   g_prof_start = static_cast<cudaEvent_t>(start);
   g_prof_stop = static_cast<cudaEvent_t>(stop);
+  return SDP_OK;
+}
+int sdp_last_launch(int32_t* warps_per_cta_out, int32_t* ctas_out) {
+  if (warps_per_cta_out) *warps_per_cta_out = g_last_warps;
+  if (ctas_out) *ctas_out = g_last_ctas;
   return SDP_OK;
 }
 size_t sdp_reinsert_args_size(void) { return sizeof(sdp_reinsert_args); }

@@ -29,17 +29,17 @@ def _sms():
 
 
 @pytest.mark.parametrize("case", [
-    # (seed, n, Q, tiles per SM, preds): warps per SM the launch takes
-    (1, 300, 120, 20.6, "u16"),   # 21, uint8 rows, predecessors 4 per lane
-    (2, 336, 120, 24.0, "i32"),   # 24, the longest uint8 row 24 warps hold
-    (3, 350, 120, 18.0, "none"),  # 18 (88-word rows: at most 20 warps)
-    (4, 200, 300, 19.5, "u16"),   # 20, uint16 rows
-    (5, 301, 120, 20.0, "u16"),   # n % 4 = 1 with predecessors: 16 warps, two rounds
-    (6, 301, 120, 20.0, "none"),  # n % 4 = 1 without: 20 warps
-    (7, 64, 80, 50.0, "u16"),     # beyond one round of 24: 16 warps
+    # (seed, n, Q, tiles per SM, preds, warps per SM the launch takes)
+    (1, 300, 120, 20.6, "u16", 21),   # uint8 rows, predecessors 4 per lane
+    (2, 336, 120, 24.0, "i32", 24),   # the longest uint8 row 24 warps hold
+    (3, 350, 120, 18.0, "none", 18),  # 88-word rows: at most 20 warps
+    (4, 200, 300, 19.5, "u16", 20),   # uint16 rows
+    (5, 301, 120, 20.0, "u16", 16),   # n % 4 = 1 with predecessors: two rounds
+    (6, 301, 120, 20.0, "none", 20),  # n % 4 = 1 without
+    (7, 64, 80, 50.0, "u16", 16),     # beyond one round of 24
 ])
 def test_wide_launch_equals_shared_staging_and_oracle(case):
-    seed, n, Q, tps, preds = case
+    seed, n, Q, tps, preds, warps = case
     S = int(tps * _sms() * 32) - 7
     spec = wl.SplitSpec(f"wide{seed}", n, Q, S, seed, "poisson", lam=10.0 if Q < 255 else 25.0,
                         lo=1, hi=Q)
@@ -48,7 +48,9 @@ def test_wide_launch_equals_shared_staging_and_oracle(case):
     t, c = _cuda(tour), _cuda(xy)
     pk = {} if preds == "none" else {"preds": preds}
     a = sdp().split_eval(t, Q, qd, coords=c, algo="deque", **pk)
+    assert sdp().last_launch()[0] == warps  # the launch this case means to exercise
     b = sdp().split_eval(t, Q, qd, coords=c, algo="deque", warps=4, **pk)
+    assert sdp().last_launch()[0] == 4
     torch.cuda.synchronize()
     assert torch.equal(a["cost"], b["cost"])
     if preds != "none":
@@ -58,7 +60,11 @@ def test_wide_launch_equals_shared_staging_and_oracle(case):
     rows = np.concatenate([rows, [0, S - 1]])
     q = np.concatenate([wl.split_demands(spec, int(s), int(s) + 1) for s in rows])
     orc = oracle.split(tour, Q, q, coords=xy, want_margin=True)
-    check_split(a["cost"], a.get("pred"), orc, rows=rows, min_checked=0.0)
+    # at n >= 200, J(i) is large and 35-60% of positions are unique by 1e-4
+    # relative; FP32 errors of the K-form (< 1e-7 relative) also allow
+    # comparing every position unique by 1e-5 (75-88%)
+    check_split(a["cost"], a.get("pred"), orc, rows=rows, min_checked=0.3)
+    check_split(a["cost"], a.get("pred"), orc, rows=rows, margin=1e-5, min_checked=0.7)
 
 
 def test_wide_launch_with_over_capacity_and_zero_demands():
@@ -74,6 +80,7 @@ def test_wide_launch_with_over_capacity_and_zero_demands():
     q[S - 1, 0] = 900
     t, c, qd = _cuda(tour), _cuda(xy), _cuda(q)
     a = sdp().split_eval(t, Q, qd, coords=c, algo="deque", preds="u16")
+    assert sdp().last_launch()[0] == 22
     b = sdp().split_eval(t, Q, qd, coords=c, algo="deque", preds="u16", warps=4)
     torch.cuda.synchronize()
     assert torch.equal(a["cost"], b["cost"]) and torch.equal(a["pred"], b["pred"])

@@ -46,7 +46,14 @@ def _noalloc(tour, Q, demands, coords=None, dist=None, preds=True):
 
 
 def test_noalloc_rejects_oversize_without_touching_the_device():
-    api, lib = _lib()
+    from paper_2602_05179_gb300 import api
+    import os
+    if not os.path.exists(api.lib_path()):
+        pytest.skip("libsdp.so is not built")
+    try:
+        api, lib = _lib()
+    except OSError as e:  # a library that does not load here (no CUDA runtime)
+        pytest.skip(f"libsdp.so does not load: {e}")
     a = api.SplitArgs()
     a.n, a.Q, a.S, a.algo = 500, 200, 100_000_000, 0
     rc = lib.sdp_split_eval_noalloc(ctypes.byref(a), None)
@@ -91,3 +98,22 @@ def test_noalloc_matches_eval_two_calls_in_a_row():
     assert np.array_equal(preds_to_i64(pred2), preds_to_i64(ref2["pred"]))
     assert np.isinf(float(mean2)) == np.isinf(float(ref2["mean"]))
     api.status()
+
+
+@pytest.mark.gpu
+def test_noalloc_rejects_host_demands_beyond_the_scratch():
+    """Page-locked host demands need two staging buffers of min(S, 65536) * n
+    int32 each: at n = 64 and S = 65536 they alone exceed the scratch, so the
+    call is rejected before anything is launched."""
+    api, lib = _lib()
+    n, S = 64, 65536
+    rng = np.random.default_rng(9)
+    xy = np.concatenate([[[50, 50]], rng.uniform(0, 100, (n, 2))]).astype(np.float32)
+    tour = torch.from_numpy((rng.permutation(n) + 1).astype(np.int32)).cuda()
+    q = torch.ones((S, n), dtype=torch.int32).pin_memory()
+    cost = torch.empty(S, dtype=torch.float32, device="cuda")
+    a = api._split_struct(tour, 100, q, torch.from_numpy(xy).cuda(), None, cost, None, 0,
+                          "auto", None, 0, 0)
+    rc = lib.sdp_split_eval_noalloc(ctypes.byref(a), None)
+    assert rc == SDP_ERR_UNSUPPORTED
+    assert b"no-allocation scratch" in lib.sdp_last_error()
