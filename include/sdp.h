@@ -400,10 +400,10 @@ void sdp_saa_search_destroy(sdp_saa_search* s);
 #define SDP_REINSERT_AUTO 0  /* WARP (measured faster at T = 60, U = 200) */
 #define SDP_REINSERT_WARP 1  /* one warp per scenario, states across lanes */
 #define SDP_REINSERT_LANE 2  /* one lane per scenario, its cost-to-go in shared
-                                memory; needs U <= 255 (and T <= 768 at
-                                U >= 224); with a policy, its decision bits
-                                take workspace (SMs x 7 x T x ceil((U+1)/32)
-                                x 128 bytes) */
+                                memory (up to 8 warps per SM); needs U <= 255;
+                                with a policy, its decision bits take
+                                workspace (SMs x 8 x T x ceil((U+1)/32) x 128
+                                bytes) */
 typedef struct sdp_reinsert_args {
   int32_t T;                  /* 1 <= T; T * W <= 4096 where W = 8 for
                                  U < 256, 16 for U < 512, 32 for U < 1024

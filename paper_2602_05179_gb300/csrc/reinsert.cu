@@ -371,19 +371,29 @@ __global__ void __launch_bounds__(512) reinsert_routes_kernel(ReinsertArgs a) {
 // scenario s0 + l on its own (no ballots, shuffles or per-warp decision
 // stores).  Its G_{t+1} lives in shared memory laid out [state I][lane]
 // (every access of the warp hits 32 banks whatever the lanes' consumptions)
-// and is overwritten in place by G_t: the states are visited from U down to 0
-// in batches of 32, and a state's no-delivery read G_{t+1}(I - d_t) is at an
-// index <= I, so it is never one the stage has already rewritten (d_t >= 0).
-// A batch issues its 32 reads before its writes (32 independent loads in
-// flight); the batches run in a loop (a fully unrolled stage of 224 states
-// overflowed the instruction cache).  When the policy is wanted, the decision
-// bits of a day (one 32-bit word per batch, bit j = state 32k + j) go to a
-// per-warp scratch slot in global memory, [t][k][lane] (coalesced stores,
-// small enough to stay in L2), and the backtrack reads its word back.
-// Needs U < 256; seven warps (one CTA) per SM, 28 KB of shared memory each.
-// The last stage (t = 0) stores C_0 rather than G_0 (its e is taken as 0),
-// so the value and the C_0 table are read straight from the buffer.
-constexpr int kLaneWarps = 7;
+// and is overwritten in place by G_t: the states are visited from the top
+// down in batches of 32, and a state's no-delivery read G_{t+1}(I - d_t) is at
+// an index <= I, so it is never one the stage has already rewritten
+// (d_t >= 0).  A batch issues its 32 reads before its writes (32 independent
+// loads in flight).  One batch body serves every batch of a day (batches
+// k >= 1 read indices >= 0 when every lane's consumption is at most 32; batch
+// 0, and every batch of a day where some lane consumes more, takes the
+// general body that reads the linear tail below 0), so the code stays small:
+// a fully unrolled stage of 224 states overflowed the instruction cache.
+// States above U are computed like the others and never read by a real
+// state (a read is at an index <= the state's own); their decision bits are
+// masked off, and at I = U (where delivering is q = 0) the decision is forced
+// to "no delivery" -- with f_t >= 0 the comparison already keeps it, and a
+// day with f_t < 0 rewrites state U after its batch.  When the policy is
+// wanted, the decision bits of a day (one 32-bit word per batch, bit j =
+// state 32k + j) go to a per-warp scratch slot in global memory, [t][k][lane]
+// (coalesced stores, small enough to stay in L2), and the backtrack reads its
+// word back.  The policy is stored four days per 32-bit word where rows allow.
+// Needs U < 256; up to eight warps (one CTA) per SM, (U + 1 rounded up to 32)
+// x 128 bytes of shared memory each.  The last stage (t = 0) stores C_0
+// rather than G_0 (its e is taken as 0), so the value and the C_0 table are
+// read straight from the buffer.
+constexpr int kLaneWarps = 8;
 template <bool B>
 struct BoolTag {
   static constexpr bool value = B;
@@ -393,7 +403,7 @@ template <int KC, bool TABLE, bool UNIT>
 __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(ReinsertArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NI = 32 * KC;  // state slots
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int T = a.T, U = a.U;
   // shared: fixed[T], table[NI] (TABLE), then per warp G[NI][32]
   float* fixed_sm = reinterpret_cast<float*>(smem);
@@ -407,12 +417,16 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
   __syncthreads();
 
   const float h = a.h, p = a.p, c = a.c;
-  const int64_t slot = (int64_t)blockIdx.x * kLaneWarps + warp;
+  const int64_t slot = (int64_t)blockIdx.x * nwarps + warp;
   // decision word (t, k) of this lane at dw[32 * (t * KC + k)]
   uint32_t* dw = a.policy ? a.dscratch + slot * (int64_t)T * KC * 32 + lane : nullptr;
+  // valid decision bits of the top batch: states below U
+  const uint32_t top_mask = (1u << (U & 31)) - 1u;
+  // policy rows of 4-byte multiples on an aligned base: four days per store
+  const bool pol4 = (T & 3) == 0 && (reinterpret_cast<uintptr_t>(a.policy) & 3) == 0;
   bool neg = false;
   const int64_t tiles = (a.S + 31) / 32;
-  for (int64_t tile = slot; tile < tiles; tile += (int64_t)gridDim.x * kLaneWarps) {
+  for (int64_t tile = slot; tile < tiles; tile += (int64_t)gridDim.x * nwarps) {
     const int64_t s0 = tile * 32;
     const bool live = lane < a.S - s0;
     const int32_t* crow = a.cons + (s0 + (live ? lane : 0)) * T;
@@ -422,9 +436,9 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
       return live ? max(d, 0) : 0;
     };
     // stage T: C_T = 0, G_T(I) = e(I)
-#pragma unroll
+#pragma unroll 8
     for (int I = 0; I < NI; ++I)
-      Gl[32 * I] = TABLE ? table_sm[I] : __fmul_rn(h, (float)min(I, NI - 1));
+      Gl[32 * I] = TABLE ? table_sm[I] : __fmul_rn(h, (float)I);
 
     int d_next = cons_at(T - 1);
     for (int t = T - 1; t >= 0; --t) {
@@ -436,18 +450,16 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
       // G_{t+1}(j), j < 0: table e(0) + C(0) = G(0); linear C(0) + p (-j)
       auto gneg = [&](int mj) -> float { return TABLE ? G0 : __fadd_rn(C0, __fmul_rn(p, (float)mj)); };
       const float gUd = d <= U ? Gl[32 * (U - d)] : gneg(d - U);
-      const float base = __fadd_rn(fixed_sm[t], gUd);
+      const float ft = fixed_sm[t];
+      const float base = __fadd_rn(ft, gUd);
       const float he = last ? 0.f : h;
-      // batches k >= 1 read at or above index 0 in every lane when d <= 32
-      const bool fast = __all_sync(0xffffffffu, d <= 32);
       const float* Gd = Gl - 32 * d;  // G_{t+1}(I - d) = Gd[32 * I] for I >= d
       // One batch of 32 states, I = 32k + j: its 32 reads first, then the
-      // updates.  TOP: the batch holding U (padding states above U are
-      // skipped, and delivering at U is no delivery).
-      auto batch = [&](int k, bool general, auto top_tag) -> uint32_t {
-        constexpr bool TOP = decltype(top_tag)::value;
+      // updates.  GENERAL: reads below index 0 take the linear tail.
+      auto batch = [&](int k, auto general_tag) -> uint32_t {
+        constexpr bool GENERAL = decltype(general_tag)::value;
         float v[32];
-        if (general) {
+        if (GENERAL) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int src_i = 32 * k + j - d;
@@ -459,35 +471,49 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
           for (int j = 0; j < 32; ++j) v[j] = Gd[32 * (32 * k + j)];
         }
         const float fk = (float)(32 * k);  // I = fk + j exactly
-        uint32_t w = 0u;
+        // four partial words: short dependency chains for the bit ORs
+        uint32_t w4[4] = {0u, 0u, 0u, 0u};
+        float* Gk = Gl + 32 * 32 * k;
 #pragma unroll
         for (int j = 31; j >= 0; --j) {
-          const int I = 32 * k + j;
-          if (TOP && I > U) continue;  // padding states
           float dv = base;
           if (UNIT) dv = __fadd_rn(base, __fmul_rn(c, (float)(U - 32 * k) - (float)j));
-          bool dec = dv < v[j];
-          if (TOP) dec = dec && I < U;  // at I = U delivering is q = 0
+          const bool dec = dv < v[j];
           const float C = dec ? dv : v[j];
-          const float e = TABLE ? (last ? 0.f : table_sm[I]) : __fmul_rn(he, fk + (float)j);
-          Gl[32 * I] = __fadd_rn(e, C);
-          if (dec) w |= 1u << j;
+          const float e = TABLE ? (last ? 0.f : table_sm[32 * k + j]) : __fmul_rn(he, fk + (float)j);
+          Gk[32 * j] = __fadd_rn(e, C);
+          if (dec) w4[j >> 3] |= 1u << j;
         }
-        return w;
+        return (w4[0] | w4[1]) | (w4[2] | w4[3]);
       };
-      // from the top down: a batch only reads indices below its own, which
-      // later batches have not rewritten yet
+      // from the top down: a batch only reads indices at or below its own,
+      // which later batches have not rewritten yet
       uint32_t* dwt = dw ? dw + 32 * t * KC : nullptr;
-      uint32_t w = batch(KC - 1, KC == 1 || !fast, BoolTag<true>{});
-      if (dwt) dwt[32 * (KC - 1)] = w;
+      uint32_t km = top_mask;  // mask of the batch being stored (the top one first)
+      if (__all_sync(0xffffffffu, d <= 32)) {
 #pragma unroll 1
-      for (int k = KC - 2; k >= 1; --k) {
-        w = batch(k, !fast, BoolTag<false>{});
-        if (dwt) dwt[32 * k] = w;
+        for (int k = KC - 1; k >= 1; --k) {
+          const uint32_t w = batch(k, BoolTag<false>{}) & km;
+          if (dwt) dwt[32 * k] = w;
+          km = ~0u;
+        }
+      } else {
+#pragma unroll 1
+        for (int k = KC - 1; k >= 1; --k) {
+          const uint32_t w = batch(k, BoolTag<true>{}) & km;
+          if (dwt) dwt[32 * k] = w;
+          km = ~0u;
+        }
       }
-      if (KC >= 2) {
-        w = batch(0, true, BoolTag<false>{});
+      {
+        const uint32_t w = batch(0, BoolTag<true>{}) & km;
         if (dwt) dwt[0] = w;
+      }
+      // at I = U delivering is q = 0: no delivery, C = G_{t+1}(U - d).  The
+      // comparison chose it unless f_t < 0.
+      if (ft < 0.f) {
+        const float eU = TABLE ? (last ? 0.f : table_sm[U]) : __fmul_rn(he, (float)U);
+        Gl[32 * U] = __fadd_rn(eU, gUd);
       }
     }
     // value, optional C_0 table (the buffer holds C_0 now)
@@ -499,10 +525,20 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
     // backtrack: decision of the day at the path's state; deliver -> U
     if (dw) {
       int I = a.I0;
+      uint8_t* prow = a.policy + (s0 + lane) * T;
+      uint32_t pw = 0u;
       for (int t = 0; t < T; ++t) {
         const uint32_t wd = dw[32 * (t * KC + (I >> 5))];
         const int dec = (int)((wd >> (I & 31)) & 1u);
-        if (live) a.policy[(s0 + lane) * T + t] = (uint8_t)dec;
+        if (pol4) {
+          pw |= (uint32_t)dec << (8 * (t & 3));
+          if ((t & 3) == 3) {
+            if (live) *reinterpret_cast<uint32_t*>(prow + (t - 3)) = pw;
+            pw = 0u;
+          }
+        } else if (live) {
+          prow[t] = (uint8_t)dec;
+        }
         I = max((dec ? U : I) - cons_at(t), 0);
       }
     }
@@ -556,14 +592,15 @@ int by_kc(const ReinsertArgs& a, cudaStream_t st) {
 template <int KC, bool TABLE, bool UNIT>
 int launch_lane_kc(const ReinsertArgs& a, cudaStream_t st) {
   auto k = reinsert_lane_kernel<KC, TABLE, UNIT>;
-  const size_t smem = reinsert_lane_smem(a.T, a.U, TABLE);
-  if (smem > 227 * 1024) return (int)cudaErrorInvalidValue;
+  const int warps = reinsert_lane_warps(a.T, a.U, TABLE);
+  if (warps < 1) return (int)cudaErrorInvalidValue;
+  const size_t smem = reinsert_lane_smem_for(a.T, a.U, TABLE, warps);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int64_t tiles = (a.S + 31) / 32;
-  const int64_t need = (tiles + kLaneWarps - 1) / kLaneWarps;
+  const int64_t need = (tiles + warps - 1) / warps;
   const int grid = (int)imin64(need, (int64_t)num_sms());
-  if (grid > 0) k<<<grid, kLaneWarps * 32, smem, st>>>(a);
+  if (grid > 0) k<<<grid, warps * 32, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -619,15 +656,25 @@ int lane_by_kc(const ReinsertArgs& a, cudaStream_t st) {
 }
 }  // namespace
 
+size_t reinsert_lane_smem_for(int T, int U, bool table, int warps) {
+  const int NI = 32 * ((U + 1 + 31) / 32);
+  return (((size_t)T * 4 + 15) & ~(size_t)15) + (table ? (size_t)NI * 4 : 0) +
+         (size_t)warps * NI * 32 * 4;
+}
+
+// Warps per CTA (one CTA per SM): as many as the shared memory holds, up to 8.
+int reinsert_lane_warps(int T, int U, bool table) {
+  int w = kLaneWarps;
+  while (w > 0 && reinsert_lane_smem_for(T, U, table, w) > 227 * 1024) --w;
+  return w;
+}
+
 bool reinsert_lane_supported(int T, int U) {
-  return U >= 0 && U < 256 && T >= 1 && T <= 4096 &&
-         reinsert_lane_smem(T, U, true) <= 227 * 1024;
+  return U >= 0 && U < 256 && T >= 1 && T <= 4096 && reinsert_lane_warps(T, U, true) >= 4;
 }
 
 size_t reinsert_lane_smem(int T, int U, bool table) {
-  const int NI = 32 * ((U + 1 + 31) / 32);
-  return (((size_t)T * 4 + 15) & ~(size_t)15) + (table ? (size_t)NI * 4 : 0) +
-         (size_t)kLaneWarps * NI * 32 * 4;
+  return reinsert_lane_smem_for(T, U, table, reinsert_lane_warps(T, U, table));
 }
 
 size_t reinsert_lane_scratch_bytes(int T, int U) {

@@ -268,6 +268,8 @@ int launch_reinsert(const ReinsertArgs& a, cudaStream_t st);
 // decision scratch it needs when the policy is wanted
 bool reinsert_lane_supported(int T, int U);
 size_t reinsert_lane_smem(int T, int U, bool table);
+size_t reinsert_lane_smem_for(int T, int U, bool table, int warps);
+int reinsert_lane_warps(int T, int U, bool table);
 size_t reinsert_lane_scratch_bytes(int T, int U);
 
 int num_sms();
