@@ -368,64 +368,124 @@ __global__ void __launch_bounds__(512) reinsert_routes_kernel(ReinsertArgs a) {
 
 // ------------------------------------------------------- one scenario per lane
 // reinsert_lane_kernel: the same recursion with lane l of a warp running
-// scenario s0 + l on its own (no ballots, shuffles or per-warp decision
-// stores).  Its G_{t+1} lives in shared memory laid out [state I][lane]
-// (every access of the warp hits 32 banks whatever the lanes' consumptions)
-// and is overwritten in place by G_t: the states are visited from the top
-// down in batches of 32, and a state's no-delivery read G_{t+1}(I - d_t) is at
-// an index <= I, so it is never one the stage has already rewritten
-// (d_t >= 0).  A batch issues its 32 reads before its writes (32 independent
-// loads in flight).  One batch body serves every batch of a day (batches
-// k >= 1 read indices >= 0 when every lane's consumption is at most 32; batch
-// 0, and every batch of a day where some lane consumes more, takes the
-// general body that reads the linear tail below 0), so the code stays small:
-// a fully unrolled stage of 224 states overflowed the instruction cache.
-// States above U are computed like the others and never read by a real
-// state (a read is at an index <= the state's own); their decision bits are
-// masked off, and at I = U (where delivering is q = 0) the decision is forced
-// to "no delivery" -- with f_t >= 0 the comparison already keeps it, and a
-// day with f_t < 0 rewrites state U after its batch.  When the policy is
-// wanted, the decision bits of a day (one 32-bit word per batch, bit j =
-// state 32k + j) go to a per-warp scratch slot in global memory, [t][k][lane]
-// (coalesced stores, small enough to stay in L2), and the backtrack reads its
-// word back.  The policy is stored four days per 32-bit word where rows allow.
-// Needs U < 256; up to eight warps (one CTA) per SM, (U + 1 rounded up to 32)
-// x 128 bytes of shared memory each.  The last stage (t = 0) stores C_0
-// rather than G_0 (its e is taken as 0), so the value and the C_0 table are
-// read straight from the buffer.
+// scenario s0 + l on its own (no ballots or shuffles).  Layout and order:
+//  - G_{t+1} lives in shared memory laid out [row][lane] (every access of the
+//    warp hits 32 banks whatever the lanes' consumptions), state I at row
+//    I + P with P = 32 KC - (U + 1), so the top row is state U and rows
+//    0 .. P-1 hold G_{t+1}(j) of the negative end-of-day inventories
+//    j = -P .. -1 (C_{t+1}(0) plus the stockout cost), written at the start of
+//    each day for the lanes' consumptions.
+//  - G is overwritten in place by G_t: the rows are visited from the top down
+//    in batches of 32, and a state's no-delivery read G_{t+1}(I - d_t) is at a
+//    row <= its own, so it is never one the stage has already rewritten
+//    (d_t >= 0).  A batch issues its 32 reads before its writes.
+//  - One batch body serves every batch of a day (reads at immediate offsets)
+//    while every lane's consumption is at most 32 (batch 0: at most P, with
+//    the reads of the P rows below state 0 clamped to the buffer); a day with
+//    more takes the general body, which evaluates the stockout tail.  Keeping
+//    the bodies few keeps the code small: a fully unrolled stage of 224 states
+//    overflowed the instruction cache.
+//  - e(I) comes from a CTA-wide row-indexed table (four rows per broadcast
+//    load), a table of zeros in the last stage, which stores C_0 rather than
+//    G_0, so the value and the C_0 table are read straight from the buffer.
+//  - Bit j of decision word k is row 32 k + j; the bits of the P rows below
+//    state 0 are never read, and at I = U (where delivering is q = 0) the
+//    decision is forced to "no delivery" -- with f_t >= 0 the comparison
+//    already keeps it, and a day with f_t < 0 rewrites state U after its
+//    batch.  When the policy is wanted the words of a day go to a per-warp
+//    scratch slot in global memory, [tile parity][t][k][lane] (coalesced
+//    stores), and the backtrack of a tile runs one day per stage day of the
+//    next tile (the last tile's after its stage loop), so its dependent reads
+//    of the words come back while the next tile computes.  The policy is
+//    stored four days per 32-bit word where rows allow.
+// Needs U < 256; up to eight warps (one CTA) per SM, 32 KC x 128 bytes of
+// shared memory each.
 constexpr int kLaneWarps = 8;
-template <bool B>
-struct BoolTag {
-  static constexpr bool value = B;
+template <int M>
+struct IntTag {
+  static constexpr int value = M;
 };
 
 template <int KC, bool TABLE, bool UNIT>
 __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(ReinsertArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NI = 32 * KC;  // state slots
+  constexpr int NI = 32 * KC;  // rows
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int T = a.T, U = a.U;
-  // shared: fixed[T], table[NI] (TABLE), then per warp G[NI][32]
-  float* fixed_sm = reinterpret_cast<float*>(smem);
-  size_t off = ((size_t)T * 4 + 15) & ~(size_t)15;
-  float* table_sm = reinterpret_cast<float*>(smem + off);
-  if (TABLE) off += (size_t)NI * 4;
+  const int P = NI - (U + 1);  // rows below state 0
+  // shared: etab[NI] (e of each row), ztab[32] zeros, ptab[33] (p m for
+  // m = 0..32), fixed[T], then per warp G[NI][32]
+  float* etab = reinterpret_cast<float*>(smem);
+  float* ztab = etab + NI;
+  float* ptab = ztab + 32;
+  float* fixed_sm = ptab + 36;
+  const size_t off = (((size_t)NI + 32 + 36 + (size_t)T) * 4 + 15) & ~(size_t)15;
   float* Gl = reinterpret_cast<float*>(smem + off) + (size_t)warp * NI * 32 + lane;
+  const float h = a.h, p = a.p, c = a.c;
+  for (int r = threadIdx.x; r < NI; r += blockDim.x) {
+    const int I = r - P;
+    etab[r] = I < 0 ? 0.f : (TABLE ? __ldg(a.table + I) : __fmul_rn(h, (float)I));
+  }
+  for (int m = threadIdx.x; m < 32; m += blockDim.x) ztab[m] = 0.f;
+  for (int m = threadIdx.x; m < 36; m += blockDim.x) ptab[m] = __fmul_rn(p, (float)m);
   for (int t = threadIdx.x; t < T; t += blockDim.x) fixed_sm[t] = __ldg(a.fixed + t);
-  if (TABLE)
-    for (int i = threadIdx.x; i < NI; i += blockDim.x) table_sm[i] = __ldg(a.table + min(i, U));
   __syncthreads();
 
-  const float h = a.h, p = a.p, c = a.c;
   const int64_t slot = (int64_t)blockIdx.x * nwarps + warp;
-  // decision word (t, k) of this lane at dw[32 * (t * KC + k)]
-  uint32_t* dw = a.policy ? a.dscratch + slot * (int64_t)T * KC * 32 + lane : nullptr;
-  // valid decision bits of the top batch: states below U
-  const uint32_t top_mask = (1u << (U & 31)) - 1u;
+  // decision word (parity, t, k) of this lane at dw[32 * ((parity * T + t) * KC + k)]
+  uint32_t* dw = a.policy ? a.dscratch + slot * (int64_t)2 * T * KC * 32 + lane : nullptr;
   // policy rows of 4-byte multiples on an aligned base: four days per store
   const bool pol4 = (T & 3) == 0 && (reinterpret_cast<uintptr_t>(a.policy) & 3) == 0;
+  const float e0 = TABLE ? etab[P] : 0.f;  // e(j) for j <= 0 in table mode
   bool neg = false;
+
+  // ---- backtrack of a finished tile, one day at a time (see above)
+  struct Backtrack {
+    int I, t;        // path state at day t
+    uint32_t w;      // decision word of day t at I (loaded a day ahead)
+    uint32_t pw;     // policy bytes of the current 4-day group
+    int d;           // consumption of day t
+    const int32_t* crow;
+    uint8_t* prow;
+    const uint32_t* words;
+    bool live;
+  } bt;
+  bt.t = T;  // nothing to backtrack yet
+  bt.I = 0; bt.w = 0u; bt.pw = 0u; bt.d = 0; bt.crow = a.cons; bt.prow = nullptr;
+  bt.words = nullptr; bt.live = false;
+  auto bt_start = [&](const int32_t* crow, int64_t s, bool live, const uint32_t* words) {
+    bt.I = a.I0;
+    bt.t = 0;
+    bt.pw = 0u;
+    bt.crow = crow;
+    bt.prow = a.policy + s * T;
+    bt.words = words;
+    bt.live = live;
+    bt.w = words[32 * ((bt.I + P) >> 5)];
+    bt.d = live ? max(__ldg(crow), 0) : 0;
+  };
+  auto bt_day = [&]() {
+    const int t = bt.t;
+    const int dec = (int)((bt.w >> ((bt.I + P) & 31)) & 1u);
+    if (pol4) {
+      bt.pw |= (uint32_t)dec << (8 * (t & 3));
+      if ((t & 3) == 3) {
+        if (bt.live) *reinterpret_cast<uint32_t*>(bt.prow + (t - 3)) = bt.pw;
+        bt.pw = 0u;
+      }
+    } else if (bt.live) {
+      bt.prow[t] = (uint8_t)dec;
+    }
+    bt.I = max((dec ? U : bt.I) - bt.d, 0);
+    bt.t = t + 1;
+    if (t + 1 < T) {
+      bt.w = bt.words[32 * ((t + 1) * KC + ((bt.I + P) >> 5))];
+      bt.d = bt.live ? max(__ldg(bt.crow + t + 1), 0) : 0;
+    }
+  };
+
   const int64_t tiles = (a.S + 31) / 32;
+  int parity = 0;
   for (int64_t tile = slot; tile < tiles; tile += (int64_t)gridDim.x * nwarps) {
     const int64_t s0 = tile * 32;
     const bool live = lane < a.S - s0;
@@ -435,114 +495,115 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
       neg |= live && d < 0;
       return live ? max(d, 0) : 0;
     };
-    // stage T: C_T = 0, G_T(I) = e(I)
+    // stage T: C_T = 0, G_T = e (rows below state 0 are written per day)
 #pragma unroll 8
-    for (int I = 0; I < NI; ++I)
-      Gl[32 * I] = TABLE ? table_sm[I] : __fmul_rn(h, (float)I);
+    for (int r = 0; r < NI; ++r) Gl[32 * r] = etab[r];
+    uint32_t* dwp = dw ? dw + 32 * (int64_t)parity * T * KC : nullptr;
 
     int d_next = cons_at(T - 1);
     for (int t = T - 1; t >= 0; --t) {
       const int d = d_next;
       if (t > 0) d_next = cons_at(t - 1);  // one day ahead
+      if (bt.t < T) bt_day();              // the previous tile's path
       const bool last = t == 0;
-      const float G0 = Gl[0];  // G_{t+1}(0) = e(0) + C_{t+1}(0)
+      const float G0 = Gl[32 * P];  // G_{t+1}(0) = e(0) + C_{t+1}(0)
       const float C0 = TABLE ? 0.f : G0;  // linear mode: e(0) = 0
       // G_{t+1}(j), j < 0: table e(0) + C(0) = G(0); linear C(0) + p (-j)
       auto gneg = [&](int mj) -> float { return TABLE ? G0 : __fadd_rn(C0, __fmul_rn(p, (float)mj)); };
-      const float gUd = d <= U ? Gl[32 * (U - d)] : gneg(d - U);
+      const float gUd = d <= U ? Gl[32 * (U + P - d)] : gneg(d - U);
       const float ft = fixed_sm[t];
       const float base = __fadd_rn(ft, gUd);
-      const float he = last ? 0.f : h;
-      const float* Gd = Gl - 32 * d;  // G_{t+1}(I - d) = Gd[32 * I] for I >= d
-      // One batch of 32 states, I = 32k + j: its 32 reads first, then the
-      // updates.  GENERAL: reads below index 0 take the linear tail.
-      auto batch = [&](int k, auto general_tag) -> uint32_t {
-        constexpr bool GENERAL = decltype(general_tag)::value;
+      const float* et = last ? ztab : etab;
+      const int dmax = __reduce_max_sync(0xffffffffu, d);
+      // rows below state 0 that this day reads at immediate offsets:
+      // j = -1 .. -min(d, P)
+      if (dmax <= 32) {
+        const int mmax = min(dmax, P);
+        for (int m = 1; m <= mmax; ++m)
+          Gl[32 * (P - m)] = TABLE ? G0 : __fadd_rn(C0, ptab[m]);
+      }
+      // One batch of 32 rows r = 32k + j (state I = r - P): its 32 reads
+      // first, then the updates.  MODE 0: reads at immediate offsets; 1:
+      // reads clamped at row 0 (batch 0 with every d <= P); 2: general, the
+      // stockout tail evaluated below state 0.
+      auto batch = [&](int k, auto mode_tag) -> uint32_t {
+        constexpr int MODE = decltype(mode_tag)::value;
         float v[32];
-        if (GENERAL) {
+        if (MODE == 2) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int src_i = 32 * k + j - d;
-            const float g = Gl[32 * max(src_i, 0)];
-            v[j] = src_i >= 0 ? g : gneg(-src_i);
+            const int src = 32 * k + j - P - d;  // state read
+            const float g = Gl[32 * (max(src, 0) + P)];
+            v[j] = src >= 0 ? g : gneg(-src);
           }
+        } else if (MODE == 1) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = Gl[32 * max(32 * k + j - d, 0)];
         } else {
+          const float* Gd = Gl - 32 * d;
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = Gd[32 * (32 * k + j)];
         }
-        const float fk = (float)(32 * k);  // I = fk + j exactly
+        const float4* e4 = reinterpret_cast<const float4*>(et + (last ? 0 : 32 * k));
         // four partial words: short dependency chains for the bit ORs
         uint32_t w4[4] = {0u, 0u, 0u, 0u};
         float* Gk = Gl + 32 * 32 * k;
 #pragma unroll
-        for (int j = 31; j >= 0; --j) {
-          float dv = base;
-          if (UNIT) dv = __fadd_rn(base, __fmul_rn(c, (float)(U - 32 * k) - (float)j));
-          const bool dec = dv < v[j];
-          const float C = dec ? dv : v[j];
-          const float e = TABLE ? (last ? 0.f : table_sm[32 * k + j]) : __fmul_rn(he, fk + (float)j);
-          Gk[32 * j] = __fadd_rn(e, C);
-          if (dec) w4[j >> 3] |= 1u << j;
+        for (int q4 = 7; q4 >= 0; --q4) {
+          const float4 ev = e4[q4];
+          const float es[4] = {ev.x, ev.y, ev.z, ev.w};
+#pragma unroll
+          for (int u = 3; u >= 0; --u) {
+            const int j = 4 * q4 + u;
+            float dv = base;
+            if (UNIT) dv = __fadd_rn(base, __fmul_rn(c, (float)(U + P - 32 * k) - (float)j));
+            const bool dec = dv < v[j];
+            const float C = dec ? dv : v[j];
+            Gk[32 * j] = __fadd_rn(es[u], C);
+            if (dec) w4[j >> 3] |= 1u << j;
+          }
         }
         return (w4[0] | w4[1]) | (w4[2] | w4[3]);
       };
-      // from the top down: a batch only reads indices at or below its own,
+      // from the top down: a batch only reads rows at or below its own,
       // which later batches have not rewritten yet
-      uint32_t* dwt = dw ? dw + 32 * t * KC : nullptr;
-      uint32_t km = top_mask;  // mask of the batch being stored (the top one first)
-      if (__all_sync(0xffffffffu, d <= 32)) {
+      uint32_t* dwt = dwp ? dwp + 32 * t * KC : nullptr;
+      uint32_t km = 0x7FFFFFFFu;  // the top row is state U: no delivery there
+      if (dmax <= 32) {
 #pragma unroll 1
         for (int k = KC - 1; k >= 1; --k) {
-          const uint32_t w = batch(k, BoolTag<false>{}) & km;
+          const uint32_t w = batch(k, IntTag<0>{}) & km;
           if (dwt) dwt[32 * k] = w;
           km = ~0u;
         }
       } else {
 #pragma unroll 1
         for (int k = KC - 1; k >= 1; --k) {
-          const uint32_t w = batch(k, BoolTag<true>{}) & km;
+          const uint32_t w = batch(k, IntTag<2>{}) & km;
           if (dwt) dwt[32 * k] = w;
           km = ~0u;
         }
       }
       {
-        const uint32_t w = batch(0, BoolTag<true>{}) & km;
+        const uint32_t w = (dmax <= P ? batch(0, IntTag<1>{}) : batch(0, IntTag<2>{})) & km;
         if (dwt) dwt[0] = w;
       }
       // at I = U delivering is q = 0: no delivery, C = G_{t+1}(U - d).  The
       // comparison chose it unless f_t < 0.
-      if (ft < 0.f) {
-        const float eU = TABLE ? (last ? 0.f : table_sm[U]) : __fmul_rn(he, (float)U);
-        Gl[32 * U] = __fadd_rn(eU, gUd);
-      }
+      if (ft < 0.f) Gl[32 * (U + P)] = __fadd_rn(et[last ? 0 : U + P], gUd);
     }
+    // the previous tile's path ends before this tile's starts
+    while (bt.t < T) bt_day();
     // value, optional C_0 table (the buffer holds C_0 now)
     if (live) {
-      a.value[s0 + lane] = Gl[32 * a.I0];
+      a.value[s0 + lane] = Gl[32 * (a.I0 + P)];
       if (a.value0)
-        for (int I = 0; I <= U; ++I) a.value0[(s0 + lane) * (U + 1) + I] = Gl[32 * I];
+        for (int I = 0; I <= U; ++I) a.value0[(s0 + lane) * (U + 1) + I] = Gl[32 * (I + P)];
     }
-    // backtrack: decision of the day at the path's state; deliver -> U
-    if (dw) {
-      int I = a.I0;
-      uint8_t* prow = a.policy + (s0 + lane) * T;
-      uint32_t pw = 0u;
-      for (int t = 0; t < T; ++t) {
-        const uint32_t wd = dw[32 * (t * KC + (I >> 5))];
-        const int dec = (int)((wd >> (I & 31)) & 1u);
-        if (pol4) {
-          pw |= (uint32_t)dec << (8 * (t & 3));
-          if ((t & 3) == 3) {
-            if (live) *reinterpret_cast<uint32_t*>(prow + (t - 3)) = pw;
-            pw = 0u;
-          }
-        } else if (live) {
-          prow[t] = (uint8_t)dec;
-        }
-        I = max((dec ? U : I) - cons_at(t), 0);
-      }
-    }
+    if (dwp) bt_start(crow, s0 + (live ? lane : 0), live, dwp);
+    parity ^= 1;
   }
+  while (bt.t < T) bt_day();
   if (__any_sync(0xffffffffu, neg) && lane == 0) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
 }
 
@@ -656,9 +717,9 @@ int lane_by_kc(const ReinsertArgs& a, cudaStream_t st) {
 }
 }  // namespace
 
-size_t reinsert_lane_smem_for(int T, int U, bool table, int warps) {
+size_t reinsert_lane_smem_for(int T, int U, bool /*table*/, int warps) {
   const int NI = 32 * ((U + 1 + 31) / 32);
-  return (((size_t)T * 4 + 15) & ~(size_t)15) + (table ? (size_t)NI * 4 : 0) +
+  return ((((size_t)NI + 32 + 36 + (size_t)T) * 4 + 15) & ~(size_t)15) +
          (size_t)warps * NI * 32 * 4;
 }
 
@@ -679,7 +740,7 @@ size_t reinsert_lane_smem(int T, int U, bool table) {
 
 size_t reinsert_lane_scratch_bytes(int T, int U) {
   const int KC = (U + 1 + 31) / 32;
-  return (size_t)num_sms() * kLaneWarps * (size_t)T * KC * 32 * 4;
+  return (size_t)num_sms() * kLaneWarps * 2 * (size_t)T * KC * 32 * 4;
 }
 
 int launch_reinsert(const ReinsertArgs& a, cudaStream_t st) {

@@ -136,7 +136,23 @@ __device__ __forceinline__ StepRec tmem_rec(StepRec r) {
   return r;
 }
 
+// As tmem_rec, with the selector putting the demand at bits 16..31.
 template <typename QT>
+__device__ __forceinline__ StepRec tmem_rec16(StepRec r) {
+  const uint32_t c = r.col;
+  if (sizeof(QT) == 1) {
+    r.col = c >> 2;
+    r.pad = 0x4044u | ((c & 3u) << 8);  // byte c % 4 -> byte 2
+  } else {
+    const uint32_t b = 2u * (c & 1u);
+    r.col = c >> 1;
+    r.pad = 0x0044u | (b << 8) | ((b + 1u) << 12);  // half c % 2 -> bytes 2, 3
+  }
+  return r;
+}
+
+// HI: the records carry tmem_rec16 selectors (demand at bits 16..31).
+template <typename QT, bool HI = false>
 struct TmemQ {
   uint32_t taddr;  // lane field = warp quadrant, column = first word of the row
   uint32_t word;
@@ -145,7 +161,8 @@ struct TmemQ {
   __device__ __forceinline__ int take(const StepRec& r) {
     __syncwarp();  // the deque loops diverge; tcgen05 ops need the whole warp
     tmem_wait_ld(word);
-    return (int)__byte_perm(word, 0u, r.pad);
+    const uint32_t v = __byte_perm(word, 0u, r.pad);
+    return (int)(HI ? v >> 16 : v);
   }
 };
 
@@ -174,6 +191,12 @@ __host__ __device__ __forceinline__ int staged_row_stride(int n, int qbytes) {
   int rs = (n * qbytes + 3) & ~3;
   if (((rs >> 2) & 1) == 0) rs += 4;
   return rs;
+}
+
+// Bytes of the TMEM kernels' column / selector array (TmemGroup) after the
+// records: positions 1 .. n plus 3 x 8 look-ahead copies.
+__host__ __device__ __forceinline__ size_t cs_bytes(int n) {
+  return (((size_t)n + 24) * 4 + 15) & ~(size_t)15;
 }
 
 // 32-bit TMEM columns per scenario row (rounded up to the 4-column stores).
@@ -511,6 +534,134 @@ struct DequeState {
   }
 };
 
+// Compact deque step for tiles without a demand above Q (hard capacity), one
+// scenario per lane.  Same deque as DequeState (pop from the back every entry
+// with a larger psi, push p = i-1, pop from the front every entry whose route
+// exceeds Q; the front is the argmin, smallest p on ties), with fewer
+// instructions and a shorter dependent chain per position:
+//   - an entry is (psi, L(p) * 2^16 + p) and the lane keeps
+//     Lent = L(i) * 2^16 + i, so the new entry is the previous Lent and
+//     "route p+1..i exceeds Q" is (Lent - ent) > Q * 2^16 + 65535 (mod 2^32):
+//     exact because the prefix loads of the entries tested differ by at most
+//     2Q < 2^16 and i - p < 2^16; the low 16 bits of the front entry are the
+//     predecessor, those of Lent - front the distance i - pred(i);
+//   - a new psi below the front's (the deque's minimum) pops every entry: the
+//     deque restarts at the new entry, so the back-pop loop needs no
+//     emptiness test (it stops at the front at the latest);
+//   - ring slots are byte offsets (multiples of 256: 32 lanes x 8 bytes) into
+//     a [RING][32] ring of 8-byte entries.
+// The newest entry (route s_i alone, load q_i <= Q) never pops from the
+// front, so neither loop can empty the deque.  maxsz records the largest
+// deque (x 256); a scenario whose deque outgrows the ring is recomputed by the
+// plain kernel.
+template <int RING>
+struct FastDeque {
+  unsigned char* lb;   // this lane's slot 0 of the ring
+  uint32_t head, tail; // byte offsets of the front and of the next free slot
+  uint32_t Lent;       // L(i) * 2^16 + i
+  uint32_t fent;       // front entry: L(p) * 2^16 + p
+  uint32_t maxsz;
+  float K, fpsi, bpsi;
+  static constexpr uint32_t kSlots = (uint32_t)(RING - 1) << 8;
+  __device__ __forceinline__ uint2* at(uint32_t off) const {
+    return reinterpret_cast<uint2*>(lb + (off & kSlots));
+  }
+  __device__ __forceinline__ void init(uint2* ring_pl, int lane) {
+    lb = reinterpret_cast<unsigned char*>(ring_pl + lane);
+    head = tail = 0u;
+    Lent = fent = 0u;
+    maxsz = 0u;
+    K = 0.f;
+    fpsi = CUDART_INF_F;  // the first step restarts the deque at entry p = 0
+    bpsi = -CUDART_INF_F;
+  }
+  // position i with demand q16 = q_i << 16 and record (a_i, ce_i)
+  __device__ __forceinline__ void step(uint32_t q16, float a, float ce, uint32_t Qc) {
+    const float psi = __fadd_rn(K, a);  // psi(i-1)
+    const uint32_t ent = Lent;          // (L(i-1), i-1)
+    Lent += q16 + 1u;
+    const bool restart = psi < fpsi;
+    if (restart) {
+      tail = head;
+      fpsi = psi;
+      fent = ent;
+      bpsi = -CUDART_INF_F;
+    }
+    while (bpsi > psi) {
+      tail -= 256u;
+      bpsi = __uint_as_float(at(tail - 256u)->x);
+    }
+    *at(tail) = make_uint2(__float_as_uint(psi), ent);
+    tail += 256u;
+    bpsi = psi;
+    maxsz = max(maxsz, tail - head);
+    while (Lent - fent > Qc) {
+      head += 256u;
+      const uint2 e = *at(head);
+      fpsi = __uint_as_float(e.x);
+      fent = e.y;
+    }
+    K = __fadd_rn(fpsi, ce);
+  }
+  __device__ __forceinline__ bool overflow() const { return maxsz > (uint32_t)RING * 256u; }
+};
+
+// TMEM demands fetched a group of G positions at a time: the loads of group
+// g + 1 are issued right after the wait for group g, so each
+// tcgen05.wait::ld (which waits for all of the thread's outstanding loads)
+// covers G steps and finds its loads long complete.  cs[k] (shared) = TMEM
+// column of position k + 1 << 16 | the tmem_rec16 selector; the array holds
+// copies of position n up to index n + 2G.
+template <int G>
+struct TmemGroup {
+  uint32_t taddr;
+  const uint32_t* cs;
+  uint32_t wc[G], sc[G];  // current group: words, selectors
+  uint32_t wn[G], sn[G];  // next group (in flight)
+  __device__ __forceinline__ void issue(int k0) {  // positions k0 + 1 .. k0 + G
+#pragma unroll
+    for (int u = 0; u < G; u += 4) {
+      const uint4 v = *reinterpret_cast<const uint4*>(cs + k0 + u);
+      const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        sn[u + e] = x[e];
+        wn[u + e] = tmem_ld1(taddr + (x[e] >> 16));
+      }
+    }
+  }
+  __device__ __forceinline__ void wait() {
+    __syncwarp();  // the deque loops diverge; tcgen05 ops need the whole warp
+    if (G == 8) {
+      asm volatile("tcgen05.wait::ld.sync.aligned;"
+                   : "+r"(wn[0]), "+r"(wn[1]), "+r"(wn[2 % G]), "+r"(wn[3 % G]), "+r"(wn[4 % G]),
+                     "+r"(wn[5 % G]), "+r"(wn[6 % G]), "+r"(wn[7 % G])::"memory");
+    } else {
+      asm volatile("tcgen05.wait::ld.sync.aligned;"
+                   : "+r"(wn[0]), "+r"(wn[1 % G]), "+r"(wn[2 % G]), "+r"(wn[3 % G])::"memory");
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      wc[u] = wn[u];
+      sc[u] = sn[u];
+    }
+  }
+  __device__ __forceinline__ uint32_t q16(int u) const { return __byte_perm(wc[u], 0u, sc[u]); }
+};
+
+// TMEM row with the demand returned at bits 16..31 (the record's pad is the
+// byte-permute selector that puts it there; see tmem_rec16).
+struct TmemQ16 {
+  uint32_t taddr;
+  uint32_t word;
+  __device__ __forceinline__ void prefetch(const StepRec& r) { word = tmem_ld1(taddr + r.col); }
+  __device__ __forceinline__ uint32_t take(const StepRec& r) {
+    __syncwarp();  // the deque loops diverge; tcgen05 ops need the whole warp
+    tmem_wait_ld(word);
+    return __byte_perm(word, 0u, r.pad);
+  }
+};
+
 // Predecessor stage: [NS * 32 rows][kBatch positions] with an odd word pitch,
 // so the per-step writes of the 32 lanes (one row each) hit 32 banks.
 template <typename PT>
@@ -730,6 +881,78 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
   }
 }
 
+// The DP of one scenario per lane with FastDeque steps, for tiles without a
+// demand above Q, rows in TMEM, demands fetched KG positions ahead
+// (TmemGroup; cs as there), records (a_i, ce_i) from shared memory.  Every
+// lane of the warp runs it (lanes beyond the tile on stale data, outputs
+// dropped).
+// OUT == kOutNone: cost only; kOutDirect: predecessors stored by each lane, 4
+// positions per store (n % 4 == 0, aligned rows); kOutDeltaLane: i - pred(i)
+// packed 4 (uint8) or 2 (uint16) per word into the [word][lane] scratch dout
+// (check_delta: a tile with zero demands, where a route may be longer than
+// the staging type holds).
+constexpr int kGroup = 8;
+template <typename QT, typename PT, int RING, int OUT>
+__device__ __forceinline__ void dp_fast(uint32_t taddr, const uint32_t* cs, int n, int Q,
+                                        const StepRec* rec, uint2* ring_pl, int lane,
+                                        PT* pred_tile, int rows, bool check_delta, bool* bad,
+                                        float* K_out, uint32_t* dout) {
+  constexpr int G = kGroup;
+  constexpr int kPer = 4 / (int)sizeof(QT);  // deltas per word (kOutDeltaLane)
+  constexpr int kBits = 8 * (int)sizeof(QT);
+  constexpr uint32_t kLow = sizeof(QT) == 1 ? 0xFFu : 0xFFFFu;
+  const uint32_t Qc = ((uint32_t)Q << 16) | 0xFFFFu;
+  const uint32_t rec_s = (uint32_t)__cvta_generic_to_shared(rec);
+  FastDeque<RING> st;
+  st.init(ring_pl, lane);
+  TmemGroup<G> tg;
+  tg.taddr = taddr;
+  tg.cs = cs;
+  tg.issue(0);
+  tg.wait();
+  tg.issue(G);
+  const bool live = lane < rows;
+  PT* prow = (OUT == kOutDirect) ? pred_tile + (int64_t)lane * n : nullptr;
+  uint32_t any = 0u;   // OR of the deltas (kOutDeltaLane): one range test per row
+  uint32_t f[4];       // last four front entries (kOutDirect)
+  uint32_t dw = 0u;    // delta word being packed (kOutDeltaLane)
+  const int ng = (n + G - 1) / G;
+  for (int g = 0; g < ng; ++g) {
+    const int i0 = g * G + 1;
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int i = i0 + u;
+      if (G * (g + 1) > n && i > n) break;  // ragged last group
+      const StepRec r = ld_rec_shared(rec_s + 16u * (uint32_t)(i - 1));
+      st.step(tg.q16(u), r.a, r.ce, Qc);
+      if (OUT == kOutDirect) {
+        f[u & 3] = st.fent;
+        if ((u & 3) == 3 && live) {
+          if (sizeof(PT) == 2) {
+            *reinterpret_cast<uint2*>(prow + (i - 4)) =
+                make_uint2(__byte_perm(f[0], f[1], 0x5410), __byte_perm(f[2], f[3], 0x5410));
+          } else {
+            *reinterpret_cast<int4*>(prow + (i - 4)) =
+                make_int4((int)(f[0] & 0xFFFFu), (int)(f[1] & 0xFFFFu), (int)(f[2] & 0xFFFFu),
+                          (int)(f[3] & 0xFFFFu));
+          }
+        }
+      } else if (OUT == kOutDeltaLane) {
+        const uint32_t dl = (st.Lent - st.fent) & 0xFFFFu;  // i - pred(i)
+        if (check_delta) any |= dl;
+        const int sl = (i - 1) % kPer;
+        dw = (sl == 0 ? 0u : dw) | ((dl & kLow) << (kBits * sl));
+        if (sl == kPer - 1 || i == n) dout[((i - 1) / kPer) * 32] = dw;
+      }
+    }
+    tg.wait();
+    tg.issue((g + 2) * G);
+  }
+  tg.wait();  // the look-ahead group past the row
+  *bad |= st.overflow() || (check_delta && any > (sizeof(QT) == 1 ? 255u : 65535u));
+  *K_out = st.K;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ kernels
@@ -870,8 +1093,13 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
   // tour records in shared memory (a row that fits a warp's TMEM columns has
   // n <= 512), plus a copy of position n after them
   StepRec* rec = reinterpret_cast<StepRec*>(smem);
-  for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
-  const size_t off = ((size_t)n + 2) * sizeof(StepRec);
+  for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec16<QT>(a.rec[min(k, n - 1)]);
+  uint32_t* cs = reinterpret_cast<uint32_t*>(rec + n + 2);
+  for (int k = threadIdx.x; k < n + 3 * kGroup; k += blockDim.x) {
+    const StepRec r = rec[min(k, n - 1)];
+    cs[k] = (r.col << 16) | r.pad;
+  }
+  const size_t off = ((size_t)n + 2) * sizeof(StepRec) + cs_bytes(n);
   const size_t stage_bytes = OUT == kOutStream ? stage_bytes_of<PT, 1>() : 0;
   const size_t per_warp = ring_bytes(RING) + stage_bytes;
   unsigned char* wbase = smem + off + per_warp * warp;
@@ -898,21 +1126,22 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
     PT* pred_tile = a.pred ? reinterpret_cast<PT*>(a.pred) + s0 * n : nullptr;
     const int prow = pred_tile ? rows : 0;
     constexpr int UNR = XW == 0 ? 2 : 1;
-    using Src = TmemQ<QT>;
+    using Src = TmemQ<QT, true>;
     const TileFlags tf = ingest_tile_tmem<QT, XW == 0 ? 16 : 8>(tsrc, rows, n, Q, taddr, lane);
-    Src src{taddr, 0u};
-    if (tf.inf_rows)
+    if (tf.inf_rows) {
+      Src src{taddr, 0u};
       dp_rows<1, QT, PT, RING, OUT, true, true, Src, UNR>(
           &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
           false, &first_inf, &bad, &K);
-    else if (tf.small_loads)
-      dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR, true>(
-          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
-          false, &first_inf, &bad, &K);
-    else
+    } else if (OUT == kOutStream) {  // predecessors through the stage (n % 4 != 0)
+      Src src{taddr, 0u};
       dp_rows<1, QT, PT, RING, OUT, false, true, Src, UNR>(
           &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
           false, &first_inf, &bad, &K);
+    } else {
+      dp_fast<QT, PT, RING, OUT>(taddr, cs, n, Q, rec, ring_pl, lane, pred_tile, prow, false,
+                                 &bad, &K, nullptr);
+    }
     neg |= tf.neg;
     const bool valid = lane < rows;
     bad = bad && valid;
@@ -970,8 +1199,13 @@ __global__ void __launch_bounds__(MAXT, 1) split_tmem_adj_kernel(SplitDequeArgs 
     tmem_relinquish();
   }
   StepRec* rec = reinterpret_cast<StepRec*>(smem);
-  for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec<QT>(a.rec[min(k, n - 1)]);
-  size_t off = ((size_t)n + 2) * sizeof(StepRec);
+  for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec16<QT>(a.rec[min(k, n - 1)]);
+  uint32_t* cs = reinterpret_cast<uint32_t*>(rec + n + 2);
+  for (int k = threadIdx.x; k < n + 3 * kGroup; k += blockDim.x) {
+    const StepRec r = rec[min(k, n - 1)];
+    cs[k] = (r.col << 16) | r.pad;
+  }
+  size_t off = ((size_t)n + 2) * sizeof(StepRec) + cs_bytes(n);
   unsigned int* hist_sm = reinterpret_cast<unsigned int*>(smem + off);
   off += ((size_t)(2 * n + 1) * 4 + 15) & ~(size_t)15;
   for (int k = threadIdx.x; k < 2 * n + 1; k += blockDim.x) hist_sm[k] = 0u;
@@ -993,22 +1227,18 @@ __global__ void __launch_bounds__(MAXT, 1) split_tmem_adj_kernel(SplitDequeArgs 
     uint32_t first_inf = (uint32_t)n + 1;
     bool bad = false;
     float K;
-    using Src = TmemQ<QT>;
+    using Src = TmemQ<QT, true>;
     const TileFlags tf =
         ingest_tile_tmem<QT, MAXT <= 512 ? 16 : 8>(a.demands + s0 * n, rows, n, Q, taddr, lane);
-    Src src{taddr, 0u};
-    if (tf.inf_rows)
+    if (tf.inf_rows) {
+      Src src{taddr, 0u};
       dp_rows<1, QT, int32_t, RING, kOutDeltaLane, true, true, Src, UNR>(
           &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, nullptr, nullptr, 0, tf.zero,
           &first_inf, &bad, &K, 0.f, dl);
-    else if (tf.small_loads)
-      dp_rows<1, QT, int32_t, RING, kOutDeltaLane, false, true, Src, UNR, true>(
-          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, nullptr, nullptr, 0, tf.zero,
-          &first_inf, &bad, &K, 0.f, dl);
-    else
-      dp_rows<1, QT, int32_t, RING, kOutDeltaLane, false, true, Src, UNR>(
-          &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, nullptr, nullptr, 0, tf.zero,
-          &first_inf, &bad, &K, 0.f, dl);
+    } else {
+      dp_fast<QT, int32_t, RING, kOutDeltaLane>(taddr, cs, n, Q, rec, ring_pl, lane, nullptr, 0,
+                                                tf.zero, &bad, &K, dl);
+    }
     neg |= tf.neg;
     const bool valid = lane < rows;
     bad = bad && valid;
@@ -1344,7 +1574,7 @@ DequeConfig deque_config(int n, int Q, int warps, int ring, bool hist, int pred_
   // needed.
   c.tmem = allow_tmem && !hist && tmem_row_words(n, c.qbytes) <= kTmemColsPerWarp;
   if (c.tmem) {
-    const size_t base = ((size_t)n + 2) * sizeof(StepRec);
+    const size_t base = ((size_t)n + 2) * sizeof(StepRec) + cs_bytes(n);
     const size_t per_warp = ring_bytes(ring) + stage_bytes_for(pred_bytes, 1);
     c.warps = 16;
     const size_t need = base + (size_t)c.warps * per_warp;
@@ -1372,7 +1602,7 @@ DequeConfig deque_config_wide(const DequeConfig& c, int n, int Q, int64_t S, boo
   if (nw <= 16) return c;
   DequeConfig w = c;
   w.warps = nw;
-  const size_t need = ((size_t)n + 2) * sizeof(StepRec) + (size_t)nw * ring_bytes(16);
+  const size_t need = ((size_t)n + 2) * sizeof(StepRec) + cs_bytes(n) + (size_t)nw * ring_bytes(16);
   w.smem = need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
   return w;
 }
@@ -1560,7 +1790,7 @@ template <typename QT>
 int launch_adj_t(const SplitDequeArgs& a, int nw, uint32_t* dscratch, int sms,
                  cudaStream_t st) {
   auto k = nw <= 16 ? split_tmem_adj_kernel<QT, 512> : split_tmem_adj_kernel<QT, 32 * kTmemMaxWarps>;
-  size_t smem = ((size_t)a.n + 2) * sizeof(StepRec) + (((size_t)(2 * a.n + 1) * 4 + 15) & ~(size_t)15) +
+  size_t smem = ((size_t)a.n + 2) * sizeof(StepRec) + cs_bytes(a.n) + (((size_t)(2 * a.n + 1) * 4 + 15) & ~(size_t)15) +
                 (size_t)nw * ring_bytes(16);
   if (smem < kOneCtaPerSmSmem) smem = kOneCtaPerSmSmem;  // one TMEM owner per SM
   if (smem > kMaxSmemPerCta) return (int)cudaErrorInvalidValue;

@@ -169,7 +169,7 @@ struct StreamDP {
   uint32_t base;       // ring base of the warp (aligned to kRingBytes)
   uint32_t haddr;      // front slot
   uint32_t taddr;      // next free slot
-  uint32_t Lp;         // L(i) << 16 | 0xFFFF  (prefix load mod 2^16)
+  uint32_t Lp;         // CHECK: L(i) << 16 | 0xFFFF; else L(i) << 16 + i (mod 2^32)
   uint32_t fent;       // front entry: L(p) << 16 | p
   uint32_t first_inf;  // CHECK: first position with a demand above Q
   float K, bpsi, fpsi;
@@ -181,7 +181,7 @@ struct StreamDP {
   __device__ __forceinline__ void init(uint32_t warp_base, int lane, float a1, int n) {
     base = warp_base;
     haddr = taddr = warp_base + 8u * (uint32_t)lane;
-    Lp = 0xFFFFu;
+    Lp = CHECK ? 0xFFFFu : 0u;
     fent = 0u;
     first_inf = (uint32_t)n + 1u;
     K = 0.f;
@@ -190,8 +190,42 @@ struct StreamDP {
     full = false;
   }
   // Position i with demand qh (<< 16) and record r = (a_i, ce_i).
+  //  Without a demand above Q (CHECK false): the entry of p = i-1 is the
+  // previous Lp, and "route p+1..i exceeds Q" is (Lp - ent) > Qc with
+  // Qc = Q << 16 | 0xFFFF (mod 2^32: the entries tested differ in prefix load
+  // by at most 2Q < 2^16, and i - p < 2^16); a psi below the front's (the
+  // deque's minimum) pops every entry, so the deque restarts at the new entry
+  // and the back-pop loop needs no emptiness test; the newest entry never
+  // pops from the front.
   __device__ __forceinline__ void step(int i, uint32_t qh, float2 r, uint32_t Qc, uint32_t Qh,
                                        int n) {
+    if (!CHECK) {
+      const float psi = __fadd_rn(K, r.x);
+      const uint32_t ent = Lp;
+      Lp += qh + 1u;
+      if (psi < fpsi) {
+        taddr = haddr;
+        fpsi = psi;
+        fent = ent;
+        bpsi = -CUDART_INF_F;
+      }
+      while (bpsi > psi) {
+        taddr = wrap(taddr - 256u);
+        bpsi = lds_f32(wrap(taddr - 256u));
+      }
+      sts_u2(taddr, __float_as_uint(psi), ent);
+      taddr = wrap(taddr + 256u);
+      bpsi = psi;
+      full |= taddr == haddr;
+      while (Lp - fent > Qc) {
+        haddr = wrap(haddr + 256u);
+        const uint2 e = lds_u2(haddr);
+        fpsi = __uint_as_float(e.x);
+        fent = e.y;
+      }
+      K = __fadd_rn(fpsi, r.y);
+      return;
+    }
     const float psi = __fadd_rn(K, r.x);
     const uint32_t ent = Lp - 0xFFFFu + (uint32_t)(i - 1);
     // back pops: an empty deque has bpsi = -inf
