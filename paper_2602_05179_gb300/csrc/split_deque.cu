@@ -551,16 +551,15 @@ struct DequeState {
 //   - ring slots are byte offsets (multiples of 256: 32 lanes x 8 bytes) into
 //     a [RING][32] ring of 8-byte entries.
 // The newest entry (route s_i alone, load q_i <= Q) never pops from the
-// front, so neither loop can empty the deque.  maxsz records the largest
-// deque (x 256); a scenario whose deque outgrows the ring is recomputed by the
-// plain kernel.
+// front, so neither loop can empty the deque.  A scenario whose deque
+// outgrows the ring is recomputed by the plain kernel.
 template <int RING>
 struct FastDeque {
   unsigned char* lb;   // this lane's slot 0 of the ring
   uint32_t head, tail; // byte offsets of the front and of the next free slot
   uint32_t Lent;       // L(i) * 2^16 + i
   uint32_t fent;       // front entry: L(p) * 2^16 + p
-  uint32_t maxsz;
+  bool ovf;            // the deque outgrew the ring
   float K, fpsi, bpsi;
   static constexpr uint32_t kSlots = (uint32_t)(RING - 1) << 8;
   __device__ __forceinline__ uint2* at(uint32_t off) const {
@@ -570,7 +569,7 @@ struct FastDeque {
     lb = reinterpret_cast<unsigned char*>(ring_pl + lane);
     head = tail = 0u;
     Lent = fent = 0u;
-    maxsz = 0u;
+    ovf = false;
     K = 0.f;
     fpsi = CUDART_INF_F;  // the first step restarts the deque at entry p = 0
     bpsi = -CUDART_INF_F;
@@ -591,10 +590,18 @@ struct FastDeque {
       tail -= 256u;
       bpsi = __uint_as_float(at(tail - 256u)->x);
     }
+    // A full ring would overwrite the front: the scenario is flagged (its
+    // results are recomputed) and its deque restarts at the new entry, so the
+    // ring always holds the deque it describes and both loops end.
+    if (tail - head == (uint32_t)RING * 256u) {
+      ovf = true;
+      head = tail;
+      fpsi = psi;
+      fent = ent;
+    }
     *at(tail) = make_uint2(__float_as_uint(psi), ent);
     tail += 256u;
     bpsi = psi;
-    maxsz = max(maxsz, tail - head);
     while (Lent - fent > Qc) {
       head += 256u;
       const uint2 e = *at(head);
@@ -603,7 +610,7 @@ struct FastDeque {
     }
     K = __fadd_rn(fpsi, ce);
   }
-  __device__ __forceinline__ bool overflow() const { return maxsz > (uint32_t)RING * 256u; }
+  __device__ __forceinline__ bool overflow() const { return ovf; }
 };
 
 // TMEM demands fetched a group of G positions at a time: the loads of group
@@ -891,13 +898,13 @@ __device__ __forceinline__ void dp_rows(SRC* src, QT* row, int n, int Q, const S
 // packed 4 (uint8) or 2 (uint16) per word into the [word][lane] scratch dout
 // (check_delta: a tile with zero demands, where a route may be longer than
 // the staging type holds).
+// G = 8 positions per group where registers allow (16 warps per SM), else 4.
 constexpr int kGroup = 8;
-template <typename QT, typename PT, int RING, int OUT>
+template <typename QT, typename PT, int RING, int OUT, int G = kGroup>
 __device__ __forceinline__ void dp_fast(uint32_t taddr, const uint32_t* cs, int n, int Q,
                                         const StepRec* rec, uint2* ring_pl, int lane,
                                         PT* pred_tile, int rows, bool check_delta, bool* bad,
                                         float* K_out, uint32_t* dout) {
-  constexpr int G = kGroup;
   constexpr int kPer = 4 / (int)sizeof(QT);  // deltas per word (kOutDeltaLane)
   constexpr int kBits = 8 * (int)sizeof(QT);
   constexpr uint32_t kLow = sizeof(QT) == 1 ? 0xFFu : 0xFFFFu;
@@ -1094,9 +1101,11 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
   // n <= 512), plus a copy of position n after them
   StepRec* rec = reinterpret_cast<StepRec*>(smem);
   for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec16<QT>(a.rec[min(k, n - 1)]);
+  // from the records in global memory: the shared copy above is not
+  // complete until the barrier below
   uint32_t* cs = reinterpret_cast<uint32_t*>(rec + n + 2);
   for (int k = threadIdx.x; k < n + 3 * kGroup; k += blockDim.x) {
-    const StepRec r = rec[min(k, n - 1)];
+    const StepRec r = tmem_rec16<QT>(a.rec[min(k, n - 1)]);
     cs[k] = (r.col << 16) | r.pad;
   }
   const size_t off = ((size_t)n + 2) * sizeof(StepRec) + cs_bytes(n);
@@ -1139,8 +1148,8 @@ __global__ void __launch_bounds__(512 + 32 * XW, 1) split_tmem_kernel(SplitDeque
           &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, stage, pred_tile, prow,
           false, &first_inf, &bad, &K);
     } else {
-      dp_fast<QT, PT, RING, OUT>(taddr, cs, n, Q, rec, ring_pl, lane, pred_tile, prow, false,
-                                 &bad, &K, nullptr);
+      dp_fast<QT, PT, RING, OUT, XW == 0 ? 8 : 4>(taddr, cs, n, Q, rec, ring_pl, lane,
+                                                  pred_tile, prow, false, &bad, &K, nullptr);
     }
     neg |= tf.neg;
     const bool valid = lane < rows;
@@ -1200,9 +1209,11 @@ __global__ void __launch_bounds__(MAXT, 1) split_tmem_adj_kernel(SplitDequeArgs 
   }
   StepRec* rec = reinterpret_cast<StepRec*>(smem);
   for (int k = threadIdx.x; k <= n + 1; k += blockDim.x) rec[k] = tmem_rec16<QT>(a.rec[min(k, n - 1)]);
+  // from the records in global memory: the shared copy above is not
+  // complete until the barrier below
   uint32_t* cs = reinterpret_cast<uint32_t*>(rec + n + 2);
   for (int k = threadIdx.x; k < n + 3 * kGroup; k += blockDim.x) {
-    const StepRec r = rec[min(k, n - 1)];
+    const StepRec r = tmem_rec16<QT>(a.rec[min(k, n - 1)]);
     cs[k] = (r.col << 16) | r.pad;
   }
   size_t off = ((size_t)n + 2) * sizeof(StepRec) + cs_bytes(n);
@@ -1236,8 +1247,8 @@ __global__ void __launch_bounds__(MAXT, 1) split_tmem_adj_kernel(SplitDequeArgs 
           &src, (QT*)nullptr, n, Q, rec, ring_pl, ring_idx, lane, nullptr, nullptr, 0, tf.zero,
           &first_inf, &bad, &K, 0.f, dl);
     } else {
-      dp_fast<QT, int32_t, RING, kOutDeltaLane>(taddr, cs, n, Q, rec, ring_pl, lane, nullptr, 0,
-                                                tf.zero, &bad, &K, dl);
+      dp_fast<QT, int32_t, RING, kOutDeltaLane, MAXT <= 512 ? 8 : 4>(
+          taddr, cs, n, Q, rec, ring_pl, lane, nullptr, 0, tf.zero, &bad, &K, dl);
     }
     neg |= tf.neg;
     const bool valid = lane < rows;

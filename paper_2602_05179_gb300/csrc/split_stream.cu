@@ -216,7 +216,14 @@ struct StreamDP {
       sts_u2(taddr, __float_as_uint(psi), ent);
       taddr = wrap(taddr + 256u);
       bpsi = psi;
-      full |= taddr == haddr;
+      // the ring filled up: flagged (recomputed), and the deque restarts at
+      // the new entry so that the ring keeps describing it and both loops end
+      if (taddr == haddr) {
+        full = true;
+        haddr = wrap(taddr - 256u);
+        fpsi = psi;
+        fent = ent;
+      }
       while (Lp - fent > Qc) {
         haddr = wrap(haddr + 256u);
         const uint2 e = lds_u2(haddr);
