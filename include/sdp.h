@@ -377,6 +377,11 @@ int sdp_saa_search_run(sdp_saa_search* s, int32_t iters, double* trace_out,
  * neighbour k.  Before any iteration the means are not defined. */
 int sdp_saa_search_state(sdp_saa_search* s, int32_t* tour_out, double* means_out,
                          void* stream);
+/* Capacity-feasible arcs (p, i) of Eq. eqdpA summed over the scenarios of
+ * every tour the last iteration scored (the current tour and its B
+ * neighbours), as sdp_plan_count_arcs: the throughput unit of the search.
+ * total_out: host uint64; synchronises `stream`. */
+int sdp_saa_search_count_arcs(sdp_saa_search* s, void* stream, uint64_t* total_out);
 /* sizeof(sdp_saa_search_desc) as compiled into the library (binding checks). */
 size_t sdp_saa_search_desc_size(void);
 /* sdp_plan_autotune on the search's plan, deque rings of 16 entries only:

@@ -102,6 +102,7 @@ def _load():
             "sdp_plan_kernel_ms": ([P, P], i32),
             "sdp_plan_info": ([P, P, P, P, P], i32),
             "sdp_plan_count_arcs": ([P, P, P], i32),
+            "sdp_saa_search_count_arcs": ([P, P, P], i32),
             "sdp_plan_destroy": ([P], None),
             "sdp_saa_search_create": ([P, P], i32),
             "sdp_saa_search_run": ([P, i32, P, P, P], i32),
@@ -487,6 +488,12 @@ class SaaSearch:
         _check(self._lib.sdp_saa_search_state(self._h, _dev_ptr(tour, "tour"),
                                               _dev_ptr(means, "means"), _stream(stream)))
         return tour, means
+
+    def count_arcs(self, stream=None):
+        """Feasible arcs of every tour the last iteration scored."""
+        t = ctypes.c_uint64()
+        _check(self._lib.sdp_saa_search_count_arcs(self._h, _stream(stream), ctypes.byref(t)))
+        return int(t.value)
 
     def autotune(self, cache_path=None, stream=None):
         cp = cache_path.encode() if cache_path else None

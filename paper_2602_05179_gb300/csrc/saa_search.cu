@@ -299,6 +299,12 @@ int sdp_saa_search_state(sdp_saa_search* s, int32_t* tour_out, double* means_out
   return SDP_OK;
 }
 
+int sdp_saa_search_count_arcs(sdp_saa_search* s, void* stream, uint64_t* total_out) {
+  if (!s) return sfail(SDP_ERR_INVALID_ARG, "search is NULL");
+  if (!on_own_device(s)) return sfail(SDP_ERR_INVALID_ARG, "the search's device is not current");
+  return sdp_plan_count_arcs(s->plan, stream, total_out);
+}
+
 size_t sdp_saa_search_desc_size(void) { return sizeof(sdp_saa_search_desc); }
 
 int sdp_saa_search_autotune(sdp_saa_search* s, void* stream, const char* cache_path) {
