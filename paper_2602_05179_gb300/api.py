@@ -96,6 +96,7 @@ def _load():
             "sdp_reinsert_eval": ([P, P], i32),
             "sdp_set_profile_events": ([P, P], i32),
             "sdp_last_launch": ([P, P], i32),
+            "sdp_set_fault_inject": ([ctypes.c_char_p], i32),
             "sdp_split_plan_create": ([P, P], i32),
             "sdp_plan_autotune": ([P, P, ctypes.c_char_p], i32),
             "sdp_plan_run": ([P, P], i32),
@@ -180,6 +181,79 @@ def last_launch():
     w, c = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(_load().sdp_last_launch(ctypes.byref(w), ctypes.byref(c)))
     return int(w.value), int(c.value)
+
+
+ERR_CUDA, ERR_OOM, ERR_DEVICE_CHECK = -2, -3, -6
+
+
+def set_fault_inject(spec):
+    """One-shot host-side faults, for failure-detection tests (None clears):
+    "alloc[:N]" the next N plan / search allocations fail (SDP_ERR_OOM);
+    "launch[:N]" the next N operator calls fail before launching anything
+    (SDP_ERR_CUDA); "oom[:N]" the same with SDP_ERR_OOM; "stall:NS" the next
+    streaming Split launch publishes no tile, so its DP warps' bounded waits
+    give up after NS nanoseconds and raise FLAG_DEVICE_CHECK; comma-separated
+    to combine.  SDP_FAULT_INJECT in the environment sets the same at the
+    library's first check."""
+    _check(_load().sdp_set_fault_inject(None if spec is None else spec.encode()))
+
+
+def adaptive_batches(run, S, batch=None, *, bytes_per_scenario=0, device=None, min_batch=1):
+    """Evaluate scenarios [0, S) in consecutive slices, as Algorithm "GPU-Based
+    DP with Adaptive Batching" of the paper does: the batch size comes from the
+    free device memory (bytes_per_scenario each, 80% of what is free) unless
+    given; a slice whose evaluation runs out of memory (SdpError with
+    ERR_OOM, or torch's OutOfMemoryError) is retried with half the batch, down
+    to min_batch; unused cached device memory is released after each slice
+    (the algorithm's ClearCache).  run(s0, s1) evaluates scenarios s0..s1-1.
+    Returns ([(s0, s1, result), ...] in order, [batch sizes used])."""
+    def clear():
+        if torch.cuda.is_available():
+            torch.cuda.empty_cache()
+    if batch is None:
+        batch = S
+        if bytes_per_scenario > 0 and torch.cuda.is_available():
+            free = torch.cuda.mem_get_info(device)[0]
+            batch = int(0.8 * free) // int(bytes_per_scenario)
+    batch = max(min_batch, min(int(batch), max(S, 1)))
+    out, sizes = [], [batch]
+    s0 = 0
+    while s0 < S:
+        s1 = min(S, s0 + batch)
+        try:
+            r = run(s0, s1)
+        except (SdpError, torch.cuda.OutOfMemoryError) as e:
+            if isinstance(e, SdpError) and e.code != ERR_OOM:
+                raise
+            if batch <= min_batch:
+                raise
+            batch = max(min_batch, batch // 2)
+            sizes.append(batch)
+            clear()
+            continue
+        out.append((s0, s1, r))
+        s0 = s1
+        clear()
+    return out, sizes
+
+
+def reinsert_eval_batched(T, U, I0, h, p, unit_cost, fixed, consumption, *, batch=None,
+                          min_batch=32, **kw):
+    """reinsert_eval over consumption [S, T] in adaptive batches
+    (adaptive_batches): value [S], policy [S, T] (if asked), FP64 mean over
+    all S, and the batch sizes used."""
+    S = int(consumption.shape[0])
+    per = 4 * T + 4 + T + 4 * (U + 1)  # inputs and outputs of one scenario, roughly
+    parts, sizes = adaptive_batches(
+        lambda s0, s1: reinsert_eval(T, U, I0, h, p, unit_cost, fixed, consumption[s0:s1],
+                                     mean=False, **kw),
+        S, batch, bytes_per_scenario=per, device=consumption.device, min_batch=min_batch)
+    value = torch.cat([r["value"] for _, _, r in parts]) if parts else \
+        torch.empty(0, dtype=torch.float32, device=consumption.device)
+    pol = [r["policy"] for _, _, r in parts]
+    policy = torch.cat(pol) if parts and pol[0] is not None else None
+    return {"value": value, "policy": policy, "mean": value.double().mean() if S else
+            torch.zeros((), dtype=torch.float64, device=consumption.device), "batches": sizes}
 
 
 def status(clear: bool = True) -> int:

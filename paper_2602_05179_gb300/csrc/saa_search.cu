@@ -213,7 +213,8 @@ int sdp_saa_search_create(const sdp_saa_search_desc* d, sdp_saa_search** out) {
   s->moves = d->moves;
   s->seed = d->seed;
   const int T = d->B + 1;
-  cudaError_t e = cudaMalloc((void**)&s->d_cand, sizeof(int32_t) * (size_t)T * d->n);
+  cudaError_t e = fault_alloc() ? cudaErrorMemoryAllocation  // injected (tests)
+                                : cudaMalloc((void**)&s->d_cand, sizeof(int32_t) * (size_t)T * d->n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_costs, sizeof(float) * (size_t)T * d->S);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_means, sizeof(double) * (size_t)T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_cur, sizeof(int32_t) * (size_t)d->n);

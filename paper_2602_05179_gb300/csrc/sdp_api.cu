@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -46,6 +47,69 @@ int fail(int code, const char* fmt, ...) {
 
 int cuda_fail(cudaError_t e, const char* what) {
   return fail(SDP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ fault injection
+// One-shot host-side faults for failure-detection tests (sdp_set_fault_inject,
+// or SDP_FAULT_INJECT in the environment, read at the first check).  Nothing
+// here touches a device: a fault is an error code returned before the call
+// launches anything, or (stall) a streaming launch whose producers never
+// publish a tile, so that the DP warps' bounded waits run out.
+std::mutex g_fault_mu;
+bool g_fault_env_read = false;
+int g_fault_alloc = 0;     // plan / search allocations left to fail
+int g_fault_launch = 0;    // operator calls left to fail with SDP_ERR_CUDA
+int g_fault_oom = 0;       // operator calls left to fail with SDP_ERR_OOM
+uint64_t g_fault_stall_ns = 0;  // next streaming launch: producers stall, waits give up after this
+
+int parse_faults(const char* spec) {
+  // comma-separated: alloc[:N] | launch[:N] | oom[:N] | stall:NS | none
+  const char* p = spec;
+  while (p && *p) {
+    const char* e = strchr(p, ',');
+    const size_t len = e ? (size_t)(e - p) : strlen(p);
+    char tok[64];
+    if (len >= sizeof(tok)) return -1;
+    memcpy(tok, p, len);
+    tok[len] = 0;
+    char* colon = strchr(tok, ':');
+    long long v = 1;
+    if (colon) {
+      *colon = 0;
+      char* end = nullptr;
+      v = strtoll(colon + 1, &end, 10);
+      if (!end || *end || v < 0) return -1;
+    }
+    if (!strcmp(tok, "alloc")) g_fault_alloc = (int)v;
+    else if (!strcmp(tok, "launch")) g_fault_launch = (int)v;
+    else if (!strcmp(tok, "oom")) g_fault_oom = (int)v;
+    else if (!strcmp(tok, "stall") && colon) g_fault_stall_ns = (uint64_t)v;
+    else if (!strcmp(tok, "none")) g_fault_alloc = g_fault_launch = g_fault_oom = 0, g_fault_stall_ns = 0;
+    else return -1;
+    p = e ? e + 1 : nullptr;
+  }
+  return 0;
+}
+
+void fault_env_locked() {
+  if (g_fault_env_read) return;
+  g_fault_env_read = true;
+  if (const char* e = getenv("SDP_FAULT_INJECT")) parse_faults(e);
+}
+
+bool take(int& counter) {
+  std::lock_guard<std::mutex> g(g_fault_mu);
+  fault_env_locked();
+  if (counter <= 0) return false;
+  --counter;
+  return true;
+}
+
+// An operator call about to launch: an injected failure, if one is pending.
+int fault_call() {
+  if (take(g_fault_oom)) return fail(SDP_ERR_OOM, "injected out-of-memory (SDP_FAULT_INJECT)");
+  if (take(g_fault_launch)) return fail(SDP_ERR_CUDA, "injected launch failure (SDP_FAULT_INJECT)");
+  return SDP_OK;
 }
 
 constexpr int kMaxDev = 64;
@@ -381,6 +445,9 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     sa.tflags = w.tflags; sa.cost = cost; sa.pred = pred; sa.pred_dtype = a->pred_dtype;
     sa.fb_list = w.fb_list; sa.fb_count = w.fb_count; sa.status = status;
     sa.ctas_per_sm = 0;
+    const uint64_t stall = fault_stall_ns();
+    sa.wait_ns = stall ? stall : kWaitLimitNs;
+    sa.stall = stall ? 1 : 0;
     note_launch(0, 0);
     prof_begin(st);  // both kernels of the path: pre-pass + DP
     const int e = launch_split_stream(sa, st);
@@ -457,6 +524,18 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
 
 int status_word(uint32_t** out) { return status_ptr(out); }
 
+bool fault_alloc() { return take(g_fault_alloc); }
+
+uint64_t fault_stall_ns() {
+  std::lock_guard<std::mutex> g(g_fault_mu);
+  fault_env_locked();
+  const uint64_t v = g_fault_stall_ns;
+  g_fault_stall_ns = 0;
+  return v;
+}
+
+int fault_call_hook() { return fault_call(); }
+
 int api_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
 bool api_device_ptr(const void* p) { return is_device_ptr(p); }
@@ -491,6 +570,19 @@ int sdp_set_profile_events(void* start, void* stop) {
   g_prof_stop = static_cast<cudaEvent_t>(stop);
   return SDP_OK;
 }
+int sdp_set_fault_inject(const char* spec) {
+  std::lock_guard<std::mutex> g(g_fault_mu);
+  g_fault_env_read = true;  // an explicit setting replaces the environment's
+  g_fault_alloc = g_fault_launch = g_fault_oom = 0;
+  g_fault_stall_ns = 0;
+  if (spec && parse_faults(spec)) {
+    g_fault_alloc = g_fault_launch = g_fault_oom = 0;
+    g_fault_stall_ns = 0;
+    return fail(SDP_ERR_INVALID_ARG, "bad fault spec '%s'", spec);
+  }
+  return SDP_OK;
+}
+
 int sdp_last_launch(int32_t* warps_per_cta_out, int32_t* ctas_out) {
   if (warps_per_cta_out) *warps_per_cta_out = g_last_warps;
   if (ctas_out) *ctas_out = g_last_ctas;
@@ -537,6 +629,8 @@ int sdp_split_eval(const sdp_split_args* args, void* stream) {
   if (rc) return rc;
   uint32_t* status;
   rc = status_ptr(&status);
+  if (rc) return rc;
+  rc = fault_call();
   if (rc) return rc;
   const SplitWs w = carve_split(a, a->workspace, false);
   if (a->S > 0 && a->n == 0) {
@@ -669,6 +763,8 @@ int sdp_split_backward(const sdp_split_args* args, const void* pred, const float
   uint32_t* status;
   rc = status_ptr(&status);
   if (rc) return rc;
+  rc = fault_call();
+  if (rc) return rc;
   const SplitWs w = carve_split(fwd, fwd->workspace, true);
   const int n = fwd->n;
   cudaError_t e = cudaMemsetAsync(w.hist, 0, sizeof(unsigned long long) * (2 * (size_t)n + 1), st);
@@ -750,6 +846,8 @@ int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
   if (rc) return rc;
   uint32_t* status;
   rc = status_ptr(&status);
+  if (rc) return rc;
+  rc = fault_call();
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ReinsertArgs r{};

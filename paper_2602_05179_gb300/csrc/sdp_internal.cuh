@@ -193,6 +193,8 @@ struct StreamArgs {
   uint32_t* fb_count;
   uint32_t* status;
   int ctas_per_sm;          // CTAs per SM (0 = 1)
+  uint64_t wait_ns;         // a DP warp's wait for a tile gives up after this
+  int stall;                // fault injection (tests): producers publish no tile
 };
 bool stream_supported(int n, int Q);
 // batched plan over tour-ordered row slots (one ring of slots per SM)
@@ -273,5 +275,14 @@ int reinsert_lane_warps(int T, int U, bool table);
 size_t reinsert_lane_scratch_bytes(int T, int U);
 
 int num_sms();
+
+// Host-side fault injection (sdp_set_fault_inject / SDP_FAULT_INJECT): true
+// if the next plan / search allocation is to fail; the stall time of the next
+// streaming launch (0: none); the pending failure of an operator call (0 or
+// an SDP_ERR_* code, with the message set).
+bool fault_alloc();
+uint64_t fault_stall_ns();
+int fault_call_hook();
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // device waits give up after 2 s
 
 }  // namespace sdp

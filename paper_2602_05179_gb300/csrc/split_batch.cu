@@ -73,6 +73,7 @@ int pcuda(cudaError_t e, const char* what) {
 
 template <typename T>
 cudaError_t alloc_copy(T** dst, const T* src, size_t count) {
+  if (fault_alloc()) return cudaErrorMemoryAllocation;  // injected (tests)
   cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (count ? count : 1));
   if (e != cudaSuccess) return e;
   if (src && count) e = cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
@@ -277,6 +278,8 @@ int sdp_plan_run(sdp_plan* p, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t* status;
   int rc = status_word(&status);
+  if (rc) return rc;
+  rc = fault_call_hook();
   if (rc) return rc;
   if (!p->exec) {
     // capture on a private stream so the caller's stream may be the legacy one

@@ -51,7 +51,6 @@ constexpr int kThreads = (kDpWarps + kProdWarps) * 32;
 constexpr uint32_t kStage = 64u * 1024u;      // bytes per producer stage (two)
 constexpr int kRing = 16;                     // deque ring entries per lane
 constexpr uint32_t kRingBytes = (uint32_t)kRing * 256u;  // 32 lanes x 8 B per entry
-constexpr uint64_t kWaitLimitNs = 2000000000ull;         // any wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -476,7 +475,9 @@ __device__ __forceinline__ void produce(const StreamArgs& a, int R, int64_t tb, 
     if (tile_done) __threadfence_block();
     prod_sync();  // also: the stage is free again
     if (ptid == 0) {
-      if (tile_done) st_release_shared(ready, (uint32_t)(g / subs + 1));
+      // (a.stall: fault injection for tests -- no tile is published, and the
+      // DP warps' waits run out after a.wait_ns)
+      if (tile_done && !a.stall) st_release_shared(ready, (uint32_t)(g / subs + 1));
       if (g + 2 < nchunks) {
         fence_proxy_async();
         issue(g + 2, b);
@@ -500,13 +501,13 @@ __device__ __forceinline__ void produce(const StreamArgs& a, int R, int64_t tb, 
 // Bounded wait of a DP warp for `need` published tiles; false on abort or
 // time-out.
 __device__ __forceinline__ bool wait_ready(const uint32_t* ready, const uint32_t* abort_flag,
-                                           uint32_t need) {
+                                           uint32_t need, uint64_t limit_ns) {
   if (ld_acquire_shared(ready) >= need) return true;
   const uint64_t t0 = global_ns();
   while (true) {
     if (ld_acquire_shared(ready) >= need) return true;
     if (ld_acquire_shared(abort_flag)) return false;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
     __nanosleep(128);
   }
 }
@@ -564,8 +565,9 @@ __global__ void __launch_bounds__(kThreads, 1) split_stream_kernel(StreamArgs a,
   uint32_t any_inf = 0, any_fb = 0;
   bool timed_out = false;
   for (int64_t lt = warp; tb + lt < te; lt += kDpWarps) {
-    if (!wait_ready(&ready, &abort_flag, (uint32_t)(lt + 1))) {
-      timed_out = true;
+    if (!wait_ready(&ready, &abort_flag, (uint32_t)(lt + 1), a.wait_ns)) {
+      timed_out = !ld_acquire_shared(&abort_flag);
+      st_release_shared(&abort_flag, 1u);  // the other DP warps stop waiting too
       break;
     }
     const int64_t tile = tb + lt;
@@ -889,7 +891,9 @@ int launch_split_batch_stream(const BatchStreamArgs& a, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
-int launch_split_stream(const StreamArgs& a, cudaStream_t st) {
+int launch_split_stream(const StreamArgs& a0, cudaStream_t st) {
+  StreamArgs a = a0;
+  if (a.wait_ns == 0) a.wait_ns = kWaitLimitNs;  // unset: the default limit
   int R = 32;
   while (R > 1 && (size_t)R * a.n * 4 > kStage) R >>= 1;
   if (R < 4) return (int)cudaErrorInvalidValue;
