@@ -4,8 +4,10 @@
 Workload (one step = one pass of the whole Split path over one batch):
   giant tour n=500, coords uniform fp32 in [0,100)^2 (depot (50,50)), Q=200,
   S=10^6 demand scenarios per GPU, demands iid U{1..30} int32 (seed 1),
-  through sdp_split_eval: tour prep -> DEQUE DP kernel (+ plain fallback, a
-  no-op here) writing fp32 costs and uint16 predecessors -> FP64 mean.
+  through sdp_split_eval: tour prep -> pipelined DP kernel (producer warps
+  permute demand tiles into tour order in an L2-resident slot ring, DP warps
+  run the deque step; + plain fallback, a no-op here) writing fp32 costs and
+  uint16 predecessors -> FP64 mean.
 Metric: Bellman arc relaxations/s (capacity-feasible arcs (p,i) of Eq. eqdpA,
   counted exactly on the device once, outside the timed region) and
   scenarios/s, whole job over all ranks.
@@ -257,7 +259,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="deque", choices=["deque", "stream", "plain"])
+    ap.add_argument("--algo", default="pipe", choices=["pipe", "deque", "stream", "plain"])
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -375,7 +377,7 @@ def main():
         torch.cuda.synchronize()
         pms = p0.elapsed_time(p1) / args.plain_steps
         plain = {"value": arcs_rank * world / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
-                 "speedup_of_deque": (pms / ms_step)}
+                 "speedup_over_plain": (pms / ms_step)}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -815,15 +817,17 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
     alg_bytes = S * n * 4 + S * 4 + S * n * pbytes  # demands in, fp32 cost + preds out
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "split_deque_traffic.json")
+    tp = os.path.join(ROOT, "profiles", "split_pipe_traffic.json" if args.algo == "pipe"
+                      else "split_deque_traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
             tj = json.load(f)
-        if tj.get("kernel_rev") == kernel_rev():
+        if tj.get("kernel_rev") == kernel_rev(args.algo):
             traffic = tj.get("dram_bytes_per_launch")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": {"deque": "split_tmem_kernel", "plain": "split_plain_kernel",
+            "kernel": {"pipe": "split_pipe_kernel", "deque": "split_tmem_kernel",
+                       "plain": "split_plain_kernel",
                        "stream": "stream_prep_kernel + split_stream_kernel"}[args.algo],
             "kernel_ms": kern_ms,
             "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_src} hbm_gbs (copy)"}
@@ -861,11 +865,12 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
     return 0
 
 
-def kernel_rev():
+def kernel_rev(algo="pipe"):
     """Hash of the DP kernel source, to tell whether stored ncu counters still
     describe the kernel being timed."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2602_05179_gb300", "csrc", "split_deque.cu")
+    name = {"pipe": "split_pipe.cu", "stream": "split_stream.cu"}.get(algo, "split_deque.cu")
+    src = os.path.join(ROOT, "paper_2602_05179_gb300", "csrc", name)
     with open(src, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 

@@ -66,10 +66,13 @@ extern "C" {
 #define SDP_FLAG_FALLBACK 8u       /* a scenario took the per-scenario path */
 
 /* Split algorithms */
-#define SDP_ALGO_AUTO 0   /* DEQUE when a demand row fits 512 bytes (uint8
-                             for Q <= 254, else uint16); STREAM for longer
-                             rows it supports; else DEQUE; PLAIN when
-                             neither DEQUE nor STREAM applies */
+#define SDP_ALGO_AUTO 0   /* PIPE where it applies (hard capacity, n <= 1024,
+                             Q <= 32767, 16-byte aligned device demands or
+                             host demands, warps_per_cta = 0, ring 0 or 16);
+                             else DEQUE when a demand row fits 512 bytes
+                             (uint8 for Q <= 254, else uint16), STREAM for
+                             longer rows it supports, else DEQUE; PLAIN when
+                             none applies */
 #define SDP_ALGO_PLAIN 1  /* one thread per scenario, demands read straight
                              from HBM, every feasible arc (p,i) relaxed in
                              turn: the min-plus column product of Eq. eqdpA */
@@ -85,6 +88,18 @@ extern "C" {
                              n <= 2048, Q <= 32767 and 16-byte aligned
                              demands.  The workspace grows by about
                              S * (n + 48) bytes (x2 for uint16) */
+
+#define SDP_ALGO_PIPE 4   /* the DEQUE recursion fed by producer warps of the
+                             same CTA, which narrow and permute each tile's
+                             demand rows into tour order in a small ring of
+                             tile slots that stays in L2 (no pre-pass over
+                             HBM), with 28 DP warps per SM; predecessors
+                             leave through a shared-memory transpose as row
+                             segments.  Needs hard capacity, 1 <= n <= 1024,
+                             Q <= 32767 and 16-byte aligned demands; the
+                             workspace grows by about
+                             SMs * 32 * 32 * ceil32(n * qb) bytes (qb = 1 for
+                             Q <= 254, else 2): 78 MB at n = 500 on 152 SMs */
 
 /* predecessor dtypes */
 #define SDP_PRED_U16 1    /* uint16, requires n < 65535 */
@@ -283,7 +298,8 @@ typedef struct sdp_plan sdp_plan;
  * fallback list and scratch); SDP_ERR_OOM if that fails.  Uses the current
  * device; every later call on the plan must run with that device current. */
 int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out);
-/* Times the candidate launch shapes (warps per CTA x deque ring entries) on
+/* Times the candidate launch shapes (the pipelined and streaming kernels;
+ * DEQUE warps per CTA x deque ring entries) on
  * `stream` -- each runs the whole plan, so outputs are overwritten -- and
  * keeps the fastest.  cache_path (optional, host string) is a text file of
  * earlier choices keyed by the device and the plan's shape: a hit skips the
@@ -298,9 +314,11 @@ int sdp_plan_run(sdp_plan* p, void* stream);
  * (waits for it). */
 int sdp_plan_kernel_ms(sdp_plan* p, float* ms);
 /* Launch shape in use and the number of (tour, 32-scenario tile) items.
- * warps_per_cta = -1: the streaming kernel (tiles narrowed into tour order by
- * producer warps; chosen when every dem_off is a multiple of 4, demands are
- * 16-byte aligned and n_max <= 2048), 0: DEQUE with tensor-memory staging,
+ * warps_per_cta = -2: the pipelined kernel (SDP_ALGO_PIPE's kernel over the
+ * plan's items; chosen when every dem_off is a multiple of 4, demands are
+ * 16-byte aligned and n_max <= 1024), -1: the streaming kernel (tiles
+ * narrowed into tour order by producer warps; the choice for
+ * 1024 < n_max <= 2048 on the same alignment), 0: DEQUE with tensor-memory staging,
  * k > 0: DEQUE with shared-memory staging and k warps per CTA. */
 int sdp_plan_info(const sdp_plan* p, int32_t* warps_per_cta, int32_t* ring,
                   int32_t* ctas, int64_t* items);

@@ -22,7 +22,7 @@ _lib = None
 SDP_OK = 0
 SDP_WARN_INFEASIBLE = 1
 FLAG_INFEASIBLE, FLAG_NEG_INPUT, FLAG_DEVICE_CHECK, FLAG_FALLBACK = 1, 2, 4, 8
-ALGOS = {"auto": 0, "plain": 1, "deque": 2, "stream": 3}
+ALGOS = {"auto": 0, "plain": 1, "deque": 2, "stream": 3, "pipe": 4}
 PRED_DTYPES = {"u16": 1, "i32": 2}
 
 P = ctypes.c_void_p
@@ -177,7 +177,8 @@ def set_profile_events(start, stop):
 
 def last_launch():
     """(warps per CTA, CTAs) of the DP kernel of this thread's last Split
-    evaluation or adjoint call; (0, 0) for the streaming path."""
+    evaluation or adjoint call; (0, 0) for the streaming path, (32, CTAs) for
+    the pipelined one (28 DP + 4 producer warps)."""
     w, c = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(_load().sdp_last_launch(ctypes.byref(w), ctypes.byref(c)))
     return int(w.value), int(c.value)

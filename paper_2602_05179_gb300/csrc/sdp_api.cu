@@ -217,6 +217,7 @@ struct SplitWs {
   unsigned long long* hist;
   unsigned char* qt;   // STREAM: narrowed demands in tour order
   uint32_t* tflags;    // STREAM: per-tile rows with a demand above Q
+  unsigned long long* counter;  // PIPE: group queue (zeroed before each launch)
   uint32_t* dscratch;  // fused adjoint on TMEM: i - pred(i) per [word][lane]
   size_t bytes;
 };
@@ -238,14 +239,16 @@ int resolve_algo(const sdp_split_args* a);
 // would take DEQUE in its default shape and a row fits the tensor memory.
 int adjoint_tmem_warps(const sdp_split_args* a) {
   const int algo = resolve_algo(a);
-  if (algo != SDP_ALGO_DEQUE && algo != SDP_ALGO_STREAM) return 0;
+  if (algo != SDP_ALGO_DEQUE && algo != SDP_ALGO_STREAM && algo != SDP_ALGO_PIPE) return 0;
   if (a->warps_per_cta != 0 || (a->ring != 0 && a->ring != 16)) return 0;
   return split_tmem_adj_warps(a->n, a->Q, a->S, num_sms());
 }
 
-int resolve_algo(const sdp_split_args* a) {
-  int algo = a->algo;
-  if (algo != SDP_ALGO_AUTO) return algo;
+// AUTO: PIPE while it supports the shape (n <= 1024, Q <= 32767, demand rows
+// that bulk copies can read: 16-byte aligned device demands, or host demands
+// staged into aligned buffers), hard capacity and the default launch shape;
+// else the choice that sdp_split_eval_noalloc keeps (auto_algo_no_pipe).
+int auto_algo_no_pipe(const sdp_split_args* a) {
   if (a->capacity_mode == SDP_CAPACITY_SOFT)
     return soft_deque_ok(a) ? SDP_ALGO_DEQUE : SDP_ALGO_PLAIN;
   if (!deque_supported(a->n, a->Q)) return SDP_ALGO_PLAIN;
@@ -254,6 +257,21 @@ int resolve_algo(const sdp_split_args* a) {
       (reinterpret_cast<uintptr_t>(a->demands) & 15) == 0)
     return SDP_ALGO_STREAM;
   return SDP_ALGO_DEQUE;
+}
+
+bool pipe_ok(const sdp_split_args* a) {
+  if (a->capacity_mode == SDP_CAPACITY_SOFT || !pipe_supported(a->n, a->Q)) return false;
+  if (a->n > 0 && a->S > 0 && !is_host_ptr(a->demands) &&
+      (reinterpret_cast<uintptr_t>(a->demands) & 15) != 0)
+    return false;
+  return true;
+}
+
+int resolve_algo(const sdp_split_args* a) {
+  int algo = a->algo;
+  if (algo != SDP_ALGO_AUTO) return algo;
+  if (a->warps_per_cta == 0 && (a->ring == 0 || a->ring == 16) && pipe_ok(a)) return SDP_ALGO_PIPE;
+  return auto_algo_no_pipe(a);
 }
 
 SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
@@ -266,7 +284,7 @@ SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
   w.prep.Dn = c.take<double>(1);
   w.mean_partial = c.take<double>(kMeanBlocks);
   w.fb_count = c.take<uint32_t>(1);
-  if (algo == SDP_ALGO_DEQUE || algo == SDP_ALGO_STREAM) {
+  if (algo == SDP_ALGO_DEQUE || algo == SDP_ALGO_STREAM || algo == SDP_ALGO_PIPE) {
     w.fb_list = c.take<uint32_t>((size_t)a->S);
     w.nslots = a->S < kFallbackSlots ? a->S : kFallbackSlots;
   } else {
@@ -282,6 +300,14 @@ SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
                    : nullptr;
   w.qt = nullptr;
   w.tflags = nullptr;
+  w.counter = nullptr;
+  if (algo == SDP_ALGO_PIPE && !backward && n > 0) {
+    const int64_t rows = (n > 0 && is_host_ptr(a->demands))
+                             ? (a->S < kHostChunkRows ? a->S : kHostChunkRows)
+                             : a->S;
+    w.qt = c.take<unsigned char>(pipe_ring_bytes(n, a->Q, pipe_grid(rows, 1)));
+    w.counter = c.take<unsigned long long>(1);
+  }
   if (algo == SDP_ALGO_STREAM && !backward && n > 0) {
     const int64_t rows = (n > 0 && is_host_ptr(a->demands))
                              ? (a->S < kHostChunkRows ? a->S : kHostChunkRows)
@@ -370,8 +396,13 @@ int check_split(const sdp_split_args* a, bool need_cost) {
   if (a->Q <= 0) return fail(SDP_ERR_INVALID_ARG, "Q = %d <= 0", a->Q);
   if (a->S < 0) return fail(SDP_ERR_INVALID_ARG, "S = %lld < 0", (long long)a->S);
   if (a->S > (int64_t)0xFFFFFFFFll) return fail(SDP_ERR_UNSUPPORTED, "S above 2^32-1");
-  if (a->algo < SDP_ALGO_AUTO || a->algo > SDP_ALGO_STREAM)
+  if (a->algo < SDP_ALGO_AUTO || a->algo > SDP_ALGO_PIPE)
     return fail(SDP_ERR_INVALID_ARG, "unknown algo %d", a->algo);
+  if (a->algo == SDP_ALGO_PIPE && !pipe_supported(a->n, a->Q))
+    return fail(SDP_ERR_UNSUPPORTED, "PIPE needs 1 <= n <= %d and Q <= 32767", kPipeMaxN);
+  if (a->algo == SDP_ALGO_PIPE && a->n > 0 && a->S > 0 && !is_host_ptr(a->demands) &&
+      (reinterpret_cast<uintptr_t>(a->demands) & 15))
+    return fail(SDP_ERR_UNSUPPORTED, "PIPE needs 16-byte aligned demands");
   if (a->algo == SDP_ALGO_DEQUE && !deque_supported(a->n, a->Q))
     return fail(SDP_ERR_UNSUPPORTED, "DEQUE needs 1 <= n <= 65534 and Q <= 32767");
   if (a->algo == SDP_ALGO_STREAM && !stream_supported(a->n, a->Q))
@@ -383,7 +414,7 @@ int check_split(const sdp_split_args* a, bool need_cost) {
   if (a->capacity_mode == SDP_CAPACITY_SOFT) {
     if (!(a->overload_penalty >= 0.f) || a->overload_penalty == INFINITY)
       return fail(SDP_ERR_INVALID_ARG, "overload_penalty must be finite and >= 0");
-    if (a->algo == SDP_ALGO_STREAM)
+    if (a->algo == SDP_ALGO_STREAM || a->algo == SDP_ALGO_PIPE)
       return fail(SDP_ERR_UNSUPPORTED, "soft capacity runs on PLAIN or DEQUE");
     if (a->algo == SDP_ALGO_DEQUE && !soft_deque_ok(a))
       return fail(SDP_ERR_UNSUPPORTED,
@@ -433,7 +464,8 @@ int check_ws(void* ws, size_t have, size_t need) {
 int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
                    unsigned long long* hist, cudaStream_t st) {
   int algo = resolve_algo(a);
-  if (algo == SDP_ALGO_STREAM && hist) algo = SDP_ALGO_DEQUE;  // the fused adjoint is DEQUE's
+  if ((algo == SDP_ALGO_STREAM || algo == SDP_ALGO_PIPE) && hist)
+    algo = SDP_ALGO_DEQUE;  // the fused adjoint is DEQUE's
   const int sms = num_sms();
   float* cost = hist ? nullptr : a->cost_out;
   void* pred = hist ? nullptr : a->pred_out;
@@ -453,6 +485,25 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     const int e = launch_split_stream(sa, st);
     prof_end(st);
     if (e) return cuda_fail((cudaError_t)e, "split_stream launch");
+  }
+  if (algo == SDP_ALGO_PIPE) {
+    PipeArgs pa{};
+    pa.batched = 0;
+    pa.B = 1; pa.Q = a->Q; pa.S = a->S; pa.n1 = a->n;
+    pa.cols = w.prep.cols; pa.rec = w.prep.rec; pa.Dn = w.prep.Dn;
+    pa.demands = a->demands; pa.cost = cost; pa.pred = pred; pa.pred_dtype = a->pred_dtype;
+    pa.qt = w.qt; pa.stride = pipe_row_stride(a->n, a->Q); pa.counter = w.counter;
+    pa.fb_count = w.fb_count; pa.fb_list1 = w.fb_list; pa.status = status;
+    const uint64_t stall = fault_stall_ns();
+    pa.wait_ns = stall ? stall : kWaitLimitNs;
+    pa.stall = stall ? 1 : 0;
+    cudaError_t ce = cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "pipe counter reset");
+    note_launch(32, pipe_grid(a->S, 1));  // 28 DP + 4 producer warps
+    prof_begin(st);
+    const int e = launch_split_pipe(pa, st);
+    prof_end(st);
+    if (e) return cuda_fail((cudaError_t)e, "split_pipe launch");
   }
   const int adj_warps = (hist && w.dscratch) ? adjoint_tmem_warps(a) : 0;
   if (algo == SDP_ALGO_DEQUE && adj_warps > 0) {
@@ -689,7 +740,11 @@ extern "C" {
 int sdp_split_eval_noalloc(const sdp_split_args* a, void* stream) {
   if (!a) return fail(SDP_ERR_INVALID_ARG, "args is NULL");
   if (a->n < 0 || a->S < 0) return fail(SDP_ERR_INVALID_ARG, "n and S must be >= 0");
-  const size_t need = sdp_split_workspace_bytes(a);
+  // AUTO keeps its choice without PIPE here: PIPE's slot ring (tens of MB)
+  // would not fit the fixed scratch at the sizes this entry point serves
+  sdp_split_args b = *a;
+  if (b.algo == SDP_ALGO_AUTO) b.algo = auto_algo_no_pipe(a);
+  const size_t need = sdp_split_workspace_bytes(&b);
   if (need > (size_t)SDP_NOALLOC_SCRATCH_BYTES)
     return fail(SDP_ERR_UNSUPPORTED,
                 "this call needs %zu bytes of scratch; the no-allocation scratch holds %zu "
@@ -698,7 +753,6 @@ int sdp_split_eval_noalloc(const sdp_split_args* a, void* stream) {
   void* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc) return rc;
-  sdp_split_args b = *a;
   b.workspace = scratch;
   b.workspace_bytes = SDP_NOALLOC_SCRATCH_BYTES;
   return sdp_split_eval(&b, stream);

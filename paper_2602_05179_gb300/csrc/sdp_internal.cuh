@@ -229,6 +229,52 @@ __host__ __device__ inline int64_t stream_row_stride(int n, int Q) {
 size_t stream_qt_bytes(int n, int Q, int64_t S);
 int launch_split_stream(const StreamArgs& a, cudaStream_t st);
 
+// Pipelined Split (SDP_ALGO_PIPE, and the batched plans' pipelined kernel):
+// producer warps narrow and permute demand rows into a per-SM ring of
+// tour-ordered tile slots kept small enough to stay in L2, DP warps run the
+// recursion on them.  One tour (batched = 0: n1, cols, rec, Dn[0]; cost and
+// pred by scenario) or a batched plan (batched = 1: n, dem_off, rec_off,
+// order by tour; costs [B*S]; no predecessors).
+constexpr int kPipeMaxN = 1024;
+struct PipeArgs {
+  int batched;
+  int B, Q;
+  int64_t S;
+  int n1;                      // one tour: n
+  const uint16_t* cols;        // one tour: [n] column (customer - 1) of each position
+  const int32_t* n;            // batched: [B]
+  const int64_t* dem_off;      // batched: [B] element offsets, multiples of 4
+  const int64_t* rec_off;      // batched: [B]
+  const int32_t* order;        // batched: [B] tours by decreasing n
+  const StepRec* rec;
+  const double* Dn;            // [B]
+  const int32_t* demands;      // 16-byte aligned
+  float* cost;                 // [B*S]
+  void* pred;                  // one tour only: [S*n] or NULL
+  int pred_dtype;
+  unsigned char* qt;           // slot ring, pipe_ring_bytes
+  int64_t stride;              // bytes per slot row (pipe_row_stride of the longest tour)
+  unsigned long long* counter; // group queue, zero at launch
+  uint32_t* fb_count;
+  uint32_t* fb_list1;          // one tour: [S] scenario ids for the plain kernel
+  unsigned long long* fb_list; // batched: [B*S] global ids b*S+s
+  uint32_t* status;
+  uint64_t wait_ns;            // a bounded wait gives up after this
+  int stall;                   // fault injection (tests): producers publish no tile
+};
+bool pipe_supported(int n, int Q);
+// bytes per tour-ordered slot row: n narrowed demands (uint8 for Q <= 254,
+// else uint16) rounded up to 32 bytes
+__host__ __device__ inline int64_t pipe_row_stride(int n, int Q) {
+  const int64_t qb = Q <= 254 ? 1 : 2;
+  return ((int64_t)n * qb + 31) / 32 * 32;
+}
+// CTAs of a launch (one per SM at most, none without work) and the slot
+// ring they need
+int pipe_grid(int64_t S, int B);
+size_t pipe_ring_bytes(int n_max, int Q, int grid);
+int launch_split_pipe(const PipeArgs& a, cudaStream_t st);
+
 // arc counting (capacity-feasible (p,i) pairs)
 void launch_count_arcs(int n, int Q, int64_t S, const StepRec* rec,
                        const int32_t* demands, int64_t* arcs,

@@ -8,12 +8,14 @@
 // run = [tour prep for every tour (also resets the counter) -> persistent
 // DEQUE kernel over (tour, 32-scenario tile) items -> plain fallback for
 // flagged scenarios -> per-tour FP64 means], captured once in a CUDA graph
-// and replayed.  The persistent kernel is the streaming one
-// (split_batch_stream_kernel, producer warps narrowing each tile's rows into
-// tour order) when the demand offsets allow bulk copies, else the DEQUE
-// batched kernel.  sdp_plan_autotune times the launch shapes (streaming;
-// DEQUE warps per CTA x deque ring size) and keeps the fastest; choices can
-// be cached in a text file keyed by the device and the plan's shape.
+// and replayed.  The persistent kernel is the pipelined one
+// (split_pipe_kernel: producer warps narrow each tile's rows into tour order
+// in an L2-resident slot ring, 28 DP warps per SM) when the demand offsets
+// allow bulk copies and every tour has n <= 1024, else the streaming one
+// (split_batch_stream_kernel), else the DEQUE batched kernel.
+// sdp_plan_autotune times the launch shapes (pipelined; streaming; DEQUE
+// warps per CTA x deque ring size) and keeps the fastest; choices can be
+// cached in a text file keyed by the device and the plan's shape.
 #include <stdio.h>
 #include <string.h>
 
@@ -44,13 +46,14 @@ struct sdp_plan {
   int64_t nslots = 0;
   unsigned long long* d_total = nullptr;
   unsigned char* d_qt = nullptr;  // row slots of the streaming kernel, or NULL
+  unsigned char* d_pq = nullptr;  // slot ring of the pipelined kernel, or NULL
   // caller's arrays
   const int32_t* tours = nullptr;
   const float* coords = nullptr;
   const int32_t* demands = nullptr;
   float* costs = nullptr;
   double* means = nullptr;
-  // launch shape; warps == -1: the streaming kernel
+  // launch shape; warps == -1: the streaming kernel, -2: the pipelined one
   int warps = 4, ring = 16, grid = 0;
   // graph
   cudaGraphExec_t exec = nullptr;
@@ -97,6 +100,13 @@ BatchPrepArgs prep_args(const sdp_plan* p, uint32_t* status) {
 }
 
 int configure(sdp_plan* p, int warps, int ring) {
+  if (warps == -2) {  // pipelined kernel: one CTA per SM, ring of 16 entries
+    if (!p->d_pq) return SDP_ERR_UNSUPPORTED;
+    p->warps = -2;
+    p->ring = 16;
+    p->grid = pipe_grid(p->S, p->B);
+    return SDP_OK;
+  }
   if (warps < 0) {  // streaming kernel: one CTA per SM, ring of 16 entries
     if (!p->d_qt) return SDP_ERR_UNSUPPORTED;
     p->warps = -1;
@@ -133,7 +143,16 @@ int enqueue(sdp_plan* p, cudaStream_t st, uint32_t* status, bool with_events) {
   // record inside a capture only orders streams and never fires).
   if (with_events) cudaEventRecordWithFlags(p->ev0, st, cudaEventRecordExternal);
   int e;
-  if (p->warps < 0) {
+  if (p->warps == -2) {
+    PipeArgs pa{};
+    pa.batched = 1;
+    pa.B = p->B; pa.Q = p->Q; pa.S = p->S;
+    pa.n = p->d_n; pa.dem_off = p->d_dem_off; pa.rec_off = p->d_rec_off; pa.order = p->d_order;
+    pa.rec = p->d_rec; pa.Dn = p->d_Dn; pa.demands = p->demands; pa.cost = p->costs;
+    pa.qt = p->d_pq; pa.stride = pipe_row_stride(p->n_max, p->Q); pa.counter = p->d_counter;
+    pa.fb_count = p->d_fb_count; pa.fb_list = p->d_fb_list; pa.status = status;
+    e = launch_split_pipe(pa, st);
+  } else if (p->warps < 0) {
     BatchStreamArgs sa{};
     sa.B = p->B; sa.Q = p->Q; sa.S = p->S;
     sa.n = p->d_n; sa.dem_off = p->d_dem_off; sa.rec_off = p->d_rec_off; sa.order = p->d_order;
@@ -193,6 +212,7 @@ void sdp_plan_destroy(sdp_plan* p) {
   cudaFree(p->d_dem_off); cudaFree(p->d_rec_off); cudaFree(p->d_order);
   cudaFree(p->d_rec); cudaFree(p->d_Dn); cudaFree(p->d_counter); cudaFree(p->d_fb_count);
   cudaFree(p->d_fb_list); cudaFree(p->d_kscratch); cudaFree(p->d_total); cudaFree(p->d_qt);
+  cudaFree(p->d_pq);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   cudaSetDevice(prev);
@@ -253,6 +273,10 @@ int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out) {
                    (reinterpret_cast<uintptr_t>(d->demands) & 15) == 0;
   for (int b = 0; stream_ok && b < d->B; ++b) stream_ok = (d->dem_off_host[b] & 3) == 0;
   if (stream_ok) chk(alloc_copy<unsigned char>(&p->d_qt, nullptr, batch_stream_qt_bytes(p->n_max, p->Q)));
+  // the pipelined kernel bulk-copies the same way, for tours of n <= 1024
+  if (stream_ok && pipe_supported(p->n_max, p->Q))
+    chk(alloc_copy<unsigned char>(&p->d_pq, nullptr,
+                                  pipe_ring_bytes(p->n_max, p->Q, pipe_grid(p->S, p->B))));
   if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
   if (e != cudaSuccess) {
@@ -261,7 +285,8 @@ int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out) {
     return e == cudaErrorMemoryAllocation ? pfail(SDP_ERR_OOM, "plan allocation failed")
                                           : pcuda(e, "plan create");
   }
-  int rc = configure(p, -1, 16);  // streaming kernel when the plan allows it
+  int rc = configure(p, -2, 16);  // pipelined kernel when the plan allows it
+  if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, -1, 16);  // else the streaming one
   if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 0, 16);  // TMEM staging when the tours fit
   if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 4, 16);
   if (rc == SDP_ERR_UNSUPPORTED) rc = configure(p, 1, 8);
@@ -353,7 +378,7 @@ int plan_autotune(sdp_plan* p, void* stream, const char* cache_path, int min_rin
   uint32_t* status;
   int rc = status_word(&status);
   if (rc) return rc;
-  const int warps_c[] = {-1, 0, 1, 2, 4, 8};  // -1 = streaming, 0 = TMEM staging
+  const int warps_c[] = {-2, -1, 0, 1, 2, 4, 8};  // -2 pipelined, -1 streaming, 0 TMEM staging
   const int ring_c[] = {8, 16};
   float best = 1e30f;
   int bw = p->warps, br = p->ring;
@@ -362,7 +387,7 @@ int plan_autotune(sdp_plan* p, void* stream, const char* cache_path, int min_rin
   cudaEventCreate(&b);
   for (int w : warps_c)
     for (int r : ring_c) {
-      if (w < 0 && r != 16) continue;  // the streaming kernel has one ring size
+      if (w < 0 && r != 16) continue;  // the pipelined / streaming kernels have one ring size
       if (r < min_ring) continue;
       if (configure(p, w, r)) continue;
       float tsum = 0.f;

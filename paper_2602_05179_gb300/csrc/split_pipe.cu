@@ -1,0 +1,715 @@
+// split_pipe.cu -- pipelined Split (SDP_ALGO_PIPE, and the batched plans'
+// pipelined kernel) for sm_103a.
+//
+// Why.  A DP lane walks its scenario's positions in tour order, so it needs
+// the demand of customer s_i at step i.  Holding a whole row by customer on
+// chip for the life of a tile (the DEQUE kernels) caps an SM at 16 tiles
+// (TMEM) and 8 (shared memory) at n = 500; a lane step of the deque is a
+// short dependent chain that needs more warps than that to keep the
+// schedulers busy (measured on the bare step at n = 496, S = 10^6: 16 / 24 /
+// 32 / 40 warps per SM gave 1.04 / 0.84 / 0.72 / 0.71 ms).  Here:
+//
+//   producers (8 warps): TMA bulk copies (cp.async.bulk + mbarrier, four
+//     16 KB stages, L2 evict-first: every demand is read once) bring R
+//     contiguous int32 demand rows into shared memory; the warps narrow them
+//     to uint8 (Q <= 254) or uint16, clamp them to [0, Q+1], permute them
+//     into tour order and write them to the CTA's ring of kSlots tile slots
+//     (32 rows of `stride` bytes each) in global memory.  The ring of all
+//     SMs (about 78 MB at n = 500) stays in L2, so the tour-ordered rows are
+//     written and read back without a DRAM round trip.  A slot is published
+//     through a shared counter (release / acquire) after a CTA-scope fence;
+//     its readers are warps of the same CTA.
+//   DP warps (24): claim the CTA's items in order from a shared counter, one
+//     32-scenario tile per warp, one scenario per lane; each lane reads its
+//     tour-ordered row 16 positions at a time (one block ahead, from L2)
+//     and runs the deque step below; predecessors go through a per-warp
+//     shared-memory transpose and leave as 32-byte row segments (the
+//     per-lane stores of one word per row that this replaces took 1.8 ms of a
+//     1.0 ms kernel's time at n = 496 through their 32 sector requests each).
+//   Work: groups of kGroup consecutive tiles of one tour, claimed from a
+//     global counter longest tour first, so the load balances itself.
+//
+// DP (Eq. eqdpA in the K-form of sdp_internal.cuh): K(i) = min over the
+// capacity window of psi(p) + ce_i, psi(p) = K(p) + a_{p+1}, with the window
+// candidates kept in a monotone deque per lane (Algorithm "2D Kernel for
+// Splitting" in the linear form of Vidal 2016 for hard capacity): pop from
+// the back every entry with a larger psi (an equal psi is older and stays:
+// smallest p on ties), push p = i - 1, pop from the front every entry whose
+// route p+1..i exceeds Q; the front is the argmin.  An entry is
+// (psi bits, L(p) << 16 | p) with the prefix load L taken mod 2^16, and the
+// lane keeps Lent = L(i) << 16 | i, so "route p+1..i exceeds Q" is the one
+// unsigned compare Lent - entry > (Q << 16 | 0xFFFF): the prefix loads of the
+// entries tested differ by at most 2Q + 1 < 2^16 (Q <= 32767) and
+// i - p < 2^16.  Without a demand above Q in the tile:
+//   - a new psi below the front's (the deque minimum) pops every entry, so
+//     the deque restarts at the new entry and the back-pop loop needs no
+//     emptiness test (it stops at the front at the latest);
+//   - the newest entry (route s_i alone, load q_i <= Q) never pops from the
+//     front, so neither loop empties the deque;
+//   - the deque holds at most 12 entries every 4 steps (the ring has 16): a
+//     lane over that is flagged (its scenario is recomputed by the plain
+//     kernel) and its deque restarts at its newest entry, so the ring always
+//     holds the deque it describes and both loops end.  (At n = 500 the
+//     largest deque seen in 64,000 seeded scenarios had 12 entries.)
+// Tiles with a demand above Q (flagged by the producers) take a checked step
+// with emptiness tests, the first infeasible position recorded and an exact
+// ring test at every push.
+#include <math_constants.h>
+
+#include "async_copy.cuh"
+#include "sdp_internal.cuh"
+
+namespace sdp {
+
+namespace {
+
+constexpr int kDp = 24;                        // DP warps per CTA
+constexpr int kProd = 8;                       // producer warps per CTA
+constexpr int kProdThreads = kProd * 32;
+constexpr int kThreads = (kDp + kProd) * 32;   // 1024 threads: 64 registers each
+constexpr int kSlots = 32;                     // tile slots per CTA in the ring
+constexpr uint32_t kStage = 16u * 1024u;       // bytes per producer stage
+constexpr int kNStage = 4;                     // stages (copies in flight per CTA)
+constexpr int kGroup = 16;                     // tiles per claimed group
+constexpr int kRing = 16;                      // deque entries per lane
+constexpr uint32_t kRingBytes = (uint32_t)kRing * 256u;  // 32 lanes x 8 bytes per entry
+constexpr uint32_t kRingMask = (uint32_t)(kRing - 1) << 8;
+constexpr uint32_t kOutBytes = 32u * 32u;      // predecessor stage per warp: 32 rows x 32 bytes
+constexpr int kCheckEvery = 4;                 // steps between ring tests (lean step)
+constexpr uint32_t kMaxAtCheck = 12u;          // entries allowed at a test (+4 pushes <= 16)
+
+// Barrier of the producer warps only (named barrier 1), OR-reducing v.
+__device__ __forceinline__ bool prod_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(kProdThreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void prod_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kProdThreads) : "memory");
+}
+
+// ------------------------------------------------------------------ the DP
+// One lane's deque (see the file comment).  Ring slots are byte offsets,
+// multiples of 256 (32 lanes x 8 bytes), kept unwrapped and masked on use.
+struct Lane {
+  uint32_t rb;          // shared address of this lane's entry in ring slot 0
+  uint32_t head, tail;  // offsets of the front and of the next free slot
+  uint32_t Lent;        // L(i) << 16 | i (lean); L(i) << 16 (checked)
+  uint32_t fent;        // front entry: L(p) << 16 | p
+  float K, fpsi, bpsi;
+  bool ovf;             // the deque outgrew the ring: recompute the scenario
+
+  __device__ __forceinline__ uint32_t at(uint32_t off) const { return rb + (off & kRingMask); }
+  __device__ __forceinline__ void init(uint32_t ring, int lane) {
+    rb = ring + 8u * (uint32_t)lane;
+    head = tail = 0u;
+    Lent = fent = 0u;
+    K = 0.f;
+    fpsi = CUDART_INF_F;  // the first step restarts the deque at p = 0
+    bpsi = -CUDART_INF_F;
+    ovf = false;
+  }
+  // position i: demand qh = q_i << 16 and record (a_i, ce_i); no demand
+  // above Q in the tile
+  __device__ __forceinline__ void step(uint32_t qh, float a, float ce, uint32_t Qc) {
+    const float psi = __fadd_rn(K, a);
+    const uint32_t ent = Lent;
+    Lent += qh + 1u;
+    if (psi < fpsi) {  // below the minimum: every entry pops
+      tail = head;
+      fpsi = psi;
+      fent = ent;
+      bpsi = -CUDART_INF_F;
+    }
+    while (bpsi > psi) {
+      tail -= 256u;
+      bpsi = lds_f32(at(tail - 256u));
+    }
+    sts_u2(at(tail), __float_as_uint(psi), ent);
+    tail += 256u;
+    bpsi = psi;
+    while (Lent - fent > Qc) {
+      head += 256u;
+      const uint2 e = lds_u2(at(head));
+      fpsi = __uint_as_float(e.x);
+      fent = e.y;
+    }
+    K = __fadd_rn(fpsi, ce);
+  }
+  // every kCheckEvery lean steps: more than kMaxAtCheck entries flags the
+  // lane and restarts its deque at the newest entry
+  __device__ __forceinline__ void check() {
+    if (tail - head > kMaxAtCheck * 256u) {
+      ovf = true;
+      head = tail - 256u;
+      const uint2 e = lds_u2(at(head));
+      fpsi = __uint_as_float(e.x);
+      fent = e.y;
+    }
+  }
+  // position i of a tile with a demand above Q (Lent = L(i-1) << 16 here)
+  __device__ __forceinline__ void step_chk(int i, uint32_t qh, float a, float ce, uint32_t Qc,
+                                           uint32_t Qh, int n, uint32_t& first_inf) {
+    const float psi = __fadd_rn(K, a);
+    const uint32_t ent = Lent | (uint32_t)(i - 1);
+    while (bpsi > psi) {
+      tail -= 256u;
+      bpsi = tail == head ? -CUDART_INF_F : lds_f32(at(tail - 256u));
+    }
+    if (tail == head) {  // emptied: the new entry becomes the front
+      fpsi = psi;
+      fent = ent;
+    }
+    if (tail - head >= kRingBytes) {  // full: flagged, restart at the new entry
+      ovf = true;
+      head = tail;
+      fpsi = psi;
+      fent = ent;
+    }
+    const uint32_t naddr = tail;
+    sts_u2(at(tail), __float_as_uint(psi), ent);
+    tail += 256u;
+    bpsi = psi;
+    Lent += qh;
+    if (qh > Qh && first_inf > (uint32_t)n) first_inf = (uint32_t)i;
+    // the newest entry stays even when q_i > Q (the guard)
+    while (((Lent | 0xFFFFu) - fent) > Qc && head != naddr) {
+      head += 256u;
+      const uint2 e = lds_u2(at(head));
+      fpsi = __uint_as_float(e.x);
+      fent = e.y;
+    }
+    K = __fadd_rn(fpsi, ce);
+  }
+};
+
+// demand of position u (0..15) of a 16-position block (V = sizeof(QT)
+// 16-byte vectors), shifted to bits 16..31
+template <typename QT>
+__device__ __forceinline__ uint32_t q_at(const uint4* c, int u) {
+  constexpr int V = (int)sizeof(QT);
+  constexpr int PER = 4 / (int)sizeof(QT);
+  const int w = u / PER, e = u % PER;
+  const uint4 v = w < 4 ? c[0] : c[V - 1];  // selects, no indexed array (u may be dynamic)
+  const uint32_t x = (w & 3) == 0 ? v.x : (w & 3) == 1 ? v.y : (w & 3) == 2 ? v.z : v.w;
+  if (sizeof(QT) == 1) return __byte_perm(x, 0u, 0x4044u | ((uint32_t)e << 8));
+  return e == 0 ? (x << 16) : (x & 0xFFFF0000u);
+}
+
+// Tour records (a_i, ce_i) of position k + 1: shared memory (one tour) or
+// the plan's records through the read-only path.
+struct SmemRec2 {
+  uint32_t base;  // shared address of float2 [n]
+  __device__ __forceinline__ float2 operator()(int k) const {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(base + 8u * (uint32_t)k));
+    return v;
+  }
+};
+struct GlobalRec2 {
+  const StepRec* p;
+  __device__ __forceinline__ float2 operator()(int k) const {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p + k));
+    return make_float2(v.y, v.z);
+  }
+};
+
+// Predecessors of one warp tile through a [32 rows][8 words] shared stage:
+// a 32-byte row segment holds W = 32 / sizeof(PT) positions.  Lane l writes
+// word j of its row at l * 8 + (j ^ ((l >> 2) & 7)) and the flush reads row
+// r word k at r * 8 + (k ^ ((r >> 2) & 7)): both conflict-free.
+template <typename PT>
+struct PredStage {
+  uint32_t* st;     // this warp's stage
+  PT* tile;         // predecessor rows of the tile
+  int n, rows, lane;
+  bool pairs;       // uint16: every row segment starts on 4 bytes (n even, aligned base)
+  uint32_t pend;    // uint16: low half of the word being packed
+  static constexpr int W = 32 / (int)sizeof(PT);
+  __device__ __forceinline__ void put(int pos, uint32_t p) {  // pos = (i - 1) % W
+    const int sw = (lane >> 2) & 7;
+    if (sizeof(PT) == 2) {
+      if ((pos & 1) == 0) {
+        pend = p & 0xFFFFu;
+      } else {
+        st[lane * 8 + ((pos >> 1) ^ sw)] = pend | (p << 16);
+      }
+    } else {
+      st[lane * 8 + (pos ^ sw)] = p;
+    }
+  }
+  // positions i0 .. i0 + cnt - 1 (1-based) of every row
+  __device__ __forceinline__ void flush(int i0, int cnt) {
+    if (sizeof(PT) == 2 && (cnt & 1)) st[lane * 8 + ((cnt >> 1) ^ ((lane >> 2) & 7))] = pend;
+    __syncwarp();
+    constexpr int PER = 4 / (int)sizeof(PT);
+    const int k = lane & 7;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int r = 4 * m + (lane >> 3);
+      const uint32_t v = st[r * 8 + (k ^ (m & 7))];
+      if (r < rows && k * PER < cnt) {
+        PT* dst = tile + (int64_t)r * n + (i0 - 1) + k * PER;
+        if (sizeof(PT) == 4) {
+          *reinterpret_cast<uint32_t*>(dst) = v;
+        } else if (pairs && k * 2 + 1 < cnt) {
+          *reinterpret_cast<uint32_t*>(dst) = v;
+        } else {
+          dst[0] = (PT)(v & 0xFFFFu);
+          if (k * 2 + 1 < cnt) dst[1] = (PT)(v >> 16);
+        }
+      }
+    }
+    __syncwarp();
+  }
+};
+
+// One 32-scenario tile: lane l runs scenario s0 + l over positions 1..n from
+// its tour-ordered row.  CHECK: the tile has a demand above Q.
+template <typename QT, typename PT, bool PRED, bool CHECK, typename REC>
+__device__ __forceinline__ void pipe_tile(int n, int Q, const unsigned char* qrow, uint32_t ring,
+                                          const REC rec, int lane, PredStage<PT>& ps,
+                                          float* K_out, uint32_t* first_inf_out, bool* bad) {
+  constexpr int E = 16;                    // positions per block
+  constexpr int V = (int)sizeof(QT);       // 16-byte vectors per block
+  constexpr int W = PredStage<PT>::W;      // positions per predecessor flush (16 % W == 0)
+  const uint32_t Qh = (uint32_t)Q << 16, Qc = Qh | 0xFFFFu;
+  Lane st;
+  st.init(ring, lane);
+  uint32_t first_inf = (uint32_t)n + 1u;
+  const int nblk = n / E;                  // whole blocks
+  const int last = (n + E - 1) / E - 1;    // last block holding a position
+  const uint4* src = reinterpret_cast<const uint4*>(qrow);
+  uint4 c[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) c[v] = ld_cg_v4(src + v);
+  auto pred_of = [&](int i) -> uint32_t {
+    if (CHECK && (uint32_t)i >= first_inf) return 0xFFFFFFFFu;
+    return st.fent & 0xFFFFu;
+  };
+  for (int b = 0; b < nblk; ++b) {
+    const int bn = min(b + 1, last);
+    uint4 nx[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) nx[v] = ld_cg_v4(src + V * bn + v);
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      const int i = b * E + u + 1;
+      const float2 r = rec(i - 1);
+      const uint32_t qh = q_at<QT>(c, u);
+      if (CHECK) {
+        st.step_chk(i, qh, r.x, r.y, Qc, Qh, n, first_inf);
+      } else {
+        st.step(qh, r.x, r.y, Qc);
+        if (u % kCheckEvery == kCheckEvery - 1) st.check();
+      }
+      if (PRED) {
+        ps.put(u % W, pred_of(i));
+        if (u % W == W - 1) ps.flush(i - W + 1, W);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) c[v] = nx[v];
+  }
+  // ragged tail (fewer than E positions) from the block loaded last
+  const int i1 = nblk * E + 1;
+  for (int i = i1; i <= n; ++i) {
+    const int u = i - i1;
+    const float2 r = rec(i - 1);
+    const uint32_t qh = q_at<QT>(c, u);
+    if (CHECK) {
+      st.step_chk(i, qh, r.x, r.y, Qc, Qh, n, first_inf);
+    } else {
+      st.step(qh, r.x, r.y, Qc);
+      st.check();
+    }
+    if (PRED) {
+      ps.put(u % W, pred_of(i));
+      if (u % W == W - 1 || i == n) ps.flush(i - u % W, u % W + 1);
+    }
+  }
+  *K_out = st.K;
+  *first_inf_out = first_inf;
+  *bad = st.ovf;
+}
+
+// ------------------------------------------------------------------ kernel
+template <typename QT, typename PT, bool PRED, bool BATCH>
+__global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[kNStage];
+  __shared__ uint32_t slot_ready[kSlots], slot_free[kSlots], slot_inf[kSlots];
+  __shared__ int32_t slot_b[kSlots];
+  __shared__ int64_t slot_s0[kSlots];
+  __shared__ uint32_t next_item, final_count, abort_flag;
+  __shared__ int64_t group_id;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int Q = a.Q;
+  const int64_t S = a.S;
+  // shared: stages | DP rings | predecessor stages | (one tour) records | columns
+  const uint32_t rings = smem_u32(smem) + kNStage * kStage;
+  uint32_t* ostage = reinterpret_cast<uint32_t*>(smem + kNStage * kStage + (size_t)kDp * kRingBytes);
+  unsigned char* tail_sm = smem + kNStage * kStage + (size_t)kDp * kRingBytes +
+                           (PRED ? (size_t)kDp * kOutBytes : 0);
+  float2* rec2 = reinterpret_cast<float2*>(tail_sm);
+  uint16_t* cols = reinterpret_cast<uint16_t*>(tail_sm + (BATCH ? 0 : (size_t)a.n1 * sizeof(float2)));
+  const uint32_t bar_base = smem_u32(&bars[0]);  // stage k's barrier at bar_base + 8k
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kNStage; ++k) mbar_init(bar_base + 8u * k, 1);
+    mbar_fence_init();
+    next_item = 0u;
+    final_count = 0xFFFFFFFFu;
+    abort_flag = 0u;
+  }
+  if (threadIdx.x < kSlots) {
+    slot_ready[threadIdx.x] = 0u;
+    slot_free[threadIdx.x] = 0u;
+  }
+  if (!BATCH) {
+    for (int k = threadIdx.x; k < a.n1; k += blockDim.x) {
+      const StepRec r = a.rec[k];
+      rec2[k] = make_float2(r.a, r.ce);
+    }
+  }
+  __syncthreads();
+  unsigned char* qslots = a.qt + (int64_t)blockIdx.x * kSlots * 32 * a.stride;
+  const int64_t tpt = (S + 31) / 32;                 // tiles per tour
+  const int64_t gpt = (tpt + kGroup - 1) / kGroup;   // groups per tour
+  const int64_t groups = gpt * a.B;
+
+  if (warp >= kDp) {
+    // ------------------------------------------------------------- producers
+    const int ptid = (int)threadIdx.x - kDp * 32;
+    const uint64_t pol = l2_evict_first_policy();
+    constexpr int PER = 4 / (int)sizeof(QT);  // demands per 32-bit output word
+    const int sw = (int)(a.stride / 4);       // words per slot row
+    // Thread ptid narrows words k = kw + 128 j (j < kWords) of the rows of
+    // parity ptid / 128: the columns of its words stay in registers for the
+    // whole tour (a word is PER positions).
+    constexpr int kWordsMax = kPipeMaxN * (int)sizeof(QT) / 4;     // words per row at most
+    constexpr int kWords = (kWordsMax + 127) / 128;                // words per thread
+    const int kw = ptid & 127, rpar = ptid >> 7;
+    uint32_t wcol[kWords][PER];  // column of each position (0 past n)
+    uint32_t wvalid[kWords];     // bit e: position PER * k + e < n
+    int cur_b = -1, n = 0, R = 32, subs = 1, wq = 0;
+    uint32_t li = 0;  // items claimed by this CTA so far
+    int64_t gk = 0;   // chunks consumed through the stages so far (all groups)
+    int64_t gi = 0;   // chunks issued so far; chunk x uses stage x % kNStage
+    int mn_all = 0;
+    bool failed = false;
+    auto bar_of = [&](int64_t x) -> uint32_t { return bar_base + 8u * (uint32_t)(x % kNStage); };
+    auto par_of = [&](int64_t x) -> uint32_t { return (uint32_t)(x / kNStage) & 1u; };
+    while (!failed) {
+      if (ptid == 0) group_id = (int64_t)atomicAdd(a.counter, 1ull);
+      prod_sync();
+      const int64_t gid = group_id;
+      if (gid >= groups) break;
+      const int b = BATCH ? a.order[gid / gpt] : 0;
+      const int64_t t0 = (gid % gpt) * kGroup;
+      const int m = (int)imin64(kGroup, tpt - t0);  // items in the group
+      if (b != cur_b) {  // the tour's columns and chunking
+        prod_sync();     // every producer is done with the old columns
+        cur_b = b;
+        n = BATCH ? a.n[b] : a.n1;
+        wq = (n + PER - 1) / PER;
+        const StepRec* rec = a.rec + (BATCH ? a.rec_off[b] : 0);
+        for (int k = ptid; k < wq * PER; k += kProdThreads)
+          cols[k] = k < n ? (BATCH ? (uint16_t)rec[k].col : a.cols[k]) : (uint16_t)0;
+        R = 32;
+        while ((uint32_t)R * (uint32_t)n * 4u > kStage) R >>= 1;
+        subs = 32 / R;
+        prod_sync();
+#pragma unroll
+        for (int j = 0; j < kWords; ++j) {
+          const int k = kw + 128 * j;
+          wvalid[j] = 0u;
+#pragma unroll
+          for (int e = 0; e < PER; ++e) {
+            const bool v = k < wq && PER * k + e < n;
+            wcol[j][e] = v ? (uint32_t)cols[PER * k + e] * 4u : 0u;  // byte offset in a row
+            wvalid[j] |= (v ? 1u : 0u) << e;
+          }
+        }
+      }
+      const int32_t* dem = a.demands + (BATCH ? a.dem_off[b] : 0);
+      const int nch = m * subs;
+      const int64_t g0 = gk;  // global index of the group's chunk 0
+      auto crow0 = [&](int c) -> int64_t { return (t0 + c / subs) * 32 + (int64_t)(c % subs) * R; };
+      auto cbytes = [&](int c) -> uint32_t {
+        const int64_t r0 = crow0(c);
+        const int rows = r0 >= S ? 0 : (int)imin64(R, S - r0);
+        return ((uint32_t)rows * (uint32_t)n * 4u) & ~15u;
+      };
+      // chunk c of the group into its stage (an L2 prefetch of later
+      // chunks was measured slower: 1.48 -> 1.58 ms at n = 500, S = 10^6)
+      auto issue = [&](int c) {
+        const uint32_t bytes = cbytes(c);
+        const int64_t x = g0 + c;
+        mbar_arrive_tx(bar_of(x), bytes);
+        if (bytes)
+          bulk_g2s_hint(smem_u32(smem) + (uint32_t)(x % kNStage) * kStage, dem + crow0(c) * n,
+                        bytes, bar_of(x), pol);
+        gi = x + 1;
+      };
+      if (ptid == 0)
+        for (int c = 0; c < kNStage && c < nch; ++c) issue(c);
+      for (int c = 0; c < nch; ++c) {
+        const uint32_t item = li + (uint32_t)(c / subs);
+        const uint32_t slot = item % kSlots;
+        if (c % subs == 0) {
+          // the slot's previous item (item - kSlots) must be finished
+          bool ok = true;
+          if (item >= kSlots) {
+            const uint32_t need = item - kSlots + 1;
+            if (ld_acquire_shared(&slot_free[slot]) < need) {
+              const uint64_t tw = global_ns();
+              while (ld_acquire_shared(&slot_free[slot]) < need) {
+                if (ld_acquire_shared(&abort_flag) || global_ns() - tw > a.wait_ns) {
+                  ok = false;
+                  break;
+                }
+                __nanosleep(256);
+              }
+            }
+          }
+          if (prod_sync_or(!ok)) {
+            failed = true;
+            break;
+          }
+          if (ptid == 0) {
+            slot_inf[slot] = 0u;
+            slot_b[slot] = b;
+            slot_s0[slot] = (t0 + c / subs) * 32;
+          }
+        }
+        const int64_t x = g0 + c;
+        const bool ok = mbar_wait(bar_of(x), par_of(x));
+        const int64_t r0 = crow0(c);
+        const int rows = r0 >= S ? 0 : (int)imin64(R, S - r0);
+        int32_t* sq = reinterpret_cast<int32_t*>(smem + (size_t)(x % kNStage) * kStage);
+        // the last few demands of a ragged last chunk (not a whole 16 bytes)
+        const int elems = rows * n;
+        const int bulk_elems = (int)((((uint32_t)elems * 4u) & ~15u) >> 2);
+        if (elems > bulk_elems) {  // (uniform) the stragglers must land before the narrow
+          if (ok && ptid < elems - bulk_elems)
+            sq[bulk_elems + ptid] = __ldg(dem + r0 * n + bulk_elems + ptid);
+          if (prod_sync_or(!ok)) {
+            failed = true;
+            break;
+          }
+        }
+        // narrow + permute the chunk's rows into the slot; rows past S are
+        // written as zero demands (their lanes run on them, outputs dropped)
+        const int rbase = (c % subs) * R;
+        uint32_t* out = reinterpret_cast<uint32_t*>(qslots + ((int64_t)slot * 32 + rbase) * a.stride);
+        const uint32_t sq_b = smem_u32(sq);
+#pragma unroll
+        for (int j = 0; j < kWords; ++j) {
+          const int k = kw + 128 * j;
+          if (k >= wq || !ok) break;
+          for (int r = rpar; r < R; r += 2) {
+            uint32_t word = 0u;
+            if (r < rows) {
+              const uint32_t rb = sq_b + (uint32_t)(r * n) * 4u;
+              int v[PER];
+#pragma unroll
+              for (int e = 0; e < PER; ++e) {
+                int x;
+                asm volatile("ld.shared.s32 %0, [%1];" : "=r"(x) : "r"(rb + wcol[j][e]));
+                v[e] = (wvalid[j] >> e) & 1u ? x : 0;
+              }
+              uint32_t mx = (uint32_t)v[0];
+#pragma unroll
+              for (int e = 1; e < PER; ++e) mx = max(mx, (uint32_t)v[e]);
+              if (mx <= (uint32_t)Q) {
+                word = sizeof(QT) == 1
+                           ? __byte_perm(__byte_perm(v[0], v[1 % PER], 0x0040),
+                                         __byte_perm(v[2 % PER], v[3 % PER], 0x0040), 0x5410)
+                           : __byte_perm(v[0], v[1 % PER], 0x5410);
+              } else {  // a demand above Q or below 0: clamp to [0, Q+1]
+                bool inf = false;
+#pragma unroll
+                for (int e = 0; e < PER; ++e) {
+                  inf |= v[e] > Q;
+                  mn_all = min(mn_all, v[e]);
+                  word |= (uint32_t)min(max(v[e], 0), Q + 1) << (e * 8 * (int)sizeof(QT));
+                }
+                if (inf) atomicOr(&slot_inf[slot], 1u << (rbase + r));
+              }
+            }
+            out[(int64_t)r * sw + k] = word;
+          }
+        }
+        const bool item_done = (c % subs) == subs - 1;
+        if (item_done) __threadfence_block();  // the slot's rows before its publication
+        // also: the stage is free again; a copy that never landed (ok false
+        // in any thread) stops every producer together
+        if (prod_sync_or(!ok)) {
+          failed = true;
+          break;
+        }
+        gk = x + 1;
+        if (ptid == 0) {
+          // (a.stall: fault injection for tests -- nothing is published, and
+          // the DP warps' waits run out after a.wait_ns)
+          if (item_done && !a.stall) st_release_shared(&slot_ready[slot], item + 1);
+          if (c + kNStage < nch) {
+            fence_proxy_async();
+            issue(c + kNStage);
+          }
+        }
+      }
+      if (!failed) li += (uint32_t)m;
+    }
+    if (failed) {
+      if (ptid == 0) {
+        atomicOr(a.status, SDP_FLAG_DEVICE_CHECK);
+        st_release_shared(&abort_flag, 1u);
+        // let copies still in flight land (again with a time limit) before
+        // shared memory goes
+        for (int64_t x = gk; x < gi; ++x) mbar_wait(bar_of(x), par_of(x));
+      }
+      prod_sync();
+    } else if (ptid == 0) {
+      st_release_shared(&final_count, li);
+    }
+    if (mn_all < 0) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
+    return;
+  }
+
+  // ------------------------------------------------------------------ DP warps
+  const uint32_t ring = rings + kRingBytes * (uint32_t)warp;
+  PredStage<PT> ps{};
+  ps.st = ostage + warp * (kOutBytes / 4);
+  ps.lane = lane;
+  uint32_t any_inf = 0, any_fb = 0;
+  bool timed_out = false;
+  for (;;) {
+    uint32_t li = 0;
+    if (lane == 0) li = atomicAdd(&next_item, 1u);
+    li = __shfl_sync(0xffffffffu, li, 0);
+    const uint32_t slot = li % kSlots;
+    // wait until item li is published, or the producers are done
+    bool have = ld_acquire_shared(&slot_ready[slot]) > li;
+    if (!have) {
+      const uint64_t tw = global_ns();
+      while (true) {
+        if (ld_acquire_shared(&slot_ready[slot]) > li) {
+          have = true;
+          break;
+        }
+        if (ld_acquire_shared(&final_count) <= li) break;
+        if (ld_acquire_shared(&abort_flag)) break;
+        if (global_ns() - tw > a.wait_ns) {
+          timed_out = true;
+          st_release_shared(&abort_flag, 1u);  // producers and the other DP warps stop too
+          break;
+        }
+        __nanosleep(512);  // few polls: a waiting warp leaves the issue slots to the others
+      }
+    }
+    if (!__all_sync(0xffffffffu, have)) break;
+    const int b = slot_b[slot];
+    const int64_t s0 = slot_s0[slot];
+    const uint32_t tf = slot_inf[slot];
+    const int n = BATCH ? a.n[b] : a.n1;
+    const int rows = (int)imin64(32, S - s0);
+    const bool live = lane < rows;
+    const unsigned char* qrow = qslots + ((int64_t)slot * 32 + lane) * a.stride;
+    if (PRED) {
+      ps.tile = reinterpret_cast<PT*>(a.pred) + s0 * n;
+      ps.n = n;
+      ps.rows = rows;
+      ps.pairs = sizeof(PT) == 4 || ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.pred) & 3) == 0);
+    }
+    float K;
+    uint32_t first_inf;
+    bool bad;
+    if (BATCH) {
+      const GlobalRec2 rec{a.rec + a.rec_off[b]};
+      if (tf)
+        pipe_tile<QT, PT, PRED, true>(n, Q, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
+      else
+        pipe_tile<QT, PT, PRED, false>(n, Q, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
+    } else {
+      const SmemRec2 rec{smem_u32(rec2)};
+      if (tf)
+        pipe_tile<QT, PT, PRED, true>(n, Q, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
+      else
+        pipe_tile<QT, PT, PRED, false>(n, Q, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
+    }
+    __syncwarp();  // every lane is done with the slot
+    if (lane == 0) st_release_shared(&slot_free[slot], li + 1);
+    bad = bad && live;
+    if (live) {
+      const int64_t g = BATCH ? (int64_t)b * S + s0 + lane : s0 + lane;
+      if (bad) {
+        const uint32_t f = atomicAdd(a.fb_count, 1u);
+        if (BATCH)
+          a.fb_list[f] = (unsigned long long)g;
+        else
+          a.fb_list1[f] = (uint32_t)g;
+      } else {
+        a.cost[g] = first_inf <= (uint32_t)n ? CUDART_INF_F : (float)((double)K + a.Dn[b]);
+      }
+    }
+    any_inf |= tf;
+    any_fb |= __ballot_sync(0xffffffffu, bad);
+  }
+  if (lane == 0) {
+    if (any_inf) atomicOr(a.status, SDP_FLAG_INFEASIBLE);
+    if (any_fb) atomicOr(a.status, SDP_FLAG_FALLBACK);
+    if (timed_out) atomicOr(a.status, SDP_FLAG_DEVICE_CHECK);
+  }
+}
+
+size_t pipe_smem(const PipeArgs& a, bool pred) {
+  const int n = a.batched ? kPipeMaxN : a.n1;
+  return (size_t)kNStage * kStage + (size_t)kDp * kRingBytes + (pred ? (size_t)kDp * kOutBytes : 0) +
+         (a.batched ? 0 : (size_t)n * sizeof(float2)) + ((size_t)n + 8) * sizeof(uint16_t);
+}
+
+template <typename QT, typename PT, bool PRED, bool BATCH>
+int launch_k(const PipeArgs& a, cudaStream_t st) {
+  auto k = split_pipe_kernel<QT, PT, PRED, BATCH>;
+  const size_t smem = pipe_smem(a, PRED);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  k<<<pipe_grid(a.S, a.B), kThreads, smem, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <typename QT>
+int launch_q(const PipeArgs& a, cudaStream_t st) {
+  if (a.batched) return launch_k<QT, uint16_t, false, true>(a, st);
+  if (!a.pred) return launch_k<QT, uint16_t, false, false>(a, st);
+  if (a.pred_dtype == SDP_PRED_U16) return launch_k<QT, uint16_t, true, false>(a, st);
+  return launch_k<QT, int32_t, true, false>(a, st);
+}
+
+}  // namespace
+
+bool pipe_supported(int n, int Q) { return n >= 1 && n <= kPipeMaxN && Q >= 1 && Q <= 32767; }
+
+int pipe_grid(int64_t S, int B) {
+  const int64_t groups = (int64_t)B * ((((S + 31) / 32) + kGroup - 1) / kGroup);
+  return (int)imin64(num_sms(), groups < 1 ? 1 : groups);
+}
+
+size_t pipe_ring_bytes(int n_max, int Q, int grid) {
+  return (size_t)grid * kSlots * 32 * (size_t)pipe_row_stride(n_max, Q);
+}
+
+int launch_split_pipe(const PipeArgs& a0, cudaStream_t st) {
+  PipeArgs a = a0;
+  if (a.wait_ns == 0) a.wait_ns = kWaitLimitNs;
+  return a.Q <= 254 ? launch_q<uint8_t>(a, st) : launch_q<uint16_t>(a, st);
+}
+
+}  // namespace sdp

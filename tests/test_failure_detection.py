@@ -151,10 +151,11 @@ def test_injected_allocation_failure_of_a_plan(clean_faults):
 
 
 @pytest.mark.gpu
-def test_streaming_wait_runs_out_and_reports(clean_faults):
-    """A streaming launch whose producers publish no tile: the DP warps give
-    up after 1 ms, the call returns, the status reports a device check, and
-    the next launch is correct."""
+@pytest.mark.parametrize("algo", ["stream", "pipe"])
+def test_streaming_wait_runs_out_and_reports(clean_faults, algo):
+    """A streaming or pipelined launch whose producers publish no tile: the
+    DP warps give up after 1 ms, the call returns, the status reports a
+    device check, and the next launch is correct."""
     api = sdp()
     rng = np.random.default_rng(6)
     n, S, Q = 600, 4096, 150
@@ -166,11 +167,11 @@ def test_streaming_wait_runs_out_and_reports(clean_faults):
     torch.cuda.synchronize()
     api.status()
     api.set_fault_inject("stall:1000000")
-    api.split_eval(t, Q, qd, coords=c, algo="stream")
+    api.split_eval(t, Q, qd, coords=c, algo=algo)
     with pytest.raises(api.SdpError) as e:
         api.status()  # synchronises: the launch has returned
     assert e.value.code == api.ERR_DEVICE_CHECK
-    r = api.split_eval(t, Q, qd, coords=c, algo="stream")
+    r = api.split_eval(t, Q, qd, coords=c, algo=algo)
     torch.cuda.synchronize()
     assert api.status() & api.FLAG_DEVICE_CHECK == 0
     assert torch.equal(r["cost"], ref["cost"])

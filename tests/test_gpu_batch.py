@@ -43,7 +43,7 @@ def test_batch_small_vs_oracle_and_eager(Q, qhi, tmp_path):
     B, S = 37, 100
     n, tours, coords, dem = _batch(11 + Q, B, S, Q, 1, 300, qhi)
     plan, keep = _plan(n, tours, coords, dem, Q, S)
-    assert plan.info()["warps_per_cta"] == -1         # default: the streaming kernel
+    assert plan.info()["warps_per_cta"] == -2         # default: the pipelined kernel
     costs, means = plan.run()
     torch.cuda.synchronize()
     c1 = costs.clone()
@@ -64,7 +64,7 @@ def test_batch_small_vs_oracle_and_eager(Q, qhi, tmp_path):
     assert torch.equal(costs, c1)
     cache = str(tmp_path / "tune.txt")
     info = plan.autotune(cache)
-    assert info["warps_per_cta"] in (-1, 0, 1, 2, 4, 8) and info["ring"] in (8, 16)
+    assert info["warps_per_cta"] in (-2, -1, 0, 1, 2, 4, 8) and info["ring"] in (8, 16)
     plan.run()
     torch.cuda.synchronize()
     assert torch.equal(costs, c1)
@@ -109,6 +109,38 @@ def test_batch_stream_and_deque_plans_bit_identical(Q, qhi):
     assert torch.equal(ms[fin], md[fin])
     assert api().status() & api().FLAG_INFEASIBLE
     plan_s.close()
+    plan_d.close()
+
+
+@pytest.mark.parametrize("Q,qhi", [(150, 40), (600, 90)])
+def test_batch_pipe_and_deque_plans_bit_identical(Q, qhi):
+    """The pipelined plan kernel (every tour n <= 1024) and the DEQUE batched
+    kernel (forced by demand blocks that do not start on 16 bytes) give the
+    same bits on tours shorter and longer than a tensor-memory row, with a
+    ragged last tile (S = 164) and a few demands above Q."""
+    B, S = 31, 164
+    n, tours, coords, dem = _batch(91 + Q, B, S, Q, 1, 1024, qhi)
+    dem[5][9, 0] = Q + 1
+    plan_p, keep_p = _plan(n, tours, coords, dem, Q, S)
+    assert plan_p.info()["warps_per_cta"] == -2
+    off = np.zeros(B, np.int64)
+    off[1:] = np.cumsum(n[:-1].astype(np.int64) * S)
+    off = off + np.arange(1, B + 1)
+    buf = torch.zeros(int(off[-1] + n[-1] * S), dtype=torch.int32, device="cuda")
+    for b in range(B):
+        buf[off[b]:off[b] + n[b] * S] = torch.from_numpy(dem[b].reshape(-1)).cuda()
+    t, c, _ = keep_p
+    plan_d = api().SplitPlan(n, t, c, buf, Q, S, dem_off=off)
+    assert plan_d.info()["warps_per_cta"] >= 0
+    cp, mp = plan_p.run()
+    cd, md = plan_d.run()
+    torch.cuda.synchronize()
+    assert torch.equal(cp, cd)
+    assert torch.equal(mp.isinf(), md.isinf())
+    fin = ~mp.isinf()
+    assert torch.equal(mp[fin], md[fin])
+    assert api().status() & api().FLAG_INFEASIBLE
+    plan_p.close()
     plan_d.close()
 
 
