@@ -9,8 +9,10 @@
 // schedulers busy (measured on the bare step at n = 496, S = 10^6: 16 / 24 /
 // 32 / 40 warps per SM gave 1.04 / 0.84 / 0.72 / 0.71 ms).  Here:
 //
-//   producers (8 warps): TMA bulk copies (cp.async.bulk + mbarrier, four
-//     16 KB stages, L2 evict-first: every demand is read once) bring R
+//   producers (1 issuing + 8 narrowing warps): the issuing warp claims work,
+//     sets up slots and feeds TMA bulk copies (cp.async.bulk, four 16 KB
+//     stages with full / empty mbarriers, L2 evict-first: every demand is read
+//     once) of R
 //     contiguous int32 demand rows into shared memory; the warps narrow them
 //     to uint8 (Q <= 254) or uint16, clamp them to [0, Q+1], permute them
 //     into tour order and write them to the CTA's ring of kSlots tile slots
@@ -19,7 +21,7 @@
 //     written and read back without a DRAM round trip.  A slot is published
 //     through a shared counter (release / acquire) after a CTA-scope fence;
 //     its readers are warps of the same CTA.
-//   DP warps (24): claim the CTA's items in order from a shared counter, one
+//   DP warps (23): claim the CTA's items in order from a shared counter, one
 //     32-scenario tile per warp, one scenario per lane; each lane reads its
 //     tour-ordered row 16 positions at a time (one block ahead, from L2)
 //     and runs the deque step below; predecessors go through a per-warp
@@ -63,10 +65,10 @@ namespace sdp {
 
 namespace {
 
-constexpr int kDp = 24;                        // DP warps per CTA
-constexpr int kProd = 8;                       // producer warps per CTA
-constexpr int kProdThreads = kProd * 32;
-constexpr int kThreads = (kDp + kProd) * 32;   // 1024 threads: 64 registers each
+constexpr int kDp = 23;                        // DP warps per CTA
+constexpr int kNarrow = 8;                     // narrowing warps per CTA (+ one issuing warp)
+constexpr int kNarrowThreads = kNarrow * 32;
+constexpr int kThreads = (kDp + 1 + kNarrow) * 32;  // 1024 threads: 64 registers each
 constexpr int kSlots = 32;                     // tile slots per CTA in the ring
 constexpr uint32_t kStage = 16u * 1024u;       // bytes per producer stage
 constexpr int kNStage = 4;                     // stages (copies in flight per CTA)
@@ -78,19 +80,36 @@ constexpr uint32_t kOutBytes = 32u * 32u;      // predecessor stage per warp: 32
 constexpr int kCheckEvery = 4;                 // steps between ring tests (lean step)
 constexpr uint32_t kMaxAtCheck = 12u;          // entries allowed at a test (+4 pushes <= 16)
 
-// Barrier of the producer warps only (named barrier 1), OR-reducing v.
-__device__ __forceinline__ bool prod_sync_or(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
-      " selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(kProdThreads)
-      : "memory");
-  return r != 0;
+// Stage bookkeeping written by the issuing warp before it arms the stage's
+// full barrier (release), read by the narrowing warps after their wait on it
+// (acquire).
+struct StageMeta {
+  int32_t slot, rbase, rows, n;
+  int32_t gen;   // tour generation: the narrowing warps reload their columns when it changes
+  int32_t stop;  // no more chunks: the narrowing warps leave
+  uint32_t item; // item of the chunk
+  int32_t pad;
+};
+
+__device__ __forceinline__ uint32_t atom_add_acq_rel_shared(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;"
+               : "=r"(old) : "r"(smem_u32(p)), "r"(v) : "memory");
+  return old;
 }
-__device__ __forceinline__ void prod_sync() {
-  asm volatile("bar.sync 1, %0;" ::"r"(kProdThreads) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Wait for phase `parity` of an mbarrier, giving up on the abort flag or
+// after limit_ns; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_abortable(uint32_t bar, uint32_t parity,
+                                                    const uint32_t* abort_flag, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (ld_acquire_shared(abort_flag) || global_ns() - t0 > limit_ns) return false;
+  }
 }
 
 // ------------------------------------------------------------------ the DP
@@ -342,12 +361,13 @@ __device__ __forceinline__ void pipe_tile(int n, int Q, const unsigned char* qro
 template <typename QT, typename PT, bool PRED, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[kNStage];
+  __shared__ __align__(8) uint64_t full_bar[kNStage], empty_bar[kNStage];
+  __shared__ StageMeta smeta[kNStage];
   __shared__ uint32_t slot_ready[kSlots], slot_free[kSlots], slot_inf[kSlots];
+  __shared__ uint32_t item_cnt[kSlots], item_need[kSlots];
   __shared__ int32_t slot_b[kSlots];
   __shared__ int64_t slot_s0[kSlots];
   __shared__ uint32_t next_item, final_count, abort_flag;
-  __shared__ int64_t group_id;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int Q = a.Q;
@@ -359,9 +379,14 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
                            (PRED ? (size_t)kDp * kOutBytes : 0);
   float2* rec2 = reinterpret_cast<float2*>(tail_sm);
   uint16_t* cols = reinterpret_cast<uint16_t*>(tail_sm + (BATCH ? 0 : (size_t)a.n1 * sizeof(float2)));
-  const uint32_t bar_base = smem_u32(&bars[0]);  // stage k's barrier at bar_base + 8k
+  // stage k: full (the issuer's expect_tx + the bulk copy) and empty (one
+  // arrival per narrowing warp) barriers
+  const uint32_t full0 = smem_u32(&full_bar[0]), empty0 = smem_u32(&empty_bar[0]);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < kNStage; ++k) mbar_init(bar_base + 8u * k, 1);
+    for (int k = 0; k < kNStage; ++k) {
+      mbar_init(full0 + 8u * k, 1);
+      mbar_init(empty0 + 8u * k, kNarrow);
+    }
     mbar_fence_init();
     next_item = 0u;
     final_count = 0xFFFFFFFFu;
@@ -383,201 +408,220 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   const int64_t gpt = (tpt + kGroup - 1) / kGroup;   // groups per tour
   const int64_t groups = gpt * a.B;
 
-  if (warp >= kDp) {
-    // ------------------------------------------------------------- producers
-    const int ptid = (int)threadIdx.x - kDp * 32;
+  constexpr int PER = 4 / (int)sizeof(QT);  // demands per 32-bit slot word
+  auto full_of = [&](int64_t x) -> uint32_t { return full0 + 8u * (uint32_t)(x % kNStage); };
+  auto empty_of = [&](int64_t x) -> uint32_t { return empty0 + 8u * (uint32_t)(x % kNStage); };
+  auto par_of = [&](int64_t x) -> uint32_t { return (uint32_t)(x / kNStage) & 1u; };
+
+  if (warp == kDp) {
+    // ------------------------------------------------------------ issuer
+    // Claims groups, sets up each item's slot, and feeds chunk x (R rows of
+    // one tile) into stage x % kNStage once chunk x - kNStage has been
+    // narrowed.  Lane 0 does the single-thread work; the warp loads columns.
     const uint64_t pol = l2_evict_first_policy();
-    constexpr int PER = 4 / (int)sizeof(QT);  // demands per 32-bit output word
-    const int sw = (int)(a.stride / 4);       // words per slot row
-    // Thread ptid narrows words k = kw + 128 j (j < kWords) of the rows of
-    // parity ptid / 128: the columns of its words stay in registers for the
-    // whole tour (a word is PER positions).
-    constexpr int kWordsMax = kPipeMaxN * (int)sizeof(QT) / 4;     // words per row at most
-    constexpr int kWords = (kWordsMax + 127) / 128;                // words per thread
-    const int kw = ptid & 127, rpar = ptid >> 7;
-    uint32_t wcol[kWords][PER];  // column of each position (0 past n)
-    uint32_t wvalid[kWords];     // bit e: position PER * k + e < n
-    int cur_b = -1, n = 0, R = 32, subs = 1, wq = 0;
-    uint32_t li = 0;  // items claimed by this CTA so far
-    int64_t gk = 0;   // chunks consumed through the stages so far (all groups)
-    int64_t gi = 0;   // chunks issued so far; chunk x uses stage x % kNStage
-    int mn_all = 0;
+    int cur_b = -1, n = 0, R = 32, subs = 1, gen = 0;
+    uint32_t li = 0;  // items set up by this CTA
+    int64_t x = 0;    // chunks issued
     bool failed = false;
-    auto bar_of = [&](int64_t x) -> uint32_t { return bar_base + 8u * (uint32_t)(x % kNStage); };
-    auto par_of = [&](int64_t x) -> uint32_t { return (uint32_t)(x / kNStage) & 1u; };
+    // chunk y narrowed (its stage free again), or give up
+    auto wait_done = [&](int64_t y) -> bool {
+      return y < 0 || mbar_wait_abortable(empty_of(y), par_of(y), &abort_flag, a.wait_ns);
+    };
     while (!failed) {
-      if (ptid == 0) group_id = (int64_t)atomicAdd(a.counter, 1ull);
-      prod_sync();
-      const int64_t gid = group_id;
+      int64_t gid = 0;
+      if (lane == 0) gid = (int64_t)atomicAdd(a.counter, 1ull);
+      gid = __shfl_sync(0xffffffffu, gid, 0);
       if (gid >= groups) break;
       const int b = BATCH ? a.order[gid / gpt] : 0;
       const int64_t t0 = (gid % gpt) * kGroup;
       const int m = (int)imin64(kGroup, tpt - t0);  // items in the group
-      if (b != cur_b) {  // the tour's columns and chunking
-        prod_sync();     // every producer is done with the old columns
+      if (b != cur_b) {
+        // a new tour: every issued chunk narrowed before its columns go
+        bool ok = true;
+        for (int64_t y = x - kNStage; y < x && ok; ++y) ok = wait_done(y);
+        if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
         cur_b = b;
         n = BATCH ? a.n[b] : a.n1;
-        wq = (n + PER - 1) / PER;
+        const int wqp = ((n + PER - 1) / PER) * PER;
         const StepRec* rec = a.rec + (BATCH ? a.rec_off[b] : 0);
-        for (int k = ptid; k < wq * PER; k += kProdThreads)
+        for (int k = lane; k < wqp; k += 32)
           cols[k] = k < n ? (BATCH ? (uint16_t)rec[k].col : a.cols[k]) : (uint16_t)0;
         R = 32;
         while ((uint32_t)R * (uint32_t)n * 4u > kStage) R >>= 1;
         subs = 32 / R;
-        prod_sync();
-#pragma unroll
-        for (int j = 0; j < kWords; ++j) {
-          const int k = kw + 128 * j;
-          wvalid[j] = 0u;
-#pragma unroll
-          for (int e = 0; e < PER; ++e) {
-            const bool v = k < wq && PER * k + e < n;
-            wcol[j][e] = v ? (uint32_t)cols[PER * k + e] * 4u : 0u;  // byte offset in a row
-            wvalid[j] |= (v ? 1u : 0u) << e;
-          }
-        }
+        ++gen;
+        __syncwarp();
       }
       const int32_t* dem = a.demands + (BATCH ? a.dem_off[b] : 0);
-      const int nch = m * subs;
-      const int64_t g0 = gk;  // global index of the group's chunk 0
-      auto crow0 = [&](int c) -> int64_t { return (t0 + c / subs) * 32 + (int64_t)(c % subs) * R; };
-      auto cbytes = [&](int c) -> uint32_t {
-        const int64_t r0 = crow0(c);
-        const int rows = r0 >= S ? 0 : (int)imin64(R, S - r0);
-        return ((uint32_t)rows * (uint32_t)n * 4u) & ~15u;
-      };
-      // chunk c of the group into its stage (an L2 prefetch of later
-      // chunks was measured slower: 1.48 -> 1.58 ms at n = 500, S = 10^6)
-      auto issue = [&](int c) {
-        const uint32_t bytes = cbytes(c);
-        const int64_t x = g0 + c;
-        mbar_arrive_tx(bar_of(x), bytes);
-        if (bytes)
-          bulk_g2s_hint(smem_u32(smem) + (uint32_t)(x % kNStage) * kStage, dem + crow0(c) * n,
-                        bytes, bar_of(x), pol);
-        gi = x + 1;
-      };
-      if (ptid == 0)
-        for (int c = 0; c < kNStage && c < nch; ++c) issue(c);
-      for (int c = 0; c < nch; ++c) {
-        const uint32_t item = li + (uint32_t)(c / subs);
+      for (int j = 0; j < m && !failed; ++j) {
+        const uint32_t item = li + (uint32_t)j;
         const uint32_t slot = item % kSlots;
-        if (c % subs == 0) {
+        const int64_t s0 = (t0 + j) * 32;
+        bool ok = true;
+        if (lane == 0) {
           // the slot's previous item (item - kSlots) must be finished
-          bool ok = true;
           if (item >= kSlots) {
             const uint32_t need = item - kSlots + 1;
-            if (ld_acquire_shared(&slot_free[slot]) < need) {
-              const uint64_t tw = global_ns();
-              while (ld_acquire_shared(&slot_free[slot]) < need) {
-                if (ld_acquire_shared(&abort_flag) || global_ns() - tw > a.wait_ns) {
-                  ok = false;
-                  break;
-                }
-                __nanosleep(256);
+            const uint64_t tw = global_ns();
+            while (ld_acquire_shared(&slot_free[slot]) < need) {
+              if (ld_acquire_shared(&abort_flag) || global_ns() - tw > a.wait_ns) {
+                ok = false;
+                break;
               }
+              __nanosleep(256);
             }
           }
-          if (prod_sync_or(!ok)) {
-            failed = true;
-            break;
-          }
-          if (ptid == 0) {
-            slot_inf[slot] = 0u;
-            slot_b[slot] = b;
-            slot_s0[slot] = (t0 + c / subs) * 32;
-          }
+          slot_inf[slot] = 0u;
+          slot_b[slot] = b;
+          slot_s0[slot] = s0;
+          item_cnt[slot] = 0u;
+          item_need[slot] = (uint32_t)(kNarrow * subs);
         }
-        const int64_t x = g0 + c;
-        const bool ok = mbar_wait(bar_of(x), par_of(x));
-        const int64_t r0 = crow0(c);
-        const int rows = r0 >= S ? 0 : (int)imin64(R, S - r0);
-        int32_t* sq = reinterpret_cast<int32_t*>(smem + (size_t)(x % kNStage) * kStage);
-        // the last few demands of a ragged last chunk (not a whole 16 bytes)
-        const int elems = rows * n;
-        const int bulk_elems = (int)((((uint32_t)elems * 4u) & ~15u) >> 2);
-        if (elems > bulk_elems) {  // (uniform) the stragglers must land before the narrow
-          if (ok && ptid < elems - bulk_elems)
-            sq[bulk_elems + ptid] = __ldg(dem + r0 * n + bulk_elems + ptid);
-          if (prod_sync_or(!ok)) {
-            failed = true;
-            break;
+        if (!__shfl_sync(0xffffffffu, (int)ok, 0)) { failed = true; break; }
+        for (int q = 0; q < subs; ++q) {
+          const int64_t r0 = s0 + (int64_t)q * R;
+          const int rows = r0 >= S ? 0 : (int)imin64(R, S - r0);
+          const bool okw = wait_done(x - kNStage);
+          if (!__all_sync(0xffffffffu, okw)) { failed = true; break; }
+          if (lane == 0) {
+            const int st = (int)(x % kNStage);
+            int32_t* sq = reinterpret_cast<int32_t*>(smem + (size_t)st * kStage);
+            const uint32_t bytes = ((uint32_t)rows * (uint32_t)n * 4u) & ~15u;
+            // the last few demands of a ragged last chunk (not a whole 16 bytes)
+            for (int e = (int)(bytes >> 2); e < rows * n; ++e) sq[e] = __ldg(dem + r0 * n + e);
+            StageMeta& mt = smeta[st];
+            mt.slot = (int32_t)slot;
+            mt.rbase = q * R;
+            mt.rows = rows;
+            mt.n = n;
+            mt.gen = gen;
+            mt.stop = 0;
+            mt.item = item;
+            fence_proxy_async();  // the narrowing warps' reads of the stage come first
+            mbar_arrive_tx(full_of(x), bytes);
+            if (bytes) bulk_g2s_hint(smem_u32(sq), dem + r0 * n, bytes, full_of(x), pol);
           }
-        }
-        // narrow + permute the chunk's rows into the slot; rows past S are
-        // written as zero demands (their lanes run on them, outputs dropped)
-        const int rbase = (c % subs) * R;
-        uint32_t* out = reinterpret_cast<uint32_t*>(qslots + ((int64_t)slot * 32 + rbase) * a.stride);
-        const uint32_t sq_b = smem_u32(sq);
-#pragma unroll
-        for (int j = 0; j < kWords; ++j) {
-          const int k = kw + 128 * j;
-          if (k >= wq || !ok) break;
-          for (int r = rpar; r < R; r += 2) {
-            uint32_t word = 0u;
-            if (r < rows) {
-              const uint32_t rb = sq_b + (uint32_t)(r * n) * 4u;
-              int v[PER];
-#pragma unroll
-              for (int e = 0; e < PER; ++e) {
-                int x;
-                asm volatile("ld.shared.s32 %0, [%1];" : "=r"(x) : "r"(rb + wcol[j][e]));
-                v[e] = (wvalid[j] >> e) & 1u ? x : 0;
-              }
-              uint32_t mx = (uint32_t)v[0];
-#pragma unroll
-              for (int e = 1; e < PER; ++e) mx = max(mx, (uint32_t)v[e]);
-              if (mx <= (uint32_t)Q) {
-                word = sizeof(QT) == 1
-                           ? __byte_perm(__byte_perm(v[0], v[1 % PER], 0x0040),
-                                         __byte_perm(v[2 % PER], v[3 % PER], 0x0040), 0x5410)
-                           : __byte_perm(v[0], v[1 % PER], 0x5410);
-              } else {  // a demand above Q or below 0: clamp to [0, Q+1]
-                bool inf = false;
-#pragma unroll
-                for (int e = 0; e < PER; ++e) {
-                  inf |= v[e] > Q;
-                  mn_all = min(mn_all, v[e]);
-                  word |= (uint32_t)min(max(v[e], 0), Q + 1) << (e * 8 * (int)sizeof(QT));
-                }
-                if (inf) atomicOr(&slot_inf[slot], 1u << (rbase + r));
-              }
-            }
-            out[(int64_t)r * sw + k] = word;
-          }
-        }
-        const bool item_done = (c % subs) == subs - 1;
-        if (item_done) __threadfence_block();  // the slot's rows before its publication
-        // also: the stage is free again; a copy that never landed (ok false
-        // in any thread) stops every producer together
-        if (prod_sync_or(!ok)) {
-          failed = true;
-          break;
-        }
-        gk = x + 1;
-        if (ptid == 0) {
-          // (a.stall: fault injection for tests -- nothing is published, and
-          // the DP warps' waits run out after a.wait_ns)
-          if (item_done && !a.stall) st_release_shared(&slot_ready[slot], item + 1);
-          if (c + kNStage < nch) {
-            fence_proxy_async();
-            issue(c + kNStage);
-          }
+          ++x;
         }
       }
       if (!failed) li += (uint32_t)m;
     }
-    if (failed) {
-      if (ptid == 0) {
-        atomicOr(a.status, SDP_FLAG_DEVICE_CHECK);
-        st_release_shared(&abort_flag, 1u);
-        // let copies still in flight land (again with a time limit) before
-        // shared memory goes
-        for (int64_t x = gk; x < gi; ++x) mbar_wait(bar_of(x), par_of(x));
+    if (!failed) {
+      // a stop marker in the next stage, once it is free
+      const bool ok = wait_done(x - kNStage);
+      if (!__all_sync(0xffffffffu, ok)) {
+        failed = true;
+      } else if (lane == 0) {
+        StageMeta& mt = smeta[x % kNStage];
+        mt.stop = 1;
+        mbar_arrive_tx(full_of(x), 0u);
+        st_release_shared(&final_count, li);
       }
-      prod_sync();
-    } else if (ptid == 0) {
-      st_release_shared(&final_count, li);
+    }
+    if (failed && lane == 0) {
+      atomicOr(a.status, SDP_FLAG_DEVICE_CHECK);
+      st_release_shared(&abort_flag, 1u);
+      // let copies still in flight land (again with a time limit) before
+      // shared memory goes
+      for (int64_t y = x - kNStage < 0 ? 0 : x - kNStage; y < x; ++y) mbar_wait(full_of(y), par_of(y));
+    }
+    return;
+  }
+
+  if (warp > kDp) {
+    // ---------------------------------------------------------- narrowing
+    // Chunk x: wait for its stage, narrow + permute its rows into the slot
+    // (rows past S become zero demands: their lanes run on them, outputs
+    // dropped), count it toward the item (the warp completing the item
+    // publishes it), free the stage.  Thread t owns words k = kw + 128 j of
+    // the rows of parity t / 128, their columns in registers per tour (one
+    // word per thread for rows of up to 512 bytes: the slowest thread sets
+    // the pace of the stage).
+    const int t = (int)threadIdx.x - (kDp + 1) * 32;
+    constexpr int kHalf = kNarrowThreads / 2;                       // 128
+    constexpr int kWordsMax = kPipeMaxN * (int)sizeof(QT) / 4;      // words per row at most
+    constexpr int kWords = (kWordsMax + kHalf - 1) / kHalf;         // words per thread
+    const int kw = t % kHalf, rpar = t / kHalf;
+    const int sw = (int)(a.stride / 4);  // words per slot row
+    uint32_t wcol[kWords][PER];          // byte offset in a stage row of each position
+    uint32_t wvalid[kWords];             // bit e: position PER * k + e < n
+    int cached_gen = -1, n = 0, wq = 0, R = 0;
+    int mn_all = 0;
+    for (int64_t x = 0;; ++x) {
+      if (!mbar_wait_abortable(full_of(x), par_of(x), &abort_flag, a.wait_ns)) {
+        if (lane == 0) st_release_shared(&abort_flag, 1u);
+        break;
+      }
+      const int st = (int)(x % kNStage);
+      const StageMeta mt = smeta[st];
+      if (mt.stop) break;
+      if (mt.gen != cached_gen) {
+        cached_gen = mt.gen;
+        n = mt.n;
+        wq = (n + PER - 1) / PER;
+        R = 32;  // rows per chunk, as the issuer chose them
+        while ((uint32_t)R * (uint32_t)n * 4u > kStage) R >>= 1;
+#pragma unroll
+        for (int j = 0; j < kWords; ++j) {
+          const int k = kw + kHalf * j;
+          wvalid[j] = 0u;
+#pragma unroll
+          for (int e = 0; e < PER; ++e) {
+            const bool v = k < wq && PER * k + e < n;
+            wcol[j][e] = v ? (uint32_t)cols[PER * k + e] * 4u : 0u;
+            wvalid[j] |= (v ? 1u : 0u) << e;
+          }
+        }
+      }
+      const uint32_t slot = (uint32_t)mt.slot;
+      const int rows = mt.rows;
+      const uint32_t sq_b = smem_u32(smem) + (uint32_t)st * kStage;
+      uint32_t* out = reinterpret_cast<uint32_t*>(qslots + ((int64_t)slot * 32 + mt.rbase) * a.stride);
+#pragma unroll
+      for (int j = 0; j < kWords; ++j) {
+        const int k = kw + kHalf * j;
+        if (k >= wq) break;
+        for (int r = rpar; r < R; r += 2) {
+          uint32_t word = 0u;
+          if (r < rows) {
+            const uint32_t rb = sq_b + (uint32_t)(r * n) * 4u;
+            int v[PER];
+#pragma unroll
+            for (int e = 0; e < PER; ++e) {
+              int xv;
+              asm volatile("ld.shared.s32 %0, [%1];" : "=r"(xv) : "r"(rb + wcol[j][e]));
+              v[e] = (wvalid[j] >> e) & 1u ? xv : 0;
+            }
+            uint32_t mx = (uint32_t)v[0];
+#pragma unroll
+            for (int e = 1; e < PER; ++e) mx = max(mx, (uint32_t)v[e]);
+            if (mx <= (uint32_t)Q) {
+              word = sizeof(QT) == 1
+                         ? __byte_perm(__byte_perm(v[0], v[1 % PER], 0x0040),
+                                       __byte_perm(v[2 % PER], v[3 % PER], 0x0040), 0x5410)
+                         : __byte_perm(v[0], v[1 % PER], 0x5410);
+            } else {  // a demand above Q or below 0: clamp to [0, Q+1]
+              bool inf = false;
+#pragma unroll
+              for (int e = 0; e < PER; ++e) {
+                inf |= v[e] > Q;
+                mn_all = min(mn_all, v[e]);
+                word |= (uint32_t)min(max(v[e], 0), Q + 1) << (e * 8 * (int)sizeof(QT));
+              }
+              if (inf) atomicOr(&slot_inf[slot], 1u << (mt.rbase + r));
+            }
+          }
+          out[(int64_t)r * sw + k] = word;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        // (a.stall: fault injection for tests -- nothing is published, and
+        // the DP warps' waits run out after a.wait_ns)
+        if (atom_add_acq_rel_shared(&item_cnt[slot], 1u) + 1u == item_need[slot] && !a.stall)
+          st_release_shared(&slot_ready[slot], mt.item + 1u);
+        mbar_arrive(empty_of(x));
+      }
     }
     if (mn_all < 0) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
     return;

@@ -17,9 +17,11 @@ def api():
     return a
 
 
-def _batch(seed, B, S, Q, nlo, nhi, qhi):
+def _batch(seed, B, S, Q, nlo, nhi, qhi, n_first=0):
     rng = np.random.default_rng(seed)
     n = rng.integers(nlo, nhi + 1, size=B).astype(np.int32)
+    if n_first:
+        n[0] = n_first
     tours, coords, dem = [], [], []
     for b in range(B):
         tours.append((rng.permutation(n[b]) + 1).astype(np.int32))
@@ -86,7 +88,8 @@ def test_batch_stream_and_deque_plans_bit_identical(Q, qhi):
     (S = 164: 5 tiles + 4 rows, every offset a multiple of 4) and a few
     demands above Q."""
     B, S = 29, 164
-    n, tours, coords, dem = _batch(77 + Q, B, S, Q, 1, 1100, qhi)
+    # one tour above 1024 customers: the pipelined kernel does not apply
+    n, tours, coords, dem = _batch(77 + Q, B, S, Q, 1, 1100, qhi, n_first=1100)
     dem[3][7, 0] = Q + 1
     plan_s, keep_s = _plan(n, tours, coords, dem, Q, S)
     assert plan_s.info()["warps_per_cta"] == -1
