@@ -123,7 +123,9 @@ struct Lane {
   float K, fpsi, bpsi;
   bool ovf;             // the deque outgrew the ring: recompute the scenario
 
-  __device__ __forceinline__ uint32_t at(uint32_t off) const { return rb + (off & kRingMask); }
+  // rings start on 4 KB and a lane's entry is its 8 bytes of a 256-byte
+  // slot, so the slot offset and the lane base share no bits: one LOP3
+  __device__ __forceinline__ uint32_t at(uint32_t off) const { return rb | (off & kRingMask); }
   __device__ __forceinline__ void init(uint32_t ring, int lane) {
     rb = ring + 8u * (uint32_t)lane;
     head = tail = 0u;
@@ -373,9 +375,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   const int Q = a.Q;
   const int64_t S = a.S;
   // shared: stages | DP rings | predecessor stages | (one tour) records | columns
-  const uint32_t rings = smem_u32(smem) + kNStage * kStage;
-  uint32_t* ostage = reinterpret_cast<uint32_t*>(smem + kNStage * kStage + (size_t)kDp * kRingBytes);
-  unsigned char* tail_sm = smem + kNStage * kStage + (size_t)kDp * kRingBytes +
+  const uint32_t rings = (smem_u32(smem) + kNStage * kStage + kRingBytes - 1) & ~(kRingBytes - 1);
+  const size_t rings_off = rings - smem_u32(smem);  // (the smem size holds kRingBytes of slack)
+  uint32_t* ostage = reinterpret_cast<uint32_t*>(smem + rings_off + (size_t)kDp * kRingBytes);
+  unsigned char* tail_sm = smem + rings_off + (size_t)kDp * kRingBytes +
                            (PRED ? (size_t)kDp * kOutBytes : 0);
   float2* rec2 = reinterpret_cast<float2*>(tail_sm);
   uint16_t* cols = reinterpret_cast<uint16_t*>(tail_sm + (BATCH ? 0 : (size_t)a.n1 * sizeof(float2)));
@@ -544,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     const int kw = t % kHalf, rpar = t / kHalf;
     const int sw = (int)(a.stride / 4);  // words per slot row
     uint32_t wcol[kWords][PER];          // byte offset in a stage row of each position
-    uint32_t wvalid[kWords];             // bit e: position PER * k + e < n
+    uint32_t wmask[kWords];              // the word's bits of positions below n
     int cached_gen = -1, n = 0, wq = 0, R = 0;
     int mn_all = 0;
     for (int64_t x = 0;; ++x) {
@@ -563,13 +566,17 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
         while ((uint32_t)R * (uint32_t)n * 4u > kStage) R >>= 1;
 #pragma unroll
         for (int j = 0; j < kWords; ++j) {
+          // a position past n reads the word's first column again (same
+          // value: the range test is unchanged) and is masked off after
+          // packing
           const int k = kw + kHalf * j;
-          wvalid[j] = 0u;
+          const uint32_t c0 = k < wq ? (uint32_t)cols[PER * k] * 4u : 0u;
+          wmask[j] = 0u;
 #pragma unroll
           for (int e = 0; e < PER; ++e) {
             const bool v = k < wq && PER * k + e < n;
-            wcol[j][e] = v ? (uint32_t)cols[PER * k + e] * 4u : 0u;
-            wvalid[j] |= (v ? 1u : 0u) << e;
+            wcol[j][e] = v ? (uint32_t)cols[PER * k + e] * 4u : c0;
+            wmask[j] |= v ? ((sizeof(QT) == 1 ? 0xFFu : 0xFFFFu) << (e * 8 * (int)sizeof(QT))) : 0u;
           }
         }
       }
@@ -581,38 +588,37 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
       for (int j = 0; j < kWords; ++j) {
         const int k = kw + kHalf * j;
         if (k >= wq) break;
-        for (int r = rpar; r < R; r += 2) {
-          uint32_t word = 0u;
-          if (r < rows) {
-            const uint32_t rb = sq_b + (uint32_t)(r * n) * 4u;
-            int v[PER];
+        uint32_t rb = sq_b + (uint32_t)(rpar * n) * 4u;  // stage row rpar
+        uint32_t* o = out + (int64_t)rpar * sw + k;
+        int r = rpar;
+        for (; r < rows; r += 2, rb += 8u * (uint32_t)n, o += 2 * sw) {
+          int v[PER];
+#pragma unroll
+          for (int e = 0; e < PER; ++e)
+            asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v[e]) : "r"(rb + wcol[j][e]));
+          uint32_t mx = (uint32_t)v[0];
+#pragma unroll
+          for (int e = 1; e < PER; ++e) mx = max(mx, (uint32_t)v[e]);
+          uint32_t word;
+          if (mx <= (uint32_t)Q) {
+            word = sizeof(QT) == 1
+                       ? __byte_perm(__byte_perm(v[0], v[1 % PER], 0x0040),
+                                     __byte_perm(v[2 % PER], v[3 % PER], 0x0040), 0x5410)
+                       : __byte_perm(v[0], v[1 % PER], 0x5410);
+          } else {  // a demand above Q or below 0: clamp to [0, Q+1]
+            bool inf = false;
+            word = 0u;
 #pragma unroll
             for (int e = 0; e < PER; ++e) {
-              int xv;
-              asm volatile("ld.shared.s32 %0, [%1];" : "=r"(xv) : "r"(rb + wcol[j][e]));
-              v[e] = (wvalid[j] >> e) & 1u ? xv : 0;
+              inf |= v[e] > Q;
+              mn_all = min(mn_all, v[e]);
+              word |= (uint32_t)min(max(v[e], 0), Q + 1) << (e * 8 * (int)sizeof(QT));
             }
-            uint32_t mx = (uint32_t)v[0];
-#pragma unroll
-            for (int e = 1; e < PER; ++e) mx = max(mx, (uint32_t)v[e]);
-            if (mx <= (uint32_t)Q) {
-              word = sizeof(QT) == 1
-                         ? __byte_perm(__byte_perm(v[0], v[1 % PER], 0x0040),
-                                       __byte_perm(v[2 % PER], v[3 % PER], 0x0040), 0x5410)
-                         : __byte_perm(v[0], v[1 % PER], 0x5410);
-            } else {  // a demand above Q or below 0: clamp to [0, Q+1]
-              bool inf = false;
-#pragma unroll
-              for (int e = 0; e < PER; ++e) {
-                inf |= v[e] > Q;
-                mn_all = min(mn_all, v[e]);
-                word |= (uint32_t)min(max(v[e], 0), Q + 1) << (e * 8 * (int)sizeof(QT));
-              }
-              if (inf) atomicOr(&slot_inf[slot], 1u << (mt.rbase + r));
-            }
+            if (inf) atomicOr(&slot_inf[slot], 1u << (mt.rbase + r));
           }
-          out[(int64_t)r * sw + k] = word;
+          *o = word & wmask[j];
         }
+        for (; r < R; r += 2, o += 2 * sw) *o = 0u;  // rows past S
       }
       __syncwarp();
       if (lane == 0) {
@@ -715,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
 
 size_t pipe_smem(const PipeArgs& a, bool pred) {
   const int n = a.batched ? kPipeMaxN : a.n1;
-  return (size_t)kNStage * kStage + (size_t)kDp * kRingBytes + (pred ? (size_t)kDp * kOutBytes : 0) +
+  return (size_t)kNStage * kStage + (size_t)(kDp + 1) * kRingBytes + (pred ? (size_t)kDp * kOutBytes : 0) +
          (a.batched ? 0 : (size_t)n * sizeof(float2)) + ((size_t)n + 8) * sizeof(uint16_t);
 }
 
