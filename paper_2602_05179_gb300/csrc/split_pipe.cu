@@ -250,6 +250,7 @@ struct PredStage {
   PT* tile;         // predecessor rows of the tile
   int n, rows, lane;
   bool pairs;       // uint16: every row segment starts on 4 bytes (n even, aligned base)
+  bool wide;        // every row segment starts on 8 bytes: full flushes store 8 bytes a lane
   uint32_t pend;    // uint16: low half of the word being packed
   static constexpr int W = 32 / (int)sizeof(PT);
   __device__ __forceinline__ void put(int pos, uint32_t p) {  // pos = (i - 1) % W
@@ -269,6 +270,23 @@ struct PredStage {
     if (sizeof(PT) == 2 && (cnt & 1)) st[lane * 8 + ((cnt >> 1) ^ ((lane >> 2) & 7))] = pend;
     __syncwarp();
     constexpr int PER = 4 / (int)sizeof(PT);
+    if (wide && cnt == W) {
+      // lane: word pair k2 (words 2 k2, 2 k2 + 1) of row 8 m + lane / 4; the
+      // pair sits at (2 k2 ^ s) & ~1, swapped when the row's swizzle s is odd
+      const int k2 = lane & 3;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int r = 8 * m + (lane >> 2);
+        const int sz = (r >> 2) & 7;
+        const uint2 v = *reinterpret_cast<const uint2*>(st + r * 8 + ((2 * k2 ^ sz) & ~1));
+        if (r < rows) {
+          PT* dst = tile + (int64_t)r * n + (i0 - 1) + 2 * k2 * PER;
+          *reinterpret_cast<uint2*>(dst) = (sz & 1) ? make_uint2(v.y, v.x) : v;
+        }
+      }
+      __syncwarp();
+      return;
+    }
     const int k = lane & 7;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -677,6 +695,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
       ps.n = n;
       ps.rows = rows;
       ps.pairs = sizeof(PT) == 4 || ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.pred) & 3) == 0);
+      ps.wide = (n % (8 / (int)sizeof(PT))) == 0 && (reinterpret_cast<uintptr_t>(a.pred) & 7) == 0;
     }
     float K;
     uint32_t first_inf;
