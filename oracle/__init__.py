@@ -12,7 +12,8 @@ Each function cites the passage of the paper it restates; see the C file.
 
 Parity pins (tests/test_oracle_*.py): the three worked examples printed in the
 paper (min-plus toy, Split toy, inventory toy), brute-force enumeration of all
-splits (n <= 10) and all delivery sequences (T <= 8), closed forms (single
+splits (n <= 10; with a route limit for the fleet-limited Split) and all
+delivery sequences (T <= 8), closed forms (single
 route = closed TSP tour when total demand <= Q; one route per customer when
 every demand is Q; zero consumption; deliver-every-day), invariants
 (monotonicity in Q, in the cost parameters) and central finite differences of
@@ -67,6 +68,9 @@ def _load():
         lib.oracle_split_soft.argtypes = [ctypes.c_int, P, P, P, i32, f64, i64, P, P, P, P,
                                           P, P, ctypes.c_int]
         lib.oracle_split_soft.restype = ctypes.c_int
+        lib.oracle_split_fleet.argtypes = [ctypes.c_int, P, P, P, i32, ctypes.c_int, i64, P,
+                                           P, P, P, P, P, ctypes.c_int]
+        lib.oracle_split_fleet.restype = ctypes.c_int
         lib.oracle_reinsert_routes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, f64,
                                                f64, f64, ctypes.c_int, P, P, P, i64, P, P, P,
                                                P, P, P, ctypes.c_int]
@@ -140,6 +144,37 @@ def split(tour, Q, demands, coords=None, dist=None, *, want_pred=True,
     if rc != 0:
         raise ValueError(f"oracle_split failed: {rc}")
     return {"cost": cost, "pred": pred, "margin": margin, "arcs": arcs,
+            "mean": float(mean[0])}
+
+
+def split_fleet(tour, Q, K, demands, coords=None, dist=None, *, want_route=True,
+                want_margin=False, nthreads=0):
+    """Fleet-limited Split: at most K routes (Appendix A, constraint
+    eq:fleet_size), hard capacity as in Eq. eqdpA.  Same arguments as split()
+    plus K >= 1.  Returns a dict with cost [S] (FP64, +inf where no split into
+    at most K routes fits), nroutes [S] int32, route [S, n] int32 (index of the
+    route serving each position, -1 when infeasible), margin [S] (relative gap
+    to the second-best candidate at the tightest choice of the optimal split)
+    and mean."""
+    tour = _c(tour, np.int32)
+    n = int(tour.shape[0])
+    demands = _c(demands, np.int32)
+    if n > 0:
+        demands = demands.reshape(-1, n)
+    S = int(demands.shape[0]) if demands.ndim == 2 else 0
+    coords = _c(coords, np.float32)
+    dist = _c(dist, np.float32)
+    cost = np.empty(S, np.float64)
+    nroutes = np.empty(S, np.int32)
+    route = np.empty((S, n), np.int32) if want_route else None
+    margin = np.empty(S, np.float64) if want_margin else None
+    mean = np.zeros(1, np.float64)
+    rc = _load().oracle_split_fleet(n, _ptr(tour), _ptr(coords), _ptr(dist), int(Q), int(K), S,
+                                    _ptr(demands), _ptr(cost), _ptr(nroutes), _ptr(route),
+                                    _ptr(margin), _ptr(mean), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_split_fleet failed: {rc}")
+    return {"cost": cost, "nroutes": nroutes, "route": route, "margin": margin,
             "mean": float(mean[0])}
 
 

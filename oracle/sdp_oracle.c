@@ -197,6 +197,148 @@ int oracle_split(int n, const int32_t* tour, const float* coords,
   return 0;
 }
 
+/* Fleet-limited Split, one scenario (Appendix A, extensive model: constraint
+ * eq:fleet_size allows at most K vehicles, i.e. at most K routes; the
+ * giant-tour example with "three vehicles available").  Reading F1: hard
+ * capacity as in Eq. eqdpA, at most K routes.  With J_k(i) the cost of
+ * serving positions 1..i with exactly k routes:
+ *     J_0(0) = 0,  J_0(i) = +inf (i > 0),  J_k(0) = +inf (k > 0),
+ *     J_k(i) = min over capacity-feasible p < i of J_{k-1}(p) + W(p,i),
+ * and cost = min_{1 <= k <= K} J_k(n) (n = 0: cost 0, no route).  Ties: the
+ * smallest p at every (k, i) (reading S4), then the fewest routes.  J and M
+ * are scratch [(K+1)*(n+1)] doubles, P [(K+1)*(n+1)] int32 (the argmin p).
+ * *nroutes = routes of the optimal split (0 when infeasible); route[i-1] =
+ * index of the route serving position i (0-based, in tour order), -1 when
+ * infeasible.  *margin = min over the choices along the optimal split (each
+ * argmin p, and the choice of k) of (second best - best) / |best|, +inf when
+ * every choice had a single candidate. */
+static double split_fleet_one(int n, const int32_t* tour, const cost_t* c, int32_t Q, int K,
+                              const int32_t* q_by_customer, double* J, int32_t* P,
+                              double* M, int32_t* nroutes, int32_t* route, double* margin) {
+  const int w = n + 1;
+  for (int k = 0; k <= K; ++k)
+    for (int i = 0; i <= n; ++i) {
+      J[k * w + i] = INFINITY;
+      P[k * w + i] = -1;
+      M[k * w + i] = INFINITY;
+    }
+  J[0] = 0.0;
+  for (int k = 1; k <= K; ++k) {
+    for (int i = 1; i <= n; ++i) {
+      double best = INFINITY, second = INFINITY;
+      int32_t bestp = -1;
+      int64_t load = 0;
+      double inner = 0.0; /* sum_{m=p+1}^{i-1} c(s_m, s_{m+1}) */
+      const double back = cost_ab(c, tour[i - 1], 0);
+      for (int p = i - 1; p >= 0; --p) {
+        const int sp1 = tour[p];
+        load += q_by_customer[sp1 - 1];
+        if (load > Q) break;
+        if (p < i - 1) inner += cost_ab(c, sp1, tour[p + 1]);
+        const double prev = J[(k - 1) * w + p];
+        if (isinf(prev)) continue;
+        const double cand = prev + (cost_ab(c, 0, sp1) + inner + back);
+        if (cand <= best) {  /* p runs downwards: "<=" keeps the smallest p */
+          if (bestp >= 0) second = best < second ? best : second;
+          best = cand;
+          bestp = p;
+        } else if (cand < second) {
+          second = cand;
+        }
+      }
+      J[k * w + i] = best;
+      P[k * w + i] = bestp;
+      M[k * w + i] = (bestp < 0 || isinf(second)) ? INFINITY
+                                                  : (second - best) / fmax(fabs(best), 1e-300);
+    }
+  }
+  if (n == 0) {
+    *nroutes = 0;
+    *margin = INFINITY;
+    return 0.0;
+  }
+  double best = INFINITY, second = INFINITY;
+  int bestk = 0;
+  for (int k = 1; k <= K; ++k) {
+    const double v = J[k * w + n];
+    if (v < best) {  /* "<": the fewest routes on ties */
+      second = best;
+      best = v;
+      bestk = k;
+    } else if (v < second) {
+      second = v;
+    }
+  }
+  double mg = (bestk == 0 || isinf(second)) ? INFINITY : (second - best) / fmax(fabs(best), 1e-300);
+  *nroutes = bestk;
+  if (bestk == 0) {
+    if (route)
+      for (int i = 0; i < n; ++i) route[i] = -1;
+    *margin = INFINITY;
+    return INFINITY;
+  }
+  int i = n, k = bestk;
+  while (i > 0) {
+    const int p = P[k * w + i];
+    mg = fmin(mg, M[k * w + i]);
+    if (route)
+      for (int m = p; m < i; ++m) route[m] = k - 1;
+    i = p;
+    --k;
+  }
+  *margin = mg;
+  return best;
+}
+
+/* Fleet-limited Split over S scenarios (arguments as oracle_split, plus K >=
+ * 1).  cost_out [S] FP64 (+inf where no split into at most K routes fits the
+ * capacity); nroutes_out [S], route_out [S*n], margin_out [S] optional;
+ * mean_out as in oracle_split.  Returns 0, -1 on a bad argument, -2 when out
+ * of memory. */
+int oracle_split_fleet(int n, const int32_t* tour, const float* coords, const float* dist,
+                       int32_t Q, int K, int64_t S, const int32_t* demands, double* cost_out,
+                       int32_t* nroutes_out, int32_t* route_out, double* margin_out,
+                       double* mean_out, int nthreads) {
+  if (n < 0 || S < 0 || Q <= 0 || K < 1 || !cost_out) return -1;
+  if ((coords == NULL) == (dist == NULL) && n > 0) return -1;
+  cost_t c = {n, coords, dist};
+  int bad = 0;
+  const size_t cells = (size_t)(K + 1) * (size_t)(n + 1);
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads) reduction(| : bad)
+#endif
+  {
+    double* J = (double*)malloc(sizeof(double) * cells);
+    double* M = (double*)malloc(sizeof(double) * cells);
+    int32_t* P = (int32_t*)malloc(sizeof(int32_t) * cells);
+    if (!J || !M || !P) bad = 1;
+    else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+      for (int64_t s = 0; s < S; ++s) {
+        int32_t nr = 0;
+        double mg = INFINITY;
+        cost_out[s] = split_fleet_one(n, tour, &c, Q, K, demands + s * n, J, P, M, &nr,
+                                      route_out ? route_out + s * n : NULL, &mg);
+        if (nroutes_out) nroutes_out[s] = nr;
+        if (margin_out) margin_out[s] = mg;
+      }
+    }
+    free(J);
+    free(M);
+    free(P);
+  }
+  if (bad) return -2;
+  if (mean_out) {
+    double sum = 0.0;
+    for (int64_t s = 0; s < S; ++s) sum += cost_out[s];
+    *mean_out = S > 0 ? sum / (double)S : 0.0;
+  }
+  return 0;
+}
+
 /* Soft-capacity Split, one scenario (the penalised route load of the
  * paper's CVRPSD model, Sec. "MILP formulation": a route whose load exceeds
  * the capacity pays beta per unit of excess, l_k >= load_k - C, l_k >= 0, in

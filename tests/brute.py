@@ -14,17 +14,20 @@ def euclid(coords, a, b):
     return math.sqrt(dx * dx + dy * dy)
 
 
-def split_brute(tour, q_by_customer, Q, cost):
+def split_brute(tour, q_by_customer, Q, cost, max_routes=None):
     """Min over all partitions of the tour into consecutive routes whose load
-    is <= Q of the summed route costs (depot -> customers in tour order ->
-    depot).  cost(a, b) gives the travel cost between nodes (0 = depot).
-    Returns (best cost, list of optimal partitions as lists of routes)."""
+    is <= Q (and, if max_routes is given, into at most that many routes) of
+    the summed route costs (depot -> customers in tour order -> depot).
+    cost(a, b) gives the travel cost between nodes (0 = depot).  Returns
+    (best cost, list of optimal partitions as lists of routes)."""
     n = len(tour)
     if n == 0:
         return 0.0, [[]]
     best, arg = math.inf, []
     for mask in range(1 << (n - 1)):
         cuts = [k for k in range(1, n) if mask >> (k - 1) & 1]
+        if max_routes is not None and len(cuts) + 1 > max_routes:
+            continue
         bounds = [0] + cuts + [n]
         total, ok = 0.0, True
         routes = []
@@ -58,6 +61,8 @@ def split_soft_brute(tour, q_by_customer, Q, beta, cost):
     best, arg = math.inf, []
     for mask in range(1 << (n - 1)):
         cuts = [k for k in range(1, n) if mask >> (k - 1) & 1]
+        if max_routes is not None and len(cuts) + 1 > max_routes:
+            continue
         bounds = [0] + cuts + [n]
         total = 0.0
         routes = []
