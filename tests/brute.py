@@ -61,8 +61,6 @@ def split_soft_brute(tour, q_by_customer, Q, beta, cost):
     best, arg = math.inf, []
     for mask in range(1 << (n - 1)):
         cuts = [k for k in range(1, n) if mask >> (k - 1) & 1]
-        if max_routes is not None and len(cuts) + 1 > max_routes:
-            continue
         bounds = [0] + cuts + [n]
         total = 0.0
         routes = []
