@@ -524,8 +524,8 @@ def operators(api, wl, dev, only="", steps=0, checks=True):
 
 
 def op_reinsert(c, out):
-    """Reinsertion T=60, U=200, S=10^6 (ALU bound): the default kernel against
-    the one-scenario-per-warp kernel."""
+    """Reinsertion T=60, U=200, S=10^6 (ALU bound): the default kernel (one
+    scenario per lane) against the one-scenario-per-warp kernel."""
     import torch
     rs = c.wl.REINSERT_C3
     cons = c.wl.reinsert_consumption_device(rs, c.dev)

@@ -750,9 +750,13 @@ int launch_reinsert(const ReinsertArgs& a, cudaStream_t st) {
     if (a.U > 255 || a.table) return (int)cudaErrorInvalidValue;
     return unit ? routes_by_kc<true>(a, st) : routes_by_kc<false>(a, st);
   }
-  // AUTO takes WARP: at T = 60, U = 200, S = 10^6 it runs in 6.16 ms against
-  // 7.09 ms for LANE (fewer instructions, but only 7 warps per SM to hide them)
-  if (a.algo == SDP_REINSERT_LANE && reinsert_lane_supported(a.T, a.U)) {
+  // AUTO takes LANE where it applies: at T = 60, U = 200, S = 10^6 it runs in
+  // 5.20 ms against 6.17 ms for WARP (a register-resident variant of WARP,
+  // shifting the cost-to-go by warp shuffles, was measured at 6.59 ms: a
+  // shuffle and a select cost what the shared load and store they replace
+  // do, and WARP is issue-bound at 82%, not bound by shared memory)
+  if ((a.algo == SDP_REINSERT_LANE || a.algo == SDP_REINSERT_AUTO) &&
+      reinsert_lane_supported(a.T, a.U)) {
     if (a.table) return unit ? lane_by_kc<true, true>(a, st) : lane_by_kc<true, false>(a, st);
     return unit ? lane_by_kc<false, true>(a, st) : lane_by_kc<false, false>(a, st);
   }

@@ -41,7 +41,7 @@ def test_reinsert_paper_toy(algo):
     assert float(r["mean"]) == g["value"]
 
 
-@pytest.mark.parametrize("algo", ["auto", "lane"])
+@pytest.mark.parametrize("algo", ["auto", "warp", "lane"])
 @pytest.mark.parametrize("case", [
     # seed, T, U, I0, S, lam, table, unit_cost
     (0, 8, 12, 5, 100, 4.0, False, 0.0),
