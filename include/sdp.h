@@ -240,6 +240,37 @@ int sdp_split_eval(const sdp_split_args* a, void* stream);
 #define SDP_NOALLOC_SCRATCH_BYTES (16u << 20)
 int sdp_split_eval_noalloc(const sdp_split_args* a, void* stream);
 
+/* Fleet-limited Split: at most max_routes routes per scenario (Appendix A,
+ * extensive model, constraint eq:fleet_size -- the giant-tour example there
+ * has "three vehicles available"), hard capacity as in Eq. eqdpA.  With
+ * J_k(i) the cost of serving positions 1..i with exactly k routes,
+ *     J_k(i) = min over capacity-feasible p < i of J_{k-1}(p) + W(p,i),
+ *     J_0(0) = 0, J_0(i > 0) = J_k(0) = +inf,  cost = min_{k <= K} J_k(n),
+ * ties to the smallest p at every (k, i), then to the fewest routes.
+ *   a:           as for sdp_split_eval, with pred_out = NULL, hard capacity,
+ *                device demands, algo SDP_ALGO_AUTO (one warp per scenario,
+ *                the route counts across its lanes) or SDP_ALGO_PLAIN (one
+ *                thread per scenario, every feasible p of every layer; the
+ *                same FP32 operations and bits); cost_out [S] fp32 (+inf
+ *                where no split into at most max_routes routes fits Q, or a
+ *                demand exceeds Q: SDP_WARN_INFEASIBLE at the next status
+ *                read), mean_out optional; workspace of at least
+ *                sdp_split_fleet_workspace_bytes(a, max_routes, route_out !=
+ *                NULL) bytes (device, 256-byte aligned).
+ *   max_routes:  K, 1..64.
+ *   nroutes_out: [S] int32 device or NULL: routes of the optimal split, 0
+ *                when infeasible.
+ *   route_out:   [S*n] uint8 device or NULL: route_out[s*n + i-1] = index
+ *                (0-based, in tour order) of the route serving position i;
+ *                0xFF for every position of an infeasible scenario.
+ * Errors: SDP_ERR_INVALID_ARG (as sdp_split_eval; pred_out set; host
+ * pointers), SDP_ERR_UNSUPPORTED (max_routes outside 1..64, n > 65534,
+ * Q > 32767, soft capacity, another algo), SDP_ERR_WORKSPACE. */
+size_t sdp_split_fleet_workspace_bytes(const sdp_split_args* a, int32_t max_routes,
+                                       int32_t want_routes);
+int sdp_split_fleet_eval(const sdp_split_args* a, int32_t max_routes, int32_t* nroutes_out,
+                         uint8_t* route_out, void* stream);
+
 /* Number of capacity-feasible arcs (p,i), p < i, load(s_{p+1..i}) <= Q, per
  * scenario -- the relaxations of Eq. eqdpA, the throughput unit.
  * arcs_out [S] int64 or NULL; total_out [1] uint64 (device) or NULL. */
@@ -420,7 +451,8 @@ void sdp_saa_search_destroy(sdp_saa_search* s);
  * Backward DP C_T = 0, C_t(I) = min(no delivery, delivery), ties to no
  * delivery; value = C_0(I0); policy = decisions along the optimal path. */
 /* Reinsertion kernels */
-#define SDP_REINSERT_AUTO 0  /* WARP (measured faster at T = 60, U = 200) */
+#define SDP_REINSERT_AUTO 0  /* LANE where it applies (measured faster at
+                                T = 60, U = 200), else WARP */
 #define SDP_REINSERT_WARP 1  /* one warp per scenario, states across lanes */
 #define SDP_REINSERT_LANE 2  /* one lane per scenario, its cost-to-go in shared
                                 memory (up to 8 warps per SM); needs U <= 255;

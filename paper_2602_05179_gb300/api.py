@@ -90,6 +90,8 @@ def _load():
             "sdp_split_workspace_bytes": ([P], sz),
             "sdp_split_eval": ([P, P], i32),
             "sdp_split_count_arcs": ([P, P, P, P], i32),
+            "sdp_split_fleet_workspace_bytes": ([P, i32, i32], sz),
+            "sdp_split_fleet_eval": ([P, i32, P, P, P], i32),
             "sdp_split_backward_workspace_bytes": ([P], sz),
             "sdp_split_backward": ([P, P, P, P, P, P], i32),
             "sdp_reinsert_workspace_bytes": ([P], sz),
@@ -319,6 +321,31 @@ def split_eval(tour, Q, demands, *, coords=None, dist=None, preds=None, algo="au
     a.workspace, a.workspace_bytes = ws.data_ptr(), ws.numel()
     _check(_load().sdp_split_eval(ctypes.byref(a), _stream(stream)))
     return {"cost": cost, "pred": pred, "mean": m}
+
+
+def split_fleet_eval(tour, Q, demands, max_routes, *, coords=None, dist=None, routes=True,
+                     algo="auto", mean=True, stream=None):
+    """Fleet-limited Split: at most max_routes routes per scenario (hard
+    capacity).  Arguments as split_eval; algo "auto" or "plain".  Returns
+    dict(cost fp32 [S] (+inf where no split fits), nroutes int32 [S],
+    route uint8 [S, n] (route of each position, 255 when infeasible) or None,
+    mean fp64 0-d tensor or None)."""
+    _load()
+    dev = tour.device
+    n = int(tour.numel())
+    S = int(demands.shape[0])
+    cost = torch.empty(S, dtype=torch.float32, device=dev)
+    nroutes = torch.empty(S, dtype=torch.int32, device=dev)
+    route = torch.empty((S, n), dtype=torch.uint8, device=dev) if routes else None
+    m = torch.empty((), dtype=torch.float64, device=dev) if mean else None
+    a = _split_struct(tour, Q, demands, coords, dist, cost, None, 0, algo, m, 0, 0)
+    ws = _workspace(_load().sdp_split_fleet_workspace_bytes(ctypes.byref(a), int(max_routes),
+                                                            1 if routes else 0), dev)
+    a.workspace, a.workspace_bytes = ws.data_ptr(), ws.numel()
+    _check(_load().sdp_split_fleet_eval(ctypes.byref(a), int(max_routes),
+                                        _dev_ptr(nroutes, "nroutes"), _dev_ptr(route, "route"),
+                                        _stream(stream)))
+    return {"cost": cost, "nroutes": nroutes, "route": route, "mean": m}
 
 
 def split_count_arcs(tour, Q, demands, *, coords=None, dist=None, per_scenario=True,

@@ -758,6 +758,132 @@ int sdp_split_eval_noalloc(const sdp_split_args* a, void* stream) {
   return sdp_split_eval(&b, stream);
 }
 
+// ------------------------------------------------------ fleet-limited Split
+}  // extern "C"
+
+namespace {
+struct FleetWs {
+  TourPrep prep;
+  double* mean_partial;
+  uint32_t* fb_count;
+  uint32_t* fb_list;
+  float* kscratch;
+  uint16_t* pscratch;
+  uint16_t* dscratch;
+  int64_t nslots;
+  int grid;
+  size_t bytes;
+};
+constexpr int64_t kFleetPlainSlots = 65536;   // PLAIN: scenarios in flight
+constexpr int64_t kFleetFallbackSlots = 1024; // recomputation of flagged scenarios
+
+FleetWs carve_fleet(const sdp_split_args* a, int K, bool routes, void* base) {
+  FleetWs w{};
+  Carver c{static_cast<unsigned char*>(base)};
+  const int n = a->n;
+  const bool plain = a->algo == SDP_ALGO_PLAIN;
+  w.prep.rec = c.take<StepRec>((size_t)n);
+  w.prep.cols = c.take<uint16_t>((size_t)n);
+  w.prep.Dn = c.take<double>(1);
+  w.mean_partial = c.take<double>(kMeanBlocks);
+  w.fb_count = c.take<uint32_t>(1);
+  w.fb_list = plain ? nullptr : c.take<uint32_t>((size_t)a->S);
+  const int64_t cap = plain ? kFleetPlainSlots : kFleetFallbackSlots;
+  w.nslots = a->S < cap ? a->S : cap;
+  if (w.nslots < 1) w.nslots = 1;
+  w.kscratch = c.take<float>((size_t)w.nslots * 2 * (size_t)(n + 1));
+  w.pscratch = routes ? c.take<uint16_t>((size_t)w.nslots * K * (size_t)n) : nullptr;
+  w.grid = plain || n == 0 ? 0 : fleet_grid(n, K, a->S);
+  w.dscratch = (routes && !plain && n > 0) ? c.take<uint16_t>(fleet_dscratch_elems(n, K, w.grid))
+                                          : nullptr;
+  w.bytes = c.off;
+  return w;
+}
+
+int check_fleet(const sdp_split_args* a, int32_t K) {
+  int rc = check_split(a, true);
+  if (rc) return rc;
+  if (K < 1 || K > kFleetMaxK) return fail(SDP_ERR_UNSUPPORTED, "max_routes = %d outside 1..%d", K, kFleetMaxK);
+  if (a->n > 65534) return fail(SDP_ERR_UNSUPPORTED, "fleet-limited Split needs n <= 65534");
+  if (a->Q > 32767) return fail(SDP_ERR_UNSUPPORTED, "fleet-limited Split needs Q <= 32767");
+  if (a->capacity_mode != SDP_CAPACITY_HARD)
+    return fail(SDP_ERR_UNSUPPORTED, "fleet-limited Split takes hard capacity");
+  if (a->pred_out) return fail(SDP_ERR_INVALID_ARG, "fleet-limited Split returns routes, not pred_out");
+  if (a->algo != SDP_ALGO_AUTO && a->algo != SDP_ALGO_PLAIN)
+    return fail(SDP_ERR_UNSUPPORTED, "fleet-limited Split takes algo AUTO or PLAIN");
+  if (a->n > 0 && a->S > 0 && !is_device_ptr(a->demands))
+    return fail(SDP_ERR_INVALID_ARG, "fleet-limited Split needs device demands");
+  return SDP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t sdp_split_fleet_workspace_bytes(const sdp_split_args* a, int32_t max_routes,
+                                       int32_t want_routes) {
+  if (!a || a->n < 0 || a->S < 0 || max_routes < 1 || max_routes > kFleetMaxK) return 0;
+  return carve_fleet(a, max_routes, want_routes != 0, nullptr).bytes;
+}
+
+int sdp_split_fleet_eval(const sdp_split_args* a, int32_t max_routes, int32_t* nroutes_out,
+                         uint8_t* route_out, void* stream) {
+  int rc = check_fleet(a, max_routes);
+  if (rc) return rc;
+  if (nroutes_out && a->S > 0 && !is_device_ptr(nroutes_out))
+    return fail(SDP_ERR_INVALID_ARG, "nroutes_out must be a device pointer");
+  if (route_out && a->S > 0 && a->n > 0 && !is_device_ptr(route_out))
+    return fail(SDP_ERR_INVALID_ARG, "route_out must be a device pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool routes = route_out != nullptr && a->n > 0;
+  const FleetWs need = carve_fleet(a, max_routes, routes, nullptr);
+  rc = check_ws(a->workspace, a->workspace_bytes, need.bytes);
+  if (rc) return rc;
+  uint32_t* status;
+  rc = status_ptr(&status);
+  if (rc) return rc;
+  rc = fault_call();
+  if (rc) return rc;
+  const FleetWs w = carve_fleet(a, max_routes, routes, a->workspace);
+  if (a->S > 0 && a->n == 0) {
+    cudaError_t e = cudaMemsetAsync(a->cost_out, 0, sizeof(float) * a->S, st);
+    if (e == cudaSuccess && nroutes_out) e = cudaMemsetAsync(nroutes_out, 0, sizeof(int32_t) * a->S, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset fleet outputs");
+  } else if (a->S > 0) {
+    launch_tour_prep(a->tour, a->n, a->coords, a->dist, w.prep, status, w.fb_count, st);
+    SplitFleetArgs f{};
+    f.n = a->n; f.Q = a->Q; f.K = max_routes; f.S = a->S;
+    f.rec = w.prep.rec; f.Dn = w.prep.Dn; f.demands = a->demands;
+    f.cost = a->cost_out; f.nroutes = nroutes_out; f.route = routes ? route_out : nullptr;
+    f.fb_count = w.fb_count; f.status = status;
+    f.kscratch = w.kscratch; f.pscratch = w.pscratch; f.nslots = w.nslots;
+    int e = 0;
+    if (a->algo == SDP_ALGO_PLAIN) {
+      f.fb_list = nullptr;  // every scenario
+      note_launch(8, (int)((w.nslots + 255) / 256));
+      prof_begin(st);
+      e = launch_split_fleet_plain(f, st);
+      prof_end(st);
+      if (e) return cuda_fail((cudaError_t)e, "split_fleet_plain launch");
+    } else {
+      f.fb_list = w.fb_list;
+      f.dscratch = w.dscratch;
+      note_launch(8, w.grid);
+      prof_begin(st);
+      e = launch_split_fleet(f, w.grid, st);
+      prof_end(st);
+      if (e) return cuda_fail((cudaError_t)e, "split_fleet launch");
+      e = launch_split_fleet_plain(f, st);  // the flagged scenarios, if any
+      if (e) return cuda_fail((cudaError_t)e, "split_fleet_plain launch");
+    }
+  }
+  if (a->mean_out) {
+    launch_mean(a->cost_out, a->S, w.mean_partial, a->mean_out, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mean launch");
+  }
+  return SDP_OK;
+}
+
 int sdp_split_count_arcs(const sdp_split_args* args, int64_t* arcs_out, uint64_t* total_out,
                          void* stream) {
   int rc = check_split(args, false);
@@ -842,7 +968,8 @@ namespace {
 // the lane kernel keeps its decision bits in the workspace when the policy
 // is wanted
 bool reinsert_uses_lane(const sdp_reinsert_args* a) {
-  return a->algo == SDP_REINSERT_LANE && a->n_routes == 0 && reinsert_lane_supported(a->T, a->U);
+  return (a->algo == SDP_REINSERT_LANE || a->algo == SDP_REINSERT_AUTO) && a->n_routes == 0 &&
+         reinsert_lane_supported(a->T, a->U);
 }
 size_t reinsert_scratch_bytes(const sdp_reinsert_args* a) {
   return (reinsert_uses_lane(a) && a->policy_out && a->S > 0)

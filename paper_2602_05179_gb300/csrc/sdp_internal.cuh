@@ -275,6 +275,32 @@ int pipe_grid(int64_t S, int B);
 size_t pipe_ring_bytes(int n_max, int Q, int grid);
 int launch_split_pipe(const PipeArgs& a, cudaStream_t st);
 
+// Fleet-limited Split (at most K routes, K <= 64): one warp per scenario
+// with the route-count layers across lanes, and a one-thread-per-scenario
+// layered kernel (PLAIN, and the recomputation of flagged scenarios).
+constexpr int kFleetMaxK = 64;
+struct SplitFleetArgs {
+  int n, Q, K;
+  int64_t S;
+  const StepRec* rec;
+  const double* Dn;
+  const int32_t* demands;
+  float* cost;               // [S]
+  int32_t* nroutes;          // [S] or NULL
+  uint8_t* route;            // [S*n] or NULL: route of each position, 0xFF if infeasible
+  uint16_t* dscratch;        // warp kernel with routes: fleet_dscratch_elems
+  uint32_t* fb_list;         // warp kernel: flagged scenarios; plain: NULL = all S
+  uint32_t* fb_count;
+  float* kscratch;           // plain: [nslots * 2 * (n+1)]
+  uint16_t* pscratch;        // plain with routes: [nslots * K * n]
+  int64_t nslots;
+  uint32_t* status;
+};
+int fleet_grid(int n, int K, int64_t S);
+size_t fleet_dscratch_elems(int n, int K, int grid);
+int launch_split_fleet(const SplitFleetArgs& a, int grid, cudaStream_t st);
+int launch_split_fleet_plain(const SplitFleetArgs& a, cudaStream_t st);
+
 // arc counting (capacity-feasible (p,i) pairs)
 void launch_count_arcs(int n, int Q, int64_t S, const StepRec* rec,
                        const int32_t* demands, int64_t* arcs,
