@@ -264,7 +264,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--only", default="",
-                    choices=["", "reinsert", "routes", "batch", "adjoint", "soft", "saa"],
+                    choices=["", "reinsert", "routes", "batch", "adjoint", "soft", "fleet", "saa"],
                     help="run one operator line alone (profiling)")
     ap.add_argument("--preds", default="u16", choices=["u16", "i32", "none"])
     ap.add_argument("--no-operators", action="store_true",
@@ -514,7 +514,7 @@ def operators(api, wl, dev, only="", steps=0, checks=True):
     import torch
     c = OpCtx(api, wl, dev, steps, checks)
     fns = {"reinsert": op_reinsert, "routes": op_routes, "adjoint": op_adjoint,
-           "soft": op_soft, "batch": op_batch, "saa": op_saa}
+           "soft": op_soft, "fleet": op_fleet, "batch": op_batch, "saa": op_saa}
     out = {}
     for k in ([only] if only else list(fns)):
         fns[k](c, out)
@@ -678,6 +678,63 @@ def op_soft(c, out):
         line["errors"] = split_errors(r["cost"][idx].cpu().numpy(), _preds_i64(r["pred"][idx]),
                                       orc)
     out["split_soft_n500_S1e6_beta10"] = line
+
+
+def op_fleet(c, out):
+    """Fleet-limited Split (at most K = 42 routes) on the Split benchmark's
+    recipe (n = 500, Q = 200, U{1..30}) with S = 65,536: the limit binds
+    (about 39-42 routes are needed).  Work unit: the K-layer relaxations,
+    K x feasible arcs per scenario (2 ops each); the plain comparison runs
+    every feasible p of every layer, one thread per scenario, on 4,096
+    scenarios."""
+    import dataclasses
+    import torch
+    K, S = 42, 65536
+    spec = dataclasses.replace(c.wl.SPLIT_C2, S=S)
+    tour, xy, _ = c.wl.split_tour(spec)
+    t = torch.from_numpy(tour).to(c.dev)
+    cc = torch.from_numpy(xy).to(c.dev)
+    q = c.wl.split_demands_device(spec, c.dev, 0, S)
+    arcs, total = c.api.split_count_arcs(t, spec.Q, q, coords=cc, per_scenario=False)
+    torch.cuda.synchronize()
+    rel = float(total) * K
+    fn = lambda: c.api.split_fleet_eval(t, spec.Q, q, K, coords=cc)
+    ms, kms = _timed(fn, c.steps or 5)
+    c.api.status()
+    r = fn()
+    fell_back = bool(c.api.status() & c.api.FLAG_FALLBACK)
+    Sp = 4096
+    qp = q[:Sp].contiguous()
+    pms, pkms = _timed(lambda: c.api.split_fleet_eval(t, spec.Q, qp, K, coords=cc, algo="plain"),
+                       1, warmup=1)
+    rp = c.api.split_fleet_eval(t, spec.Q, qp, K, coords=cc, algo="plain")
+    torch.cuda.synchronize()
+    same = all(bool(torch.equal(r[k][:Sp], rp[k])) for k in ("cost", "nroutes", "route"))
+    fin = torch.isfinite(r["cost"])
+    line = {"value": S / (ms / 1e3), "unit": "scenarios/s", "ms_per_step": ms, "kernel_ms": kms,
+            "kernel": "split_fleet_kernel (one warp per scenario, route counts across lanes)",
+            "max_routes": K, "feasible_frac": float(fin.float().mean()),
+            "plain_fallback_used": fell_back,
+            "layer_relaxations_per_s": rel / (kms / 1e3),
+            "roofline": c.alu_roof(2 * rel, kms),
+            "vs_plain": {"path": "one thread per scenario, every feasible p of every layer",
+                         "sample": Sp, "kernel_ms": pkms,
+                         "speedup_per_scenario": (pkms / Sp) / (kms / S),
+                         "bit_identical": same}}
+    if c.checks:
+        import oracle
+        rows = sample_rows(S, 128, 21)
+        qh = np.concatenate([c.wl.split_demands(spec, int(k), int(k) + 1) for k in rows])
+        orc = oracle.split_fleet(tour, spec.Q, K, qh, coords=xy, want_margin=True)
+        idx = torch.from_numpy(rows).to(c.dev)
+        line["errors"] = _rel(r["cost"][idx].cpu().numpy().astype(np.float64), orc["cost"])
+        uniq = np.isfinite(orc["cost"]) & (orc["margin"] > 1e-5)
+        nr = r["nroutes"][idx].cpu().numpy()
+        ro = r["route"][idx].cpu().numpy().astype(np.int64)
+        line["errors"]["routes_checked"] = int(uniq.sum())
+        line["errors"]["route_mismatch"] = int((ro[uniq] != orc["route"][uniq]).any(1).sum() +
+                                               (nr[uniq] != orc["nroutes"][uniq]).sum())
+    out[f"fleet_n500_Q200_K{K}_S65536"] = line
 
 
 def op_batch(c, out):

@@ -264,7 +264,7 @@ int sdp_split_eval_noalloc(const sdp_split_args* a, void* stream);
  *                (0-based, in tour order) of the route serving position i;
  *                0xFF for every position of an infeasible scenario.
  * Errors: SDP_ERR_INVALID_ARG (as sdp_split_eval; pred_out set; host
- * pointers), SDP_ERR_UNSUPPORTED (max_routes outside 1..64, n > 65534,
+ * pointers), SDP_ERR_UNSUPPORTED (max_routes outside 1..64, n > 16384,
  * Q > 32767, soft capacity, another algo), SDP_ERR_WORKSPACE. */
 size_t sdp_split_fleet_workspace_bytes(const sdp_split_args* a, int32_t max_routes,
                                        int32_t want_routes);

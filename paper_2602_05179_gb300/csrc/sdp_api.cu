@@ -771,7 +771,7 @@ struct FleetWs {
   uint16_t* pscratch;
   uint16_t* dscratch;
   int64_t nslots;
-  int grid;
+  FleetConfig cfg;
   size_t bytes;
 };
 constexpr int64_t kFleetPlainSlots = 65536;   // PLAIN: scenarios in flight
@@ -793,8 +793,8 @@ FleetWs carve_fleet(const sdp_split_args* a, int K, bool routes, void* base) {
   if (w.nslots < 1) w.nslots = 1;
   w.kscratch = c.take<float>((size_t)w.nslots * 2 * (size_t)(n + 1));
   w.pscratch = routes ? c.take<uint16_t>((size_t)w.nslots * K * (size_t)n) : nullptr;
-  w.grid = plain || n == 0 ? 0 : fleet_grid(n, K, a->S);
-  w.dscratch = (routes && !plain && n > 0) ? c.take<uint16_t>(fleet_dscratch_elems(n, K, w.grid))
+  w.cfg = plain || n == 0 ? FleetConfig{} : fleet_config(n, K, a->S);
+  w.dscratch = (routes && !plain && n > 0) ? c.take<uint16_t>(fleet_dscratch_elems(n, K, w.cfg))
                                           : nullptr;
   w.bytes = c.off;
   return w;
@@ -804,7 +804,7 @@ int check_fleet(const sdp_split_args* a, int32_t K) {
   int rc = check_split(a, true);
   if (rc) return rc;
   if (K < 1 || K > kFleetMaxK) return fail(SDP_ERR_UNSUPPORTED, "max_routes = %d outside 1..%d", K, kFleetMaxK);
-  if (a->n > 65534) return fail(SDP_ERR_UNSUPPORTED, "fleet-limited Split needs n <= 65534");
+  if (a->n > 16384) return fail(SDP_ERR_UNSUPPORTED, "fleet-limited Split needs n <= 16384");
   if (a->Q > 32767) return fail(SDP_ERR_UNSUPPORTED, "fleet-limited Split needs Q <= 32767");
   if (a->capacity_mode != SDP_CAPACITY_HARD)
     return fail(SDP_ERR_UNSUPPORTED, "fleet-limited Split takes hard capacity");
@@ -867,9 +867,9 @@ int sdp_split_fleet_eval(const sdp_split_args* a, int32_t max_routes, int32_t* n
     } else {
       f.fb_list = w.fb_list;
       f.dscratch = w.dscratch;
-      note_launch(8, w.grid);
+      note_launch(w.cfg.warps, w.cfg.grid);
       prof_begin(st);
-      e = launch_split_fleet(f, w.grid, st);
+      e = launch_split_fleet(f, w.cfg, st);
       prof_end(st);
       if (e) return cuda_fail((cudaError_t)e, "split_fleet launch");
       e = launch_split_fleet_plain(f, st);  // the flagged scenarios, if any

@@ -296,9 +296,13 @@ struct SplitFleetArgs {
   int64_t nslots;
   uint32_t* status;
 };
-int fleet_grid(int n, int K, int64_t S);
-size_t fleet_dscratch_elems(int n, int K, int grid);
-int launch_split_fleet(const SplitFleetArgs& a, int grid, cudaStream_t st);
+struct FleetConfig {
+  int warps;  // warps per CTA (0: the tour's records do not fit)
+  int grid;
+};
+FleetConfig fleet_config(int n, int K, int64_t S);
+size_t fleet_dscratch_elems(int n, int K, const FleetConfig& c);
+int launch_split_fleet(const SplitFleetArgs& a, const FleetConfig& c, cudaStream_t st);
 int launch_split_fleet_plain(const SplitFleetArgs& a, cudaStream_t st);
 
 // arc counting (capacity-feasible (p,i) pairs)

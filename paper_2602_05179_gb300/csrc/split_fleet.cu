@@ -19,11 +19,10 @@
 // takes layer 0: K_0(0) = 0, else +inf), and each lane keeps its layer's
 // window candidates in a monotone deque (entries (psi bits, L(p) << 16 | p),
 // rings [slot][entry][lane] in shared memory): pop the back while its psi is
-// larger (an equal one is older: smallest p), push p = i - 1 (unreachable
-// states push +inf, which never pops a finite entry and reaches the front
-// only when nothing finite is left), pop the front while the route p+1..i
-// exceeds Q (the newest entry stays even when q_i > Q; the first such
-// position makes every later J infinite).  With route output, i - p of every
+// larger (an equal one is older: smallest p), push p = i - 1 unless its state
+// is unreachable (+inf), pop the front while the route p+1..i exceeds Q; an
+// empty window reads +inf (a demand above Q at position i empties it, and
+// the first such position makes every later J infinite).  With route output, i - p of every
 // (i, k) goes to the warp's scratch row [i][k] and lane 0 walks the optimal
 // split back.  A deque that outgrows its ring flags the scenario;
 // split_fleet_plain_kernel (one thread per scenario, every feasible p of
@@ -36,9 +35,9 @@ namespace sdp {
 
 namespace {
 
-constexpr int kFRing = 16;                          // deque entries per layer and lane
+constexpr int kFRing = 32;                          // deque entries per layer and lane
 constexpr uint32_t kFRingBytes = kFRing * 256u;     // one layer's ring for 32 lanes
-constexpr int kFWarps = 8;                          // warps per CTA
+constexpr int kFMaxWarps = 16;                      // warps per CTA at most (as shared memory allows)
 constexpr int kFAhead = 8;                          // demands loaded ahead
 
 __device__ __forceinline__ float flds(uint32_t a) {
@@ -74,32 +73,42 @@ struct FleetDeque {
     K = CUDART_INF_F;
     full = false;
   }
-  // push entry (psi, ent) of p = i-1, then drop expired fronts; Lc = L(i)<<16
+  // push entry (psi, ent) of p = i-1, then drop expired fronts; Lc = L(i)<<16.
+  // An unreachable state (psi = +inf) is not pushed: it could only be the
+  // minimum of an empty window, which reads +inf anyway (pushed, such entries
+  // would pile up behind each other over a long unreachable stretch).
   __device__ __forceinline__ void step(float psi, uint32_t ent, uint32_t Lc, uint32_t Qc,
                                        float ce) {
-    while (bpsi > psi) {
-      tail -= 256u;
-      bpsi = tail == head ? -CUDART_INF_F : flds(at(tail - 256u));
+    if (psi != CUDART_INF_F) {
+      while (bpsi > psi) {
+        tail -= 256u;
+        bpsi = tail == head ? -CUDART_INF_F : flds(at(tail - 256u));
+      }
+      if (tail == head) {
+        fpsi = psi;
+        fent = ent;
+      }
+      if (tail - head >= kFRingBytes) {  // full: flagged, restart at the new entry
+        full = true;
+        head = tail;
+        fpsi = psi;
+        fent = ent;
+      }
+      fsts2(at(tail), __float_as_uint(psi), ent);
+      tail += 256u;
+      bpsi = psi;
     }
-    if (tail == head) {
-      fpsi = psi;
-      fent = ent;
-    }
-    if (tail - head >= kFRingBytes) {  // full: flagged, restart at the new entry
-      full = true;
-      head = tail;
-      fpsi = psi;
-      fent = ent;
-    }
-    const uint32_t naddr = tail;
-    fsts2(at(tail), __float_as_uint(psi), ent);
-    tail += 256u;
-    bpsi = psi;
-    while (((Lc | 0xFFFFu) - fent) > Qc && head != naddr) {
+    while (tail != head && ((Lc | 0xFFFFu) - fent) > Qc) {
       head += 256u;
-      const uint2 e = flds2(at(head));
-      fpsi = __uint_as_float(e.x);
-      fent = e.y;
+      if (head != tail) {
+        const uint2 e = flds2(at(head));
+        fpsi = __uint_as_float(e.x);
+        fent = e.y;
+      }
+    }
+    if (tail == head) {  // nothing feasible in the window
+      fpsi = CUDART_INF_F;
+      bpsi = -CUDART_INF_F;
     }
     K = __fadd_rn(fpsi, ce);
   }
@@ -108,9 +117,9 @@ struct FleetDeque {
 // KS: slots per lane (layers = 32 KS >= K); ROUTES: keep i - p of every
 // (i, k) in the warp's scratch for the backtrack.
 template <int KS, bool ROUTES>
-__global__ void __launch_bounds__(kFWarps * 32) split_fleet_kernel(SplitFleetArgs a) {
+__global__ void __launch_bounds__(kFMaxWarps * 32) split_fleet_kernel(SplitFleetArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = a.n, Q = a.Q, K = a.K;
   // shared: (a_i, ce_i) and columns of the tour | per warp: KS rings,
   // route boundaries
@@ -129,11 +138,11 @@ __global__ void __launch_bounds__(kFWarps * 32) split_fleet_kernel(SplitFleetArg
   __syncthreads();
   const uint32_t Qh = (uint32_t)Q << 16, Qc = Qh | 0xFFFFu;
   const double Dn = *a.Dn;
-  const int64_t wslot = (int64_t)blockIdx.x * kFWarps + warp;
+  const int64_t wslot = (int64_t)blockIdx.x * nw + warp;
   // the warp's delta scratch: [i][k] uint16, 32 KS layers per position
   uint16_t* dsc = ROUTES ? a.dscratch + wslot * (int64_t)n * 32 * KS : nullptr;
   bool neg = false, any_fb = false, any_inf = false;
-  for (int64_t s = wslot; s < a.S; s += (int64_t)gridDim.x * kFWarps) {
+  for (int64_t s = wslot; s < a.S; s += (int64_t)gridDim.x * nw) {
     const int32_t* qrow = a.demands + s * n;
     FleetDeque dq[KS];
 #pragma unroll
@@ -318,39 +327,49 @@ __global__ void __launch_bounds__(256) split_fleet_plain_kernel(SplitFleetArgs a
   }
 }
 
-size_t fleet_smem(int n, int ks) {
-  return ((((size_t)n * 8 + (size_t)n * 2) + 255) & ~(size_t)255) +
-         (size_t)kFWarps * ((size_t)ks * kFRingBytes + 256 * 4);
-}
+size_t fleet_head(int n) { return (((size_t)n * 8 + (size_t)n * 2) + 255) & ~(size_t)255; }
+size_t fleet_per_warp(int ks) { return (size_t)ks * kFRingBytes + 256 * 4; }
 
 template <int KS, bool ROUTES>
-int launch_fleet_k(const SplitFleetArgs& a, int grid, cudaStream_t st) {
+int launch_fleet_k(const SplitFleetArgs& a, int warps, int grid, cudaStream_t st) {
   auto k = split_fleet_kernel<KS, ROUTES>;
-  const size_t smem = fleet_smem(a.n, KS);
+  const size_t smem = fleet_head(a.n) + fleet_per_warp(KS) * warps;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  k<<<grid, kFWarps * 32, smem, st>>>(a);
+  k<<<grid, warps * 32, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
 }  // namespace
 
-int fleet_grid(int n, int K, int64_t S) {
+// One CTA per SM with as many warps as its shared memory holds (up to 16);
+// fewer CTAs when there are fewer scenarios.
+FleetConfig fleet_config(int n, int K, int64_t S) {
   const int ks = K <= 32 ? 1 : 2;
-  const size_t smem = fleet_smem(n, ks);
-  const int per_sm = smem == 0 ? 1 : (int)((200 * 1024) / smem);
-  const int64_t need = (S + kFWarps - 1) / kFWarps;
-  return (int)imin64(need < 1 ? 1 : need, (int64_t)num_sms() * (per_sm < 1 ? 1 : per_sm));
+  const size_t budget = 226 * 1024;  // dynamic shared memory of one CTA per SM
+  const size_t head = fleet_head(n);
+  int warps = head >= budget ? 0 : (int)((budget - head) / fleet_per_warp(ks));
+  warps = warps > kFMaxWarps ? kFMaxWarps : warps;
+  FleetConfig c{};
+  c.warps = warps;
+  if (warps < 1) return c;
+  const int64_t need = (S + warps - 1) / warps;
+  c.grid = (int)imin64(need < 1 ? 1 : need, (int64_t)num_sms());
+  return c;
 }
 
-size_t fleet_dscratch_elems(int n, int K, int grid) {
+size_t fleet_dscratch_elems(int n, int K, const FleetConfig& c) {
   const int ks = K <= 32 ? 1 : 2;
-  return (size_t)grid * kFWarps * (size_t)n * 32 * ks;
+  return (size_t)c.grid * c.warps * (size_t)n * 32 * ks;
 }
 
-int launch_split_fleet(const SplitFleetArgs& a, int grid, cudaStream_t st) {
-  if (a.K <= 32) return a.route ? launch_fleet_k<1, true>(a, grid, st) : launch_fleet_k<1, false>(a, grid, st);
-  return a.route ? launch_fleet_k<2, true>(a, grid, st) : launch_fleet_k<2, false>(a, grid, st);
+int launch_split_fleet(const SplitFleetArgs& a, const FleetConfig& c, cudaStream_t st) {
+  if (c.warps < 1) return (int)cudaErrorInvalidValue;
+  if (a.K <= 32)
+    return a.route ? launch_fleet_k<1, true>(a, c.warps, c.grid, st)
+                   : launch_fleet_k<1, false>(a, c.warps, c.grid, st);
+  return a.route ? launch_fleet_k<2, true>(a, c.warps, c.grid, st)
+                 : launch_fleet_k<2, false>(a, c.warps, c.grid, st);
 }
 
 int launch_split_fleet_plain(const SplitFleetArgs& a, cudaStream_t st) {
