@@ -330,7 +330,7 @@ typedef struct sdp_plan sdp_plan;
  * device; every later call on the plan must run with that device current. */
 int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out);
 /* Times the candidate launch shapes (the pipelined and streaming kernels;
- * DEQUE warps per CTA x deque ring entries) on
+ * DEQUE warps per CTA x deque ring entries x scenarios per lane) on
  * `stream` -- each runs the whole plan, so outputs are overwritten -- and
  * keeps the fastest.  cache_path (optional, host string) is a text file of
  * earlier choices keyed by the device and the plan's shape: a hit skips the
@@ -353,6 +353,18 @@ int sdp_plan_kernel_ms(sdp_plan* p, float* ms);
  * k > 0: DEQUE with shared-memory staging and k warps per CTA. */
 int sdp_plan_info(const sdp_plan* p, int32_t* warps_per_cta, int32_t* ring,
                   int32_t* ctas, int64_t* items);
+/* Selects a launch shape by hand (what sdp_plan_autotune chooses among):
+ * warps_per_cta -2 (pipelined), -1 (streaming), 0 (DEQUE, tensor-memory
+ * staging) or 1..8 (DEQUE, shared-memory staging); ring 8, 16 or 32 deque
+ * entries (16 for -2 / -1 / 0); scenarios_per_lane 1, or 2 with
+ * shared-memory staging (each lane then runs two scenarios of one tour,
+ * their deques stepped together).  The next sdp_plan_run re-captures the
+ * graph.  SDP_ERR_UNSUPPORTED (and the plan keeps its shape) when the shape
+ * does not apply to this plan or does not fit an SM. */
+int sdp_plan_configure(sdp_plan* p, int32_t warps_per_cta, int32_t ring,
+                       int32_t scenarios_per_lane);
+/* Scenarios per lane of the shape in use (1 or 2). */
+int sdp_plan_scenarios_per_lane(const sdp_plan* p, int32_t* scenarios_per_lane);
 /* Total feasible arcs of the whole batch (synchronous on `stream`). */
 int sdp_plan_count_arcs(sdp_plan* p, void* stream, uint64_t* total_host);
 void sdp_plan_destroy(sdp_plan* p);

@@ -105,6 +105,8 @@ def _load():
             "sdp_plan_kernel_ms": ([P, P], i32),
             "sdp_plan_info": ([P, P, P, P, P], i32),
             "sdp_plan_count_arcs": ([P, P, P], i32),
+            "sdp_plan_configure": ([P, i32, i32, i32], i32),
+            "sdp_plan_scenarios_per_lane": ([P, P], i32),
             "sdp_saa_search_count_arcs": ([P, P, P], i32),
             "sdp_plan_destroy": ([P], None),
             "sdp_saa_search_create": ([P, P], i32),
@@ -516,10 +518,18 @@ class SplitPlan:
     def info(self):
         w, r, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         items = ctypes.c_int64()
+        ns = ctypes.c_int32()
         _check(self._lib.sdp_plan_info(self._h, ctypes.byref(w), ctypes.byref(r),
                                        ctypes.byref(c), ctypes.byref(items)))
+        _check(self._lib.sdp_plan_scenarios_per_lane(self._h, ctypes.byref(ns)))
         return {"warps_per_cta": w.value, "ring": r.value, "ctas": c.value,
-                "items": items.value}
+                "items": items.value, "scenarios_per_lane": ns.value}
+
+    def configure(self, warps_per_cta, ring=16, scenarios_per_lane=1):
+        """Select a launch shape by hand (see sdp_plan_configure)."""
+        _check(self._lib.sdp_plan_configure(self._h, int(warps_per_cta), int(ring),
+                                            int(scenarios_per_lane)))
+        return self.info()
 
     def kernel_ms(self):
         ms = ctypes.c_float()

@@ -134,8 +134,9 @@ struct BatchKernelArgs {
   uint32_t* fb_count;
   uint32_t* status;
 };
-// warps == 0: tensor-memory staging (warps per CTA chosen from n_max)
-size_t batch_smem(int n_max, int Q, int warps, int ring);
+// warps == 0: tensor-memory staging (warps per CTA chosen from n_max);
+// ns: scenarios per lane of the shared-memory kernel (1 or 2)
+size_t batch_smem(int n_max, int Q, int warps, int ring, int ns);
 int batch_tmem_warps(int n_max, int Q);
 struct BatchPrepArgs {
   const int32_t* n;
@@ -170,7 +171,7 @@ struct BatchFallbackArgs {
   int64_t nslots;
 };
 void launch_batch_fallback(const BatchFallbackArgs& a, cudaStream_t st);
-int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int grid,
+int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int ns, int grid,
                        cudaStream_t st, int* occ_out);
 
 // Split with demands streamed in tour order (SDP_ALGO_STREAM): a pre-pass

@@ -53,8 +53,9 @@ struct sdp_plan {
   const int32_t* demands = nullptr;
   float* costs = nullptr;
   double* means = nullptr;
-  // launch shape; warps == -1: the streaming kernel, -2: the pipelined one
-  int warps = 4, ring = 16, grid = 0;
+  // launch shape; warps == -1: the streaming kernel, -2: the pipelined one;
+  // ns: scenarios per lane (DEQUE kernel with shared-memory staging)
+  int warps = 4, ring = 16, ns = 1, grid = 0;
   // graph
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent kernel
@@ -99,11 +100,15 @@ BatchPrepArgs prep_args(const sdp_plan* p, uint32_t* status) {
   return a;
 }
 
-int configure(sdp_plan* p, int warps, int ring) {
+int configure(sdp_plan* p, int warps, int ring, int ns = 1) {
+  if (ns != 1 && ns != 2) return SDP_ERR_UNSUPPORTED;
+  if (ns == 2 && warps <= 0) return SDP_ERR_UNSUPPORTED;  // shared-memory DEQUE only
+  if (ring != 8 && ring != 16 && ring != 32) return SDP_ERR_UNSUPPORTED;
   if (warps == -2) {  // pipelined kernel: one CTA per SM, ring of 16 entries
     if (!p->d_pq) return SDP_ERR_UNSUPPORTED;
     p->warps = -2;
     p->ring = 16;
+    p->ns = 1;
     p->grid = pipe_grid(p->S, p->B);
     return SDP_OK;
   }
@@ -111,22 +116,25 @@ int configure(sdp_plan* p, int warps, int ring) {
     if (!p->d_qt) return SDP_ERR_UNSUPPORTED;
     p->warps = -1;
     p->ring = 16;
+    p->ns = 1;
     p->grid = num_sms();
     return SDP_OK;
   }
-  if (batch_smem(p->n_max, p->Q, warps, ring) > 227 * 1024) return SDP_ERR_UNSUPPORTED;
+  if (warps > 8) return SDP_ERR_UNSUPPORTED;
+  if (batch_smem(p->n_max, p->Q, warps, ring, ns) > 227 * 1024) return SDP_ERR_UNSUPPORTED;
   BatchKernelArgs k{};
   k.n_max = p->n_max;
   k.Q = p->Q;
   int occ = 0;
-  int e = launch_split_batch(k, warps, ring, 0, nullptr, &occ);
+  int e = launch_split_batch(k, warps, ring, ns, 0, nullptr, &occ);
   if (e) return pcuda((cudaError_t)e, "batch occupancy");
   if (occ < 1) return SDP_ERR_UNSUPPORTED;
-  const int64_t items = (int64_t)p->B * ((p->S + 31) / 32);
+  const int64_t items = (int64_t)p->B * ((((p->S + 31) / 32) + ns - 1) / ns);
   const int eff = warps > 0 ? warps : batch_tmem_warps(p->n_max, p->Q);
   const int64_t want = (items + eff - 1) / eff;
   p->warps = warps;
   p->ring = ring;
+  p->ns = ns;
   p->grid = (int)std::min<int64_t>(want, (int64_t)occ * num_sms());
   return SDP_OK;
 }
@@ -161,7 +169,7 @@ int enqueue(sdp_plan* p, cudaStream_t st, uint32_t* status, bool with_events) {
     sa.status = status; sa.qt = p->d_qt; sa.stride_max = batch_stream_stride(p->n_max, p->Q);
     e = launch_split_batch_stream(sa, st);
   } else {
-    e = launch_split_batch(k, p->warps, p->ring, p->grid, st, nullptr);
+    e = launch_split_batch(k, p->warps, p->ring, p->ns, p->grid, st, nullptr);
   }
   if (with_events) cudaEventRecordWithFlags(p->ev1, st, cudaEventRecordExternal);
   if (e) return pcuda((cudaError_t)e, "batch kernel");
@@ -364,11 +372,12 @@ int plan_autotune(sdp_plan* p, void* stream, const char* cache_path, int min_rin
       char line[512];
       while (fgets(line, sizeof(line), f)) {
         char k[400];
-        int w = 0, r = 0;
-        if (sscanf(line, "%399s %d %d", k, &w, &r) == 3 && key == k) {
+        int w = 0, r = 0, ns = 1;
+        const int got = sscanf(line, "%399s %d %d %d", k, &w, &r, &ns);
+        if (got >= 3 && key == k) {
           fclose(f);
           drop_graph(p);
-          int rc = configure(p, w, r);
+          int rc = configure(p, w, r, got == 4 ? ns : 1);
           return rc ? configure(p, 1, 8) : SDP_OK;  // cached shape no longer fits
         }
       }
@@ -380,16 +389,19 @@ int plan_autotune(sdp_plan* p, void* stream, const char* cache_path, int min_rin
   if (rc) return rc;
   const int warps_c[] = {-2, -1, 0, 1, 2, 4, 8};  // -2 pipelined, -1 streaming, 0 TMEM staging
   const int ring_c[] = {8, 16};
+  const int ns_c[] = {1, 2};  // scenarios per lane (shared-memory staging only)
   float best = 1e30f;
-  int bw = p->warps, br = p->ring;
+  int bw = p->warps, br = p->ring, bn = p->ns;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   for (int w : warps_c)
-    for (int r : ring_c) {
+    for (int r : ring_c)
+    for (int ns : ns_c) {
       if (w < 0 && r != 16) continue;  // the pipelined / streaming kernels have one ring size
+      if (w <= 0 && ns != 1) continue;
       if (r < min_ring) continue;
-      if (configure(p, w, r)) continue;
+      if (configure(p, w, r, ns)) continue;
       float tsum = 0.f;
       bool ok = true;
       for (int rep = 0; rep < 3 && ok; ++rep) {
@@ -401,17 +413,17 @@ int plan_autotune(sdp_plan* p, void* stream, const char* cache_path, int min_rin
         cudaEventElapsedTime(&ms, a, b);
         if (rep > 0) tsum += ms;  // first rep warms up
       }
-      if (ok && tsum < best) { best = tsum; bw = w; br = r; }
+      if (ok && tsum < best) { best = tsum; bw = w; br = r; bn = ns; }
     }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   drop_graph(p);
-  rc = configure(p, bw, br);
+  rc = configure(p, bw, br, bn);
   if (rc) return rc;
   if (cache_path) {
     FILE* f = fopen(cache_path, "a");
     if (f) {
-      fprintf(f, "%s %d %d\n", key.c_str(), bw, br);
+      fprintf(f, "%s %d %d %d\n", key.c_str(), bw, br, bn);
       fclose(f);
     }
   }
@@ -423,6 +435,24 @@ extern "C" {
 
 int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path) {
   return plan_autotune(p, stream, cache_path, 8);
+}
+
+int sdp_plan_configure(sdp_plan* p, int32_t warps_per_cta, int32_t ring, int32_t scenarios_per_lane) {
+  if (!p) return pfail(SDP_ERR_INVALID_ARG, "plan is NULL");
+  const int old_w = p->warps, old_r = p->ring, old_n = p->ns;
+  const int rc = configure(p, warps_per_cta, ring, scenarios_per_lane);
+  if (rc) {
+    configure(p, old_w, old_r, old_n);  // keep the plan usable
+    return rc == SDP_ERR_UNSUPPORTED ? pfail(rc, "launch shape not available for this plan") : rc;
+  }
+  drop_graph(p);
+  return SDP_OK;
+}
+
+int sdp_plan_scenarios_per_lane(const sdp_plan* p, int32_t* ns) {
+  if (!p || !ns) return pfail(SDP_ERR_INVALID_ARG, "NULL argument");
+  *ns = p->ns;
+  return SDP_OK;
 }
 
 int sdp_plan_count_arcs(sdp_plan* p, void* stream, uint64_t* total_host) {

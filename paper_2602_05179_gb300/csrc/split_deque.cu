@@ -1375,20 +1375,24 @@ __global__ void __launch_bounds__(512, 1) split_tmem_soft_kernel(SplitDequeArgs 
 // Batched Split: a persistent grid pulls work items (tour, 32-scenario tile)
 // from a global counter; items are ordered longest tour first, so the uneven
 // tours finish together.
-template <typename QT, int RING>
+// NS tiles of one tour per warp item (NS = 2: scenarios s0 + lane and
+// s0 + 32 + lane on each lane, the two deques stepped together), rows staged
+// in shared memory.
+template <typename QT, int RING, int NS>
 __global__ void __launch_bounds__(256, 1) split_batch_kernel(BatchKernelArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int Q = a.Q;
   const int row_bytes_max = staged_row_stride(a.n_max, (int)sizeof(QT));
-  const size_t per_warp = (size_t)32 * row_bytes_max + ring_bytes(RING);
+  const size_t per_warp = NS * ((size_t)32 * row_bytes_max + ring_bytes(RING));
   unsigned char* wbase = smem + per_warp * warp;
-  QT* qb = reinterpret_cast<QT*>(wbase);
-  uint2* ring_pl = reinterpret_cast<uint2*>(wbase + (size_t)32 * row_bytes_max);
-  uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + RING * 32);
+  QT* qb = reinterpret_cast<QT*>(wbase);  // NS blocks of 32 rows
+  uint2* ring_pl = reinterpret_cast<uint2*>(wbase + (size_t)NS * 32 * row_bytes_max);
+  uint16_t* ring_idx = reinterpret_cast<uint16_t*>(ring_pl + NS * RING * 32);
   const int64_t tiles = (a.S + 31) / 32;
-  const int64_t items = tiles * a.B;
+  const int64_t per_tour = (tiles + NS - 1) / NS;  // items per tour
+  const int64_t items = per_tour * a.B;
   bool neg = false;
   uint32_t any_inf = 0, any_fb = 0;
 
@@ -1399,44 +1403,62 @@ __global__ void __launch_bounds__(256, 1) split_batch_kernel(BatchKernelArgs a) 
   };
   int64_t item = pop();
   while (item < items) {
-    const int b = a.order[item / tiles];
-    const int64_t s0 = (item % tiles) * 32;
+    const int b = a.order[item / per_tour];
+    const int64_t s0 = (item % per_tour) * 32 * NS;
     const int n = a.n[b];
-    const int rows = (int)imin64(32, a.S - s0);
     const int rs_elems = staged_row_stride(n, (int)sizeof(QT)) / (int)sizeof(QT);
-    const TileFlags tf = ingest_tile<QT>(a.demands + a.dem_off[b] + s0 * n, rows, n, rs_elems,
-                                         Q, qb, lane);
-    neg |= tf.neg;
+    int rows[NS];
+    uint32_t tinf = 0;
+    SmemQ<QT> src[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int64_t st = s0 + 32 * s;
+      rows[s] = st >= a.S ? 0 : (int)imin64(32, a.S - st);
+      QT* qs = qb + (size_t)s * 32 * row_bytes_max / sizeof(QT);
+      if (rows[s] > 0) {
+        const TileFlags tf = ingest_tile<QT>(a.demands + a.dem_off[b] + st * n, rows[s], n,
+                                             rs_elems, Q, qs, lane);
+        neg |= tf.neg;
+        tinf |= tf.inf_rows;
+      }
+      src[s] = SmemQ<QT>{qs + lane * rs_elems, 0};
+    }
     const int64_t next = pop();
     __syncwarp();
-    uint32_t first_inf = (uint32_t)n + 1;
-    bool bad = false;
-    float K;
-    QT* row = qb + lane * rs_elems;
-    const StepRec* rec = a.rec + a.rec_off[b];
-    SmemQ<QT> src{row, 0};
-    if (tf.inf_rows)
-      dp_rows<1, QT, int32_t, RING, kOutNone, true, false>(&src, row, n, Q, rec, ring_pl,
-                                                           ring_idx, lane, nullptr, nullptr, 0,
-                                                           false, &first_inf, &bad, &K);
-    else
-      dp_rows<1, QT, int32_t, RING, kOutNone, false, false>(&src, row, n, Q, rec, ring_pl,
-                                                            ring_idx, lane, nullptr, nullptr, 0,
-                                                            false, &first_inf, &bad, &K);
-    const bool valid = lane < rows;
-    bad = bad && valid;
-    if (valid) {
-      const int64_t g = (int64_t)b * a.S + s0 + lane;
-      if (bad) {
-        const uint32_t k = atomicAdd(a.fb_count, 1u);
-        a.fb_list[k] = (unsigned long long)g;
-      } else {
-        a.costs[g] = first_inf <= (uint32_t)n ? CUDART_INF_F
-                                               : (float)((double)K + a.Dn[b]);
-      }
+    uint32_t first_inf[NS];
+    bool bad[NS];
+    float K[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      first_inf[s] = (uint32_t)n + 1;
+      bad[s] = false;
     }
-    any_inf |= tf.inf_rows;
-    any_fb |= __ballot_sync(0xffffffffu, bad);
+    const StepRec* rec = a.rec + a.rec_off[b];
+    if (tinf)
+      dp_rows<NS, QT, int32_t, RING, kOutNone, true, false>(src, src[0].row, n, Q, rec, ring_pl,
+                                                            ring_idx, lane, nullptr, nullptr, 0,
+                                                            false, first_inf, bad, K);
+    else
+      dp_rows<NS, QT, int32_t, RING, kOutNone, false, false>(src, src[0].row, n, Q, rec, ring_pl,
+                                                             ring_idx, lane, nullptr, nullptr, 0,
+                                                             false, first_inf, bad, K);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const bool valid = lane < rows[s];
+      const bool bd = bad[s] && valid;
+      if (valid) {
+        const int64_t g = (int64_t)b * a.S + s0 + 32 * s + lane;
+        if (bd) {
+          const uint32_t k = atomicAdd(a.fb_count, 1u);
+          a.fb_list[k] = (unsigned long long)g;
+        } else {
+          a.costs[g] = first_inf[s] <= (uint32_t)n ? CUDART_INF_F
+                                                     : (float)((double)K[s] + a.Dn[b]);
+        }
+      }
+      any_fb |= __ballot_sync(0xffffffffu, bd);
+    }
+    any_inf |= tinf;
     __syncwarp();
     item = next;
   }
@@ -1717,20 +1739,20 @@ int batch_tmem_warps(int n_max, int Q) {
   return 0;  // too long for TMEM
 }
 
-size_t batch_smem(int n_max, int Q, int warps, int ring) {
+size_t batch_smem(int n_max, int Q, int warps, int ring, int ns) {
   const int qbytes = Q <= 254 ? 1 : 2;
   if (warps == 0) {
     const int tw = batch_tmem_warps(n_max, Q);
     const size_t need = (size_t)tw * (ring_bytes(ring) + ((size_t)n_max + 2) * sizeof(StepRec));
     return need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem;
   }
-  return (size_t)warps * ((size_t)32 * staged_row_stride(n_max, qbytes) + ring_bytes(ring));
+  return (size_t)warps * ns * ((size_t)32 * staged_row_stride(n_max, qbytes) + ring_bytes(ring));
 }
 
 namespace {
-template <typename QT, int RING>
+template <typename QT, int RING, int NS>
 int batch_t(const BatchKernelArgs& a, int warps, int grid, cudaStream_t st, int* occ) {
-  const size_t smem = batch_smem(a.n_max, a.Q, warps, RING);
+  const size_t smem = batch_smem(a.n_max, a.Q, warps, RING, warps == 0 ? 1 : NS);
   if (warps == 0) {
     const int tw = batch_tmem_warps(a.n_max, a.Q);
     if (tw == 0) {
@@ -1749,7 +1771,7 @@ int batch_t(const BatchKernelArgs& a, int warps, int grid, cudaStream_t st, int*
     k<<<grid, tw * 32, smem, st>>>(a, 512 / (tw / 4));
     return (int)cudaGetLastError();
   }
-  auto k = split_batch_kernel<QT, RING>;
+  auto k = split_batch_kernel<QT, RING, NS>;
   if (occ) {  // configuration query (never during a stream capture)
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
@@ -1758,20 +1780,23 @@ int batch_t(const BatchKernelArgs& a, int warps, int grid, cudaStream_t st, int*
   k<<<grid, warps * 32, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
-template <typename QT>
+template <typename QT, int NS>
 int batch_ring(const BatchKernelArgs& a, int warps, int ring, int grid, cudaStream_t st, int* occ) {
   switch (ring) {
-    case 8: return batch_t<QT, 8>(a, warps, grid, st, occ);
-    case 32: return batch_t<QT, 32>(a, warps, grid, st, occ);
-    default: return batch_t<QT, 16>(a, warps, grid, st, occ);
+    case 8: return batch_t<QT, 8, NS>(a, warps, grid, st, occ);
+    case 32: return batch_t<QT, 32, NS>(a, warps, grid, st, occ);
+    default: return batch_t<QT, 16, NS>(a, warps, grid, st, occ);
   }
 }
 }  // namespace
 
-int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int grid, cudaStream_t st,
-                       int* occ_out) {
-  if (a.Q <= 254) return batch_ring<uint8_t>(a, warps, ring, grid, st, occ_out);
-  return batch_ring<uint16_t>(a, warps, ring, grid, st, occ_out);
+int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int ns, int grid,
+                       cudaStream_t st, int* occ_out) {
+  if (ns == 2 && warps > 0)
+    return a.Q <= 254 ? batch_ring<uint8_t, 2>(a, warps, ring, grid, st, occ_out)
+                      : batch_ring<uint16_t, 2>(a, warps, ring, grid, st, occ_out);
+  if (a.Q <= 254) return batch_ring<uint8_t, 1>(a, warps, ring, grid, st, occ_out);
+  return batch_ring<uint16_t, 1>(a, warps, ring, grid, st, occ_out);
 }
 
 // ---- fused adjoint with TMEM staging

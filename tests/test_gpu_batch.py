@@ -67,6 +67,7 @@ def test_batch_small_vs_oracle_and_eager(Q, qhi, tmp_path):
     cache = str(tmp_path / "tune.txt")
     info = plan.autotune(cache)
     assert info["warps_per_cta"] in (-2, -1, 0, 1, 2, 4, 8) and info["ring"] in (8, 16)
+    assert info["scenarios_per_lane"] in (1, 2)
     plan.run()
     torch.cuda.synchronize()
     assert torch.equal(costs, c1)
@@ -145,6 +146,42 @@ def test_batch_pipe_and_deque_plans_bit_identical(Q, qhi):
     assert api().status() & api().FLAG_INFEASIBLE
     plan_p.close()
     plan_d.close()
+
+
+@pytest.mark.parametrize("Q,qhi", [(150, 40), (600, 90)])
+def test_batch_every_autotune_shape_bit_identical(Q, qhi):
+    """Every launch shape the autotuner chooses among -- pipelined, streaming,
+    TMEM-staged DEQUE, and shared-memory DEQUE with 1..8 warps per CTA, 8 or
+    16 deque entries and one or two scenarios per lane -- gives the same bits
+    (tours of 1..500 customers, S = 165: a ragged last tile, and with two
+    scenarios per lane a last pair holding one tile)."""
+    B, S = 23, 165
+    n, tours, coords, dem = _batch(300 + Q, B, S, Q, 1, 500, qhi)
+    dem[2][4, 1] = Q + 1
+    plan, keep = _plan(n, tours, coords, dem, Q, S)
+    ref, refm = plan.run()
+    torch.cuda.synchronize()
+    ref, refm = ref.clone(), refm.clone()
+    shapes = [(-2, 16, 1), (-1, 16, 1), (0, 16, 1)]
+    shapes += [(w, r, ns) for w in (1, 2, 4, 8) for r in (8, 16) for ns in (1, 2)]
+    tried, tried_ns2 = 0, 0
+    for w, r, ns in shapes:
+        try:
+            info = plan.configure(w, r, ns)
+        except api().SdpError as e:
+            assert e.code == -5
+            continue
+        assert (info["warps_per_cta"], info["ring"], info["scenarios_per_lane"]) == (w, r, ns)
+        costs, means = plan.run()
+        torch.cuda.synchronize()
+        assert torch.equal(costs, ref), (w, r, ns)
+        assert torch.equal(means.isinf(), refm.isinf())
+        tried += 1
+        tried_ns2 += ns == 2
+    # (uint16 rows of up to 500 customers leave fewer shapes fitting an SM)
+    assert tried >= 9 and tried_ns2 >= 2
+    assert api().status() & api().FLAG_INFEASIBLE
+    plan.close()
 
 
 def test_batch_infeasible_and_fallback():
