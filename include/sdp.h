@@ -93,7 +93,7 @@ extern "C" {
                              same CTA, which narrow and permute each tile's
                              demand rows into tour order in a small ring of
                              tile slots that stays in L2 (no pre-pass over
-                             HBM), with 28 DP warps per SM; predecessors
+                             HBM), with 23 DP warps per SM; predecessors
                              leave through a shared-memory transpose as row
                              segments.  Needs hard capacity, 1 <= n <= 1024,
                              Q <= 32767 and 16-byte aligned demands; the

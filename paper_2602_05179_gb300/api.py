@@ -182,7 +182,7 @@ def set_profile_events(start, stop):
 def last_launch():
     """(warps per CTA, CTAs) of the DP kernel of this thread's last Split
     evaluation or adjoint call; (0, 0) for the streaming path, (32, CTAs) for
-    the pipelined one (28 DP + 4 producer warps)."""
+    the pipelined one (23 DP, 1 issuing and 8 narrowing warps)."""
     w, c = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(_load().sdp_last_launch(ctypes.byref(w), ctypes.byref(c)))
     return int(w.value), int(c.value)

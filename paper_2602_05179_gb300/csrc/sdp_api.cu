@@ -499,7 +499,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     pa.stall = stall ? 1 : 0;
     cudaError_t ce = cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), st);
     if (ce != cudaSuccess) return cuda_fail(ce, "pipe counter reset");
-    note_launch(32, pipe_grid(a->S, 1));  // 28 DP + 4 producer warps
+    note_launch(32, pipe_grid(a->S, 1));  // 23 DP + 1 issuing + 8 narrowing warps
     prof_begin(st);
     const int e = launch_split_pipe(pa, st);
     prof_end(st);
@@ -549,6 +549,18 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     e = launch_split_deque(d, cfg, grid, st);
     prof_end(st);
     if (e) return cuda_fail((cudaError_t)e, "split_deque launch");
+  }
+  if (algo != SDP_ALGO_PLAIN && !hist && a->capacity_mode != SDP_CAPACITY_SOFT &&
+      rescue_supported(a->n)) {
+    // the scenarios the DP kernel flagged, one warp each
+    RescueArgs r{};
+    r.batched = 0; r.Q = a->Q; r.S = a->S; r.n_max = a->n; r.n1 = a->n;
+    r.fb_list1 = w.fb_list; r.cost = cost; r.pred = pred; r.pred_dtype = a->pred_dtype;
+    r.rec = w.prep.rec; r.Dn = w.prep.Dn; r.demands = a->demands;
+    r.fb_count = w.fb_count; r.status = status;
+    const int e = launch_split_rescue(r, a->S, st);
+    if (e) return cuda_fail((cudaError_t)e, "split_rescue launch");
+    return SDP_OK;
   }
   SplitPlainArgs p{};
   p.n = a->n; p.Q = a->Q; p.S = a->S;

@@ -171,6 +171,37 @@ struct BatchFallbackArgs {
   int64_t nslots;
 };
 void launch_batch_fallback(const BatchFallbackArgs& a, cudaStream_t st);
+
+// Warp-per-scenario recomputation of flagged hard-capacity scenarios
+// (split_rescue.cu), one tour or a batched plan's entries; the same FP32
+// results as the plain kernel.
+struct RescueArgs {
+  int batched;
+  int Q;
+  int64_t S;
+  int n_max;                   // longest tour (shared memory per warp: 8 (n_max+1) bytes)
+  // one tour
+  int n1;
+  const uint32_t* fb_list1;    // [*fb_count] scenario ids
+  float* cost;                 // [S]
+  void* pred;                  // [S, n] or NULL
+  int pred_dtype;
+  // batched: entry g = b*S + s
+  const int32_t* n;
+  const int64_t* rec_off;
+  const int64_t* dem_off;
+  const unsigned long long* fb_list;
+  float* costs;                // [B*S]
+  // both
+  const StepRec* rec;
+  const double* Dn;            // [1] or [B]
+  const int32_t* demands;
+  const uint32_t* fb_count;
+  uint32_t* status;
+};
+bool rescue_supported(int n_max);
+// max_work: the most entries the list can hold (sizes the grid)
+int launch_split_rescue(const RescueArgs& a, int64_t max_work, cudaStream_t st);
 int launch_split_batch(const BatchKernelArgs& a, int warps, int ring, int ns, int grid,
                        cudaStream_t st, int* occ_out);
 

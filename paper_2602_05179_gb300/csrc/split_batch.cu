@@ -10,7 +10,7 @@
 // flagged scenarios -> per-tour FP64 means], captured once in a CUDA graph
 // and replayed.  The persistent kernel is the pipelined one
 // (split_pipe_kernel: producer warps narrow each tile's rows into tour order
-// in an L2-resident slot ring, 28 DP warps per SM) when the demand offsets
+// in an L2-resident slot ring, 23 DP warps per SM) when the demand offsets
 // allow bulk copies and every tour has n <= 1024, else the streaming one
 // (split_batch_stream_kernel), else the DEQUE batched kernel.
 // sdp_plan_autotune times the launch shapes (pipelined; streaming; DEQUE
@@ -173,12 +173,24 @@ int enqueue(sdp_plan* p, cudaStream_t st, uint32_t* status, bool with_events) {
   }
   if (with_events) cudaEventRecordWithFlags(p->ev1, st, cudaEventRecordExternal);
   if (e) return pcuda((cudaError_t)e, "batch kernel");
-  BatchFallbackArgs f{};
-  f.Q = p->Q; f.S = p->S; f.n = p->d_n; f.dem_off = p->d_dem_off; f.rec_off = p->d_rec_off;
-  f.rec = p->d_rec; f.Dn = p->d_Dn; f.demands = p->demands; f.costs = p->costs;
-  f.fb_list = p->d_fb_list; f.fb_count = p->d_fb_count; f.kscratch = p->d_kscratch;
-  f.nslots = p->nslots;
-  launch_batch_fallback(f, st);
+  if (rescue_supported(p->n_max)) {
+    // the entries the DP kernel flagged, one warp each
+    RescueArgs r{};
+    r.batched = 1; r.Q = p->Q; r.S = p->S; r.n_max = p->n_max;
+    r.n = p->d_n; r.rec_off = p->d_rec_off; r.dem_off = p->d_dem_off;
+    r.fb_list = p->d_fb_list; r.costs = p->costs;
+    r.rec = p->d_rec; r.Dn = p->d_Dn; r.demands = p->demands;
+    r.fb_count = p->d_fb_count; r.status = status;
+    const int er = launch_split_rescue(r, (int64_t)p->B * p->S, st);
+    if (er) return pcuda((cudaError_t)er, "batch rescue");
+  } else {
+    BatchFallbackArgs f{};
+    f.Q = p->Q; f.S = p->S; f.n = p->d_n; f.dem_off = p->d_dem_off; f.rec_off = p->d_rec_off;
+    f.rec = p->d_rec; f.Dn = p->d_Dn; f.demands = p->demands; f.costs = p->costs;
+    f.fb_list = p->d_fb_list; f.fb_count = p->d_fb_count; f.kscratch = p->d_kscratch;
+    f.nslots = p->nslots;
+    launch_batch_fallback(f, st);
+  }
   if (p->means) launch_batch_means(p->costs, p->B, p->S, p->means, st);
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return pcuda(ce, "batch enqueue");

@@ -18,7 +18,9 @@
 //   - the front is the argmin (kept in registers).
 // The deque is a ring of RING entries per lane in shared memory, laid out
 // [entry][lane] so every access is bank-conflict free.  A scenario whose
-// deque outgrows the ring is flagged and recomputed by the plain kernel.
+// deque outgrows the ring is flagged and recomputed: by one warp
+// (split_rescue.cu) for hard capacity, by the plain kernel for soft capacity
+// and the adjoint.
 //
 // Demand staging (two variants of the same DP).
 //   Shared memory: the tile's rows are contiguous in HBM (row-major [S, n]);
@@ -552,7 +554,7 @@ struct DequeState {
 //     a [RING][32] ring of 8-byte entries.
 // The newest entry (route s_i alone, load q_i <= Q) never pops from the
 // front, so neither loop can empty the deque.  A scenario whose deque
-// outgrows the ring is recomputed by the plain kernel.
+// outgrows the ring is recomputed (split_rescue.cu).
 template <int RING>
 struct FastDeque {
   unsigned char* lb;   // this lane's slot 0 of the ring

@@ -48,11 +48,13 @@
 //     emptiness test (it stops at the front at the latest);
 //   - the newest entry (route s_i alone, load q_i <= Q) never pops from the
 //     front, so neither loop empties the deque;
-//   - the deque holds at most 12 entries every 4 steps (the ring has 16): a
-//     lane over that is flagged (its scenario is recomputed by the plain
-//     kernel) and its deque restarts at its newest entry, so the ring always
-//     holds the deque it describes and both loops end.  (At n = 500 the
-//     largest deque seen in 64,000 seeded scenarios had 12 entries.)
+//   - the deque holds at most 14 entries every 2 steps (the ring has 16): a
+//     lane over that is flagged (its scenario is recomputed by the warp
+//     kernel of split_rescue.cu) and its deque restarts at its newest entry,
+//     so the ring always holds the deque it describes and both loops end.
+//     (At n = 500 the largest deque seen in 64,000 seeded scenarios had 12
+//     entries; a seeded n = 1000 tour with Q = 400 reached 16 in 6% of its
+//     scenarios, which a test every 4 steps at 12 entries flagged.)
 // Tiles with a demand above Q (flagged by the producers) take a checked step
 // with emptiness tests, the first infeasible position recorded and an exact
 // ring test at every push.
@@ -77,8 +79,10 @@ constexpr int kRing = 16;                      // deque entries per lane
 constexpr uint32_t kRingBytes = (uint32_t)kRing * 256u;  // 32 lanes x 8 bytes per entry
 constexpr uint32_t kRingMask = (uint32_t)(kRing - 1) << 8;
 constexpr uint32_t kOutBytes = 32u * 32u;      // predecessor stage per warp: 32 rows x 32 bytes
-constexpr int kCheckEvery = 4;                 // steps between ring tests (lean step)
-constexpr uint32_t kMaxAtCheck = 12u;          // entries allowed at a test (+4 pushes <= 16)
+constexpr int kCheckEvery = 2;                 // steps between ring tests (lean step)
+constexpr uint32_t kMaxAtCheck = 14u;          // entries allowed at a test (+2 pushes <= 16)
+static_assert(kMaxAtCheck + kCheckEvery <= (uint32_t)kRing && 16 % kCheckEvery == 0,
+              "a test must leave room for the pushes until the next one");
 
 // Stage bookkeeping written by the issuing warp before it arms the stage's
 // full barrier (release), read by the narrowing warps after their wait on it

@@ -1,6 +1,6 @@
 """GPU parity of the pipelined Split path (SDP_ALGO_PIPE: producer warps
 narrow and permute each tile's demand rows into tour order in an L2-resident
-slot ring, 28 DP warps per SM run the deque step, predecessors leave through
+slot ring, 23 DP warps per SM run the deque step, predecessors leave through
 a shared-memory transpose) against the FP64 oracle and, bit for bit, against
 the PLAIN and DEQUE kernels, through the C ABI."""
 import ctypes
@@ -176,7 +176,7 @@ def test_pipe_ring_overflow_fallback():
 
 def test_pipe_monotone_window_overflow():
     """Customers on a ray from the depot, zero demands: psi rises along the
-    tour, nothing pops from the back, and the deque outgrows the 12 entries
+    tour, nothing pops from the back, and the deque outgrows the 14 entries
     the ring test allows; those scenarios are recomputed and match the
     oracle."""
     n, S, Q = 60, 40, 1000
