@@ -305,7 +305,7 @@ SplitWs carve_split(const sdp_split_args* a, void* base, bool backward) {
     const int64_t rows = (n > 0 && is_host_ptr(a->demands))
                              ? (a->S < kHostChunkRows ? a->S : kHostChunkRows)
                              : a->S;
-    w.qt = c.take<unsigned char>(pipe_ring_bytes(n, a->Q, pipe_grid(rows, 1)));
+    w.qt = c.take<unsigned char>(pipe_ring_bytes(n, a->Q, rows, 1, false));
     w.counter = c.take<unsigned long long>(1);
   }
   if (algo == SDP_ALGO_STREAM && !backward && n > 0) {
@@ -499,7 +499,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     pa.stall = stall ? 1 : 0;
     cudaError_t ce = cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), st);
     if (ce != cudaSuccess) return cuda_fail(ce, "pipe counter reset");
-    note_launch(32, pipe_grid(a->S, 1));  // 23 DP + 1 issuing + 8 narrowing warps
+    note_launch(32, pipe_grid(a->S, 1, false));  // 23 DP + 1 issuing + 8 narrowing warps
     prof_begin(st);
     const int e = launch_split_pipe(pa, st);
     prof_end(st);

@@ -285,6 +285,7 @@ struct PipeArgs {
   void* pred;                  // one tour only: [S*n] or NULL
   int pred_dtype;
   unsigned char* qt;           // slot ring, pipe_ring_bytes
+  int nslot;                   // slots per CTA (set by launch_split_pipe)
   int64_t stride;              // bytes per slot row (pipe_row_stride of the longest tour)
   unsigned long long* counter; // group queue, zero at launch
   uint32_t* fb_count;
@@ -303,8 +304,8 @@ __host__ __device__ inline int64_t pipe_row_stride(int n, int Q) {
 }
 // CTAs of a launch (one per SM at most, none without work) and the slot
 // ring they need
-int pipe_grid(int64_t S, int B);
-size_t pipe_ring_bytes(int n_max, int Q, int grid);
+int pipe_grid(int64_t S, int B, bool batched);
+size_t pipe_ring_bytes(int n_max, int Q, int64_t S, int B, bool batched);
 int launch_split_pipe(const PipeArgs& a, cudaStream_t st);
 
 // Fleet-limited Split (at most K routes, K <= 64): one warp per scenario

@@ -109,7 +109,7 @@ int configure(sdp_plan* p, int warps, int ring, int ns = 1) {
     p->warps = -2;
     p->ring = 16;
     p->ns = 1;
-    p->grid = pipe_grid(p->S, p->B);
+    p->grid = pipe_grid(p->S, p->B, true);
     return SDP_OK;
   }
   if (warps < 0) {  // streaming kernel: one CTA per SM, ring of 16 entries
@@ -296,7 +296,7 @@ int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out) {
   // the pipelined kernel bulk-copies the same way, for tours of n <= 1024
   if (stream_ok && pipe_supported(p->n_max, p->Q))
     chk(alloc_copy<unsigned char>(&p->d_pq, nullptr,
-                                  pipe_ring_bytes(p->n_max, p->Q, pipe_grid(p->S, p->B))));
+                                  pipe_ring_bytes(p->n_max, p->Q, p->S, p->B, true)));
   if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
   if (e != cudaSuccess) {

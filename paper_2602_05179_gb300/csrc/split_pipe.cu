@@ -71,14 +71,23 @@ constexpr int kDp = 23;                        // DP warps per CTA
 constexpr int kNarrow = 8;                     // narrowing warps per CTA (+ one issuing warp)
 constexpr int kNarrowThreads = kNarrow * 32;
 constexpr int kThreads = (kDp + 1 + kNarrow) * 32;  // 1024 threads: 64 registers each
-constexpr int kSlots = 32;                     // tile slots per CTA in the ring
+constexpr int kSlots = 32;                     // tile slots per CTA in the ring, at most
 constexpr uint32_t kStage = 16u * 1024u;       // bytes per producer stage
 constexpr int kNStage = 4;                     // stages (copies in flight per CTA)
-constexpr int kGroup = 16;                     // tiles per claimed group
+// tiles per claimed group: one tour takes them one at a time, so that the
+// CTAs' tile counts differ by one at most and every DP warp of the launch
+// gets within a tile of the same share (groups of 16 left 208 tiles on most
+// CTAs, 9.04 rounds of 23 warps, where the mean is 8.94: 1.204 -> 1.174 ms
+// at n = 500, S = 10^6); a batched plan claims 16, since every group may
+// change the tour, and a new tour waits for the chunks in flight.
+constexpr int kGroupOne = 1;
+constexpr int kGroupBatch = 16;
+__host__ __device__ constexpr int pipe_group(bool batched) { return batched ? kGroupBatch : kGroupOne; }
 constexpr int kRing = 16;                      // deque entries per lane
 constexpr uint32_t kRingBytes = (uint32_t)kRing * 256u;  // 32 lanes x 8 bytes per entry
 constexpr uint32_t kRingMask = (uint32_t)(kRing - 1) << 8;
 constexpr uint32_t kOutBytes = 32u * 32u;      // predecessor stage per warp: 32 rows x 32 bytes
+constexpr int kColsStride = kPipeMaxN + 8;     // uint16 entries per column table
 constexpr int kCheckEvery = 2;                 // steps between ring tests (lean step)
 constexpr uint32_t kMaxAtCheck = 14u;          // entries allowed at a test (+2 pushes <= 16)
 static_assert(kMaxAtCheck + kCheckEvery <= (uint32_t)kRing && 16 % kCheckEvery == 0,
@@ -246,8 +255,10 @@ struct GlobalRec2 {
 
 // Predecessors of one warp tile through a [32 rows][8 words] shared stage:
 // a 32-byte row segment holds W = 32 / sizeof(PT) positions.  Lane l writes
-// word j of its row at l * 8 + (j ^ ((l >> 2) & 7)) and the flush reads row
-// r word k at r * 8 + (k ^ ((r >> 2) & 7)): both conflict-free.
+// word j of its row at l * 8 + (j ^ s(l)), s(l) = 2 ((l >> 2) & 3), and the
+// flush reads row r word k at r * 8 + (k ^ s(r)).  The swizzle is even, so
+// the word pairs a full flush moves as 8 bytes stay in order; the writes
+// meet 2-way bank conflicts (a shared-memory cycle, not an issue slot).
 template <typename PT>
 struct PredStage {
   uint32_t* st;     // this warp's stage
@@ -255,15 +266,15 @@ struct PredStage {
   int n, rows, lane;
   bool pairs;       // uint16: every row segment starts on 4 bytes (n even, aligned base)
   bool wide;        // every row segment starts on 8 bytes: full flushes store 8 bytes a lane
-  uint32_t pend;    // uint16: low half of the word being packed
+  uint32_t pend;    // uint16: the even position of the word being packed (its low half is used)
   static constexpr int W = 32 / (int)sizeof(PT);
   __device__ __forceinline__ void put(int pos, uint32_t p) {  // pos = (i - 1) % W
-    const int sw = (lane >> 2) & 7;
+    const int sw = ((lane >> 2) & 3) << 1;  // even: word pairs stay in order
     if (sizeof(PT) == 2) {
       if ((pos & 1) == 0) {
-        pend = p & 0xFFFFu;
+        pend = p;
       } else {
-        st[lane * 8 + ((pos >> 1) ^ sw)] = pend | (p << 16);
+        st[lane * 8 + ((pos >> 1) ^ sw)] = __byte_perm(pend, p, 0x5410);
       }
     } else {
       st[lane * 8 + (pos ^ sw)] = p;
@@ -271,7 +282,7 @@ struct PredStage {
   }
   // positions i0 .. i0 + cnt - 1 (1-based) of every row
   __device__ __forceinline__ void flush(int i0, int cnt) {
-    if (sizeof(PT) == 2 && (cnt & 1)) st[lane * 8 + ((cnt >> 1) ^ ((lane >> 2) & 7))] = pend;
+    if (sizeof(PT) == 2 && (cnt & 1)) st[lane * 8 + ((cnt >> 1) ^ (((lane >> 2) & 3) << 1))] = pend;
     __syncwarp();
     constexpr int PER = 4 / (int)sizeof(PT);
     if (wide && cnt == W) {
@@ -281,11 +292,11 @@ struct PredStage {
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int r = 8 * m + (lane >> 2);
-        const int sz = (r >> 2) & 7;
-        const uint2 v = *reinterpret_cast<const uint2*>(st + r * 8 + ((2 * k2 ^ sz) & ~1));
+        const int sz = ((r >> 2) & 3) << 1;
+        const uint2 v = *reinterpret_cast<const uint2*>(st + r * 8 + (2 * k2 ^ sz));
         if (r < rows) {
           PT* dst = tile + (int64_t)r * n + (i0 - 1) + 2 * k2 * PER;
-          *reinterpret_cast<uint2*>(dst) = (sz & 1) ? make_uint2(v.y, v.x) : v;
+          *reinterpret_cast<uint2*>(dst) = v;
         }
       }
       __syncwarp();
@@ -295,7 +306,7 @@ struct PredStage {
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int r = 4 * m + (lane >> 3);
-      const uint32_t v = st[r * 8 + (k ^ (m & 7))];
+      const uint32_t v = st[r * 8 + (k ^ ((m & 3) << 1))];
       if (r < rows && k * PER < cnt) {
         PT* dst = tile + (int64_t)r * n + (i0 - 1) + k * PER;
         if (sizeof(PT) == 4) {
@@ -333,7 +344,7 @@ __device__ __forceinline__ void pipe_tile(int n, int Q, const unsigned char* qro
   for (int v = 0; v < V; ++v) c[v] = ld_cg_v4(src + v);
   auto pred_of = [&](int i) -> uint32_t {
     if (CHECK && (uint32_t)i >= first_inf) return 0xFFFFFFFFu;
-    return st.fent & 0xFFFFu;
+    return sizeof(PT) == 2 ? st.fent : (st.fent & 0xFFFFu);
   };
   for (int b = 0; b < nblk; ++b) {
     const int bn = min(b + 1, last);
@@ -403,7 +414,11 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   unsigned char* tail_sm = smem + rings_off + (size_t)kDp * kRingBytes +
                            (PRED ? (size_t)kDp * kOutBytes : 0);
   float2* rec2 = reinterpret_cast<float2*>(tail_sm);
-  uint16_t* cols = reinterpret_cast<uint16_t*>(tail_sm + (BATCH ? 0 : (size_t)a.n1 * sizeof(float2)));
+  // the tour's columns; a batched plan keeps two tables, by tour generation
+  // parity, so that the issuer can write the next tour's while chunks of the
+  // current one are narrowed
+  uint16_t* cols0 = reinterpret_cast<uint16_t*>(tail_sm + (BATCH ? 0 : (size_t)a.n1 * sizeof(float2)));
+  auto cols_of = [&](int g) -> uint16_t* { return cols0 + (BATCH ? (g & 1) * kColsStride : 0); };
   // stage k: full (the issuer's expect_tx + the bulk copy) and empty (one
   // arrival per narrowing warp) barriers
   const uint32_t full0 = smem_u32(&full_bar[0]), empty0 = smem_u32(&empty_bar[0]);
@@ -428,8 +443,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     }
   }
   __syncthreads();
-  unsigned char* qslots = a.qt + (int64_t)blockIdx.x * kSlots * 32 * a.stride;
+  const uint32_t nslot = (uint32_t)a.nslot;  // this launch's slots per CTA (<= kSlots)
+  unsigned char* qslots = a.qt + (int64_t)blockIdx.x * nslot * 32 * a.stride;
   const int64_t tpt = (S + 31) / 32;                 // tiles per tour
+  constexpr int kGroup = pipe_group(BATCH);
   const int64_t gpt = (tpt + kGroup - 1) / kGroup;   // groups per tour
   const int64_t groups = gpt * a.B;
 
@@ -445,6 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     // narrowed.  Lane 0 does the single-thread work; the warp loads columns.
     const uint64_t pol = l2_evict_first_policy();
     int cur_b = -1, n = 0, R = 32, subs = 1, gen = 0;
+    int64_t gen_x0[2] = {-1, -1};  // first chunk of the latest generation of each parity
     uint32_t li = 0;  // items set up by this CTA
     int64_t x = 0;    // chunks issued
     bool failed = false;
@@ -461,32 +479,36 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
       const int64_t t0 = (gid % gpt) * kGroup;
       const int m = (int)imin64(kGroup, tpt - t0);  // items in the group
       if (b != cur_b) {
-        // a new tour: every issued chunk narrowed before its columns go
-        bool ok = true;
-        for (int64_t y = x - kNStage; y < x && ok; ++y) ok = wait_done(y);
+        // a new tour: its table is the one of two generations ago, which
+        // the narrowing warps read at that generation's first chunk (chunks
+        // are narrowed in order, so that chunk done is enough)
+        ++gen;
+        const int64_t y0 = gen_x0[gen & 1];
+        const bool ok = y0 < x - kNStage || wait_done(y0);
         if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
+        gen_x0[gen & 1] = x;
         cur_b = b;
         n = BATCH ? a.n[b] : a.n1;
         const int wqp = ((n + PER - 1) / PER) * PER;
         const StepRec* rec = a.rec + (BATCH ? a.rec_off[b] : 0);
+        uint16_t* cols = cols_of(gen);
         for (int k = lane; k < wqp; k += 32)
           cols[k] = k < n ? (BATCH ? (uint16_t)rec[k].col : a.cols[k]) : (uint16_t)0;
         R = 32;
         while ((uint32_t)R * (uint32_t)n * 4u > kStage) R >>= 1;
         subs = 32 / R;
-        ++gen;
         __syncwarp();
       }
       const int32_t* dem = a.demands + (BATCH ? a.dem_off[b] : 0);
       for (int j = 0; j < m && !failed; ++j) {
         const uint32_t item = li + (uint32_t)j;
-        const uint32_t slot = item % kSlots;
+        const uint32_t slot = item % nslot;
         const int64_t s0 = (t0 + j) * 32;
         bool ok = true;
         if (lane == 0) {
-          // the slot's previous item (item - kSlots) must be finished
-          if (item >= kSlots) {
-            const uint32_t need = item - kSlots + 1;
+          // the slot's previous item (item - nslot) must be finished
+          if (item >= nslot) {
+            const uint32_t need = item - nslot + 1;
             const uint64_t tw = global_ns();
             while (ld_acquire_shared(&slot_free[slot]) < need) {
               if (ld_acquire_shared(&abort_flag) || global_ns() - tw > a.wait_ns) {
@@ -592,6 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
           // value: the range test is unchanged) and is masked off after
           // packing
           const int k = kw + kHalf * j;
+          const uint16_t* cols = cols_of(cached_gen);
           const uint32_t c0 = k < wq ? (uint32_t)cols[PER * k] * 4u : 0u;
           wmask[j] = 0u;
 #pragma unroll
@@ -666,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     uint32_t li = 0;
     if (lane == 0) li = atomicAdd(&next_item, 1u);
     li = __shfl_sync(0xffffffffu, li, 0);
-    const uint32_t slot = li % kSlots;
+    const uint32_t slot = li % nslot;
     // wait until item li is published, or the producers are done
     bool have = ld_acquire_shared(&slot_ready[slot]) > li;
     if (!have) {
@@ -745,7 +768,8 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
 size_t pipe_smem(const PipeArgs& a, bool pred) {
   const int n = a.batched ? kPipeMaxN : a.n1;
   return (size_t)kNStage * kStage + (size_t)(kDp + 1) * kRingBytes + (pred ? (size_t)kDp * kOutBytes : 0) +
-         (a.batched ? 0 : (size_t)n * sizeof(float2)) + ((size_t)n + 8) * sizeof(uint16_t);
+         (a.batched ? 0 : (size_t)n * sizeof(float2)) +
+         (a.batched ? 2 * (size_t)kColsStride : (size_t)n + 8) * sizeof(uint16_t);
 }
 
 template <typename QT, typename PT, bool PRED, bool BATCH>
@@ -754,7 +778,7 @@ int launch_k(const PipeArgs& a, cudaStream_t st) {
   const size_t smem = pipe_smem(a, PRED);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  k<<<pipe_grid(a.S, a.B), kThreads, smem, st>>>(a);
+  k<<<pipe_grid(a.S, a.B, BATCH), kThreads, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -770,18 +794,30 @@ int launch_q(const PipeArgs& a, cudaStream_t st) {
 
 bool pipe_supported(int n, int Q) { return n >= 1 && n <= kPipeMaxN && Q >= 1 && Q <= 32767; }
 
-int pipe_grid(int64_t S, int B) {
-  const int64_t groups = (int64_t)B * ((((S + 31) / 32) + kGroup - 1) / kGroup);
+int pipe_grid(int64_t S, int B, bool batched) {
+  const int g = pipe_group(batched);
+  const int64_t groups = (int64_t)B * ((((S + 31) / 32) + g - 1) / g);
   return (int)imin64(num_sms(), groups < 1 ? 1 : groups);
 }
 
-size_t pipe_ring_bytes(int n_max, int Q, int grid) {
-  return (size_t)grid * kSlots * 32 * (size_t)pipe_row_stride(n_max, Q);
+// slots per CTA: twice a CTA's share of the tiles (a small launch spread over
+// many CTAs needs few), 2 to kSlots
+int pipe_slots(int64_t S, int B, bool batched) {
+  const int grid = pipe_grid(S, B, batched);
+  const int64_t items = (int64_t)B * ((S + 31) / 32);
+  const int64_t per = (items + grid - 1) / grid;
+  return (int)imin64(kSlots, per < 1 ? 2 : 2 * per);
+}
+
+size_t pipe_ring_bytes(int n_max, int Q, int64_t S, int B, bool batched) {
+  return (size_t)pipe_grid(S, B, batched) * (size_t)pipe_slots(S, B, batched) * 32 *
+         (size_t)pipe_row_stride(n_max, Q);
 }
 
 int launch_split_pipe(const PipeArgs& a0, cudaStream_t st) {
   PipeArgs a = a0;
   if (a.wait_ns == 0) a.wait_ns = kWaitLimitNs;
+  a.nslot = pipe_slots(a.S, a.B, a.batched != 0);
   return a.Q <= 254 ? launch_q<uint8_t>(a, st) : launch_q<uint16_t>(a, st);
 }
 

@@ -252,6 +252,25 @@ def test_auto_takes_pipe():
     assert torch.equal(r["cost"], ref["cost"]) and torch.equal(r["pred"], ref["pred"])
 
 
+@pytest.mark.parametrize("S", [1, 31, 33, 100, 4096, 152 * 32 + 1, 152 * 32 * 9 + 77])
+def test_pipe_launch_spread_and_slots(S):
+    """One tour claims its tiles one at a time: a launch has one CTA per tile
+    up to the SM count, and each CTA's ring has twice its share of the tiles
+    (2 to 32 slots); every spread gives the DEQUE kernel's bits."""
+    api = sdp()
+    tour, xy, _, q = _case(40 + S % 97, 137, S, 90, 1, 25)
+    args = (_cuda(tour), 90, _cuda(q))
+    r = api.split_eval(*args, coords=_cuda(xy), preds="u16", algo="pipe")
+    warps, ctas = api.last_launch()
+    tiles = (S + 31) // 32
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert warps == 32 and ctas == min(sms, tiles)
+    ref = api.split_eval(*args, coords=_cuda(xy), preds="u16", algo="deque")
+    torch.cuda.synchronize()
+    assert torch.equal(r["cost"], ref["cost"]) and torch.equal(r["pred"], ref["pred"])
+    assert api.status() & (api.FLAG_DEVICE_CHECK | api.FLAG_FALLBACK) == 0
+
+
 def test_pipe_c2_full_size_sampled():
     """n=500, S=10^6 generated on the device, in the launch configuration the
     benchmark times (PIPE, uint16 predecessors): all scenarios bit-identical
