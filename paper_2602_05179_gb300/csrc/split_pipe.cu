@@ -10,10 +10,9 @@
 // 32 / 40 warps per SM gave 1.04 / 0.84 / 0.72 / 0.71 ms).  Here:
 //
 //   producers (1 issuing + 8 narrowing warps): the issuing warp claims work,
-//     sets up slots and feeds TMA bulk copies (cp.async.bulk, four 16 KB
+//     sets up slots and feeds TMA bulk copies (cp.async.bulk, two 32 KB
 //     stages with full / empty mbarriers, L2 evict-first: every demand is read
-//     once) of R
-//     contiguous int32 demand rows into shared memory; the warps narrow them
+//     once) of R contiguous int32 demand rows into shared memory; the warps narrow them
 //     to uint8 (Q <= 254) or uint16, clamp them to [0, Q+1], permute them
 //     into tour order and write them to the CTA's ring of kSlots tile slots
 //     (32 rows of `stride` bytes each) in global memory.  The ring of all
@@ -72,8 +71,19 @@ constexpr int kNarrow = 8;                     // narrowing warps per CTA (+ one
 constexpr int kNarrowThreads = kNarrow * 32;
 constexpr int kThreads = (kDp + 1 + kNarrow) * 32;  // 1024 threads: 64 registers each
 constexpr int kSlots = 32;                     // tile slots per CTA in the ring, at most
-constexpr uint32_t kStage = 16u * 1024u;       // bytes per producer stage
-constexpr int kNStage = 4;                     // stages (copies in flight per CTA)
+// Producer stages.  A chunk (R whole rows of one tile) costs a fixed round
+// of barrier and bookkeeping work besides its bytes, so two 32 KB stages beat
+// four of 16 KB and eight of 8 KB with the same bytes in flight (copies and
+// narrowing alone, n = 500: 0.60 / 0.82 / 0.97 ms; the batched plan 20.8 ->
+// 19.0 ms with the per-item release below).  A batched plan, which keeps no
+// records and no predecessor stage in shared memory, takes 48 KB stages
+// (whole tiles in one chunk up to n = 384: 18.9 -> 18.5 ms); one tour keeps
+// 32 KB (48 KB measured 1.165 -> 1.210 ms at n = 500), and a third stage
+// helped neither.
+__host__ __device__ constexpr uint32_t pipe_stage_bytes(bool batched) {
+  return (batched ? 48u : 32u) * 1024u;
+}
+constexpr int kNStage = 2;                     // stages (copies in flight per CTA)
 // tiles per claimed group: one tour takes them one at a time, so that the
 // CTAs' tile counts differ by one at most and every DP warp of the launch
 // gets within a tile of the same share (groups of 16 left 208 tiles on most
@@ -110,8 +120,8 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel_shared(uint32_t* p, uint32_
                : "=r"(old) : "r"(smem_u32(p)), "r"(v) : "memory");
   return old;
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+__device__ __forceinline__ void mbar_arrive_relaxed(uint32_t bar) {
+  asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 // Wait for phase `parity` of an mbarrier, giving up on the abort flag or
 // after limit_ns; false if it did not complete.
@@ -408,6 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   const int Q = a.Q;
   const int64_t S = a.S;
   // shared: stages | DP rings | predecessor stages | (one tour) records | columns
+  constexpr uint32_t kStage = pipe_stage_bytes(BATCH);  // bytes per producer stage
   const uint32_t rings = (smem_u32(smem) + kNStage * kStage + kRingBytes - 1) & ~(kRingBytes - 1);
   const size_t rings_off = rings - smem_u32(smem);  // (the smem size holds kRingBytes of slack)
   uint32_t* ostage = reinterpret_cast<uint32_t*>(smem + rings_off + (size_t)kDp * kRingBytes);
@@ -462,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     // narrowed.  Lane 0 does the single-thread work; the warp loads columns.
     const uint64_t pol = l2_evict_first_policy();
     int cur_b = -1, n = 0, R = 32, subs = 1, gen = 0;
-    int64_t gen_x0[2] = {-1, -1};  // first chunk of the latest generation of each parity
+    int64_t gen_x0e = -1, gen_x0o = -1;  // first chunk of the latest even / odd generation
     uint32_t li = 0;  // items set up by this CTA
     int64_t x = 0;    // chunks issued
     bool failed = false;
@@ -483,10 +494,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
         // the narrowing warps read at that generation's first chunk (chunks
         // are narrowed in order, so that chunk done is enough)
         ++gen;
-        const int64_t y0 = gen_x0[gen & 1];
+        const int64_t y0 = (gen & 1) ? gen_x0o : gen_x0e;
         const bool ok = y0 < x - kNStage || wait_done(y0);
         if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
-        gen_x0[gen & 1] = x;
+        if (gen & 1) gen_x0o = x; else gen_x0e = x;
         cur_b = b;
         n = BATCH ? a.n[b] : a.n1;
         const int wqp = ((n + PER - 1) / PER) * PER;
@@ -522,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
           slot_b[slot] = b;
           slot_s0[slot] = s0;
           item_cnt[slot] = 0u;
-          item_need[slot] = (uint32_t)(kNarrow * subs);
+          item_need[slot] = (uint32_t)kNarrow;
         }
         if (!__shfl_sync(0xffffffffu, (int)ok, 0)) { failed = true; break; }
         for (int q = 0; q < subs; ++q) {
@@ -667,11 +678,17 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
       }
       __syncwarp();
       if (lane == 0) {
+        // The stage is free once every lane's shared reads of it are done:
+        // their values fed the ring stores above, and the warp has
+        // converged, so a relaxed arrival (which waits for no store) does.
+        // The item is counted once per warp, after its last chunk, with a
+        // release that covers the warp's stores of every chunk of the item.
         // (a.stall: fault injection for tests -- nothing is published, and
         // the DP warps' waits run out after a.wait_ns)
-        if (atom_add_acq_rel_shared(&item_cnt[slot], 1u) + 1u == item_need[slot] && !a.stall)
+        mbar_arrive_relaxed(empty_of(x));
+        if (mt.rbase + R >= 32 &&
+            atom_add_acq_rel_shared(&item_cnt[slot], 1u) + 1u == item_need[slot] && !a.stall)
           st_release_shared(&slot_ready[slot], mt.item + 1u);
-        mbar_arrive(empty_of(x));
       }
     }
     if (mn_all < 0) atomicOr(a.status, SDP_FLAG_NEG_INPUT);
@@ -767,7 +784,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
 
 size_t pipe_smem(const PipeArgs& a, bool pred) {
   const int n = a.batched ? kPipeMaxN : a.n1;
-  return (size_t)kNStage * kStage + (size_t)(kDp + 1) * kRingBytes + (pred ? (size_t)kDp * kOutBytes : 0) +
+  return (size_t)kNStage * pipe_stage_bytes(a.batched != 0) + (size_t)(kDp + 1) * kRingBytes + (pred ? (size_t)kDp * kOutBytes : 0) +
          (a.batched ? 0 : (size_t)n * sizeof(float2)) +
          (a.batched ? 2 * (size_t)kColsStride : (size_t)n + 8) * sizeof(uint16_t);
 }
