@@ -884,8 +884,9 @@ int sdp_split_fleet_eval(const sdp_split_args* a, int32_t max_routes, int32_t* n
       e = launch_split_fleet(f, w.cfg, st);
       prof_end(st);
       if (e) return cuda_fail((cudaError_t)e, "split_fleet launch");
-      e = launch_split_fleet_plain(f, st);  // the flagged scenarios, if any
-      if (e) return cuda_fail((cudaError_t)e, "split_fleet_plain launch");
+      // the flagged scenarios, if any
+      e = fleet_rescue_supported(a->n) ? launch_split_fleet_rescue(f, st) : launch_split_fleet_plain(f, st);
+      if (e) return cuda_fail((cudaError_t)e, "split_fleet recompute launch");
     }
   }
   if (a->mean_out) {

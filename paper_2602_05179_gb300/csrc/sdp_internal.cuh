@@ -337,6 +337,9 @@ FleetConfig fleet_config(int n, int K, int64_t S);
 size_t fleet_dscratch_elems(int n, int K, const FleetConfig& c);
 int launch_split_fleet(const SplitFleetArgs& a, const FleetConfig& c, cudaStream_t st);
 int launch_split_fleet_plain(const SplitFleetArgs& a, cudaStream_t st);
+// the flagged scenarios (fb_list), one warp each; the plain kernel's bits
+bool fleet_rescue_supported(int n);
+int launch_split_fleet_rescue(const SplitFleetArgs& a, cudaStream_t st);
 
 // arc counting (capacity-feasible (p,i) pairs)
 void launch_count_arcs(int n, int Q, int64_t S, const StepRec* rec,

@@ -24,10 +24,17 @@
 // empty window reads +inf (a demand above Q at position i empties it, and
 // the first such position makes every later J infinite).  With route output, i - p of every
 // (i, k) goes to the warp's scratch row [i][k] and lane 0 walks the optimal
-// split back.  A deque that outgrows its ring flags the scenario;
-// split_fleet_plain_kernel (one thread per scenario, every feasible p of
-// every layer, the same FP32 operations) recomputes it.
+// split back.  A deque that outgrows its ring flags the scenario and
+// split_fleet_rescue_kernel recomputes it, one warp per scenario and the same
+// FP32 operations as split_fleet_plain_kernel (one thread per scenario, every
+// feasible p of every layer: PLAIN, and the recomputation for n too long for
+// the rescue's shared memory).  Rings of 16 entries, with 24 warps per CTA,
+// overflow on some scenarios of the n = 500, K = 42 workload but run it in
+// 5.4 ms of kernel where 32 entries and 16 warps took 9.0 ms; the one-thread
+// recomputation of the overflowing scenarios alone took 39 ms.
 #include <math_constants.h>
+
+#include <algorithm>
 
 #include "sdp_internal.cuh"
 
@@ -35,9 +42,9 @@ namespace sdp {
 
 namespace {
 
-constexpr int kFRing = 32;                          // deque entries per layer and lane
+constexpr int kFRing = 16;                          // deque entries per layer and lane
 constexpr uint32_t kFRingBytes = kFRing * 256u;     // one layer's ring for 32 lanes
-constexpr int kFMaxWarps = 16;                      // warps per CTA at most (as shared memory allows)
+constexpr int kFMaxWarps = 24;                      // warps per CTA at most (as shared memory allows)
 constexpr int kFAhead = 8;                          // demands loaded ahead
 
 __device__ __forceinline__ float flds(uint32_t a) {
@@ -327,6 +334,109 @@ __global__ void __launch_bounds__(256) split_fleet_plain_kernel(SplitFleetArgs a
   }
 }
 
+// Recomputation of the flagged scenarios, one warp per scenario.  Layer k
+// depends only on layer k - 1, so within a layer every position is
+// independent: lane l takes positions i = 1 + l, 33 + l, ... and scans its
+// window p = i - 1, i - 2, ... while the route load (from prefix loads in
+// shared memory) stays within Q.  K_{k-1} and K_k sit in shared memory beside
+// the prefix loads; the FP32 operations, the order of p and the tie rules are
+// split_fleet_plain_kernel's, so the results are its bits, and the route
+// deltas go to the same per-slot scratch for the same backtrack.
+constexpr int kFRescueWarps = 8;
+__host__ __device__ inline size_t fleet_rescue_per_warp(int n) { return (size_t)3 * 4 * ((size_t)n + 1); }
+
+__global__ void __launch_bounds__(kFRescueWarps * 32) split_fleet_rescue_kernel(SplitFleetArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int n = a.n, Q = a.Q, K = a.K;
+  float* Kp = reinterpret_cast<float*>(smem + (size_t)wib * fleet_rescue_per_warp(n));
+  float* Kc = Kp + (n + 1);
+  int32_t* L = reinterpret_cast<int32_t*>(Kc + (n + 1));
+  const int64_t slot = (int64_t)blockIdx.x * wpb + wib;  // < nslots (the launch sees to it)
+  uint16_t* P = a.pscratch ? a.pscratch + slot * (int64_t)K * n : nullptr;
+  const int64_t count = (int64_t)*a.fb_count;
+  const int64_t nw = (int64_t)gridDim.x * wpb;
+  for (int64_t it = slot; it < count; it += nw) {
+    const int64_t s = (int64_t)a.fb_list[it];
+    const int32_t* q = a.demands + s * n;
+    __syncwarp();  // the previous scenario's reads are done
+    int carry = 0;
+    bool over = false;
+    if (lane == 0) L[0] = 0;
+    for (int i0 = 1; i0 <= n; i0 += 32) {
+      const int i = i0 + lane;
+      int v = 0;
+      if (i <= n) {
+        const int raw = __ldg(q + __ldg(&a.rec[i - 1].col));
+        over |= raw > Q;
+        v = max(raw, 0);
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += t;
+      }
+      if (i <= n) L[i] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    const bool infeasible0 = __any_sync(0xffffffffu, over);
+    for (int i = lane; i <= n; i += 32) Kp[i] = i == 0 ? 0.f : CUDART_INF_F;
+    __syncwarp();
+    float* kp = Kp;
+    float* kc = Kc;
+    float best = CUDART_INF_F;
+    int bk = 0;
+    for (int k = 1; k <= K && !infeasible0; ++k) {
+      if (lane == 0) kc[0] = CUDART_INF_F;
+      for (int i = 1 + lane; i <= n; i += 32) {
+        const int Li = L[i];
+        float bv = CUDART_INF_F;
+        int bp = -1;
+        for (int p = i - 1; p >= 0; --p) {
+          if (Li - L[p] > Q) break;
+          const float psi = __fadd_rn(kp[p], __ldg(&a.rec[p].a));
+          if (psi <= bv) {  // p runs downwards: the smallest p on ties
+            bv = psi;
+            bp = p;
+          }
+        }
+        kc[i] = bp < 0 ? CUDART_INF_F : __fadd_rn(bv, __ldg(&a.rec[i - 1].ce));
+        if (P) P[(int64_t)(k - 1) * n + (i - 1)] = (uint16_t)(bp < 0 ? 0 : i - bp);
+      }
+      __syncwarp();  // layer k complete before it is read
+      if (kc[n] < best) {  // the fewest routes on ties
+        best = kc[n];
+        bk = k;
+      }
+      float* t = kp;
+      kp = kc;
+      kc = t;
+    }
+    const bool infeasible = infeasible0 || bk == 0 || best == CUDART_INF_F;
+    if (lane == 0) {
+      a.cost[s] = infeasible ? CUDART_INF_F : (float)((double)best + *a.Dn);
+      if (a.nroutes) a.nroutes[s] = infeasible ? 0 : bk;
+      if (infeasible) atomicOr(a.status, SDP_FLAG_INFEASIBLE);
+    }
+    if (a.route) {
+      __threadfence_block();  // the route deltas of every lane, for lane 0's backtrack
+      __syncwarp();
+      uint8_t* ro = a.route + s * n;
+      if (infeasible) {
+        for (int m = lane; m < n; m += 32) ro[m] = 0xFFu;
+      } else if (lane == 0) {
+        int i = n, k = bk;
+        while (k > 0 && i > 0) {
+          const int p = max(0, i - (int)P[(int64_t)(k - 1) * n + (i - 1)]);
+          for (int m = p; m < i; ++m) ro[m] = (uint8_t)(k - 1);
+          i = p;
+          --k;
+        }
+      }
+    }
+  }
+}
+
 size_t fleet_head(int n) { return (((size_t)n * 8 + (size_t)n * 2) + 255) & ~(size_t)255; }
 size_t fleet_per_warp(int ks) { return (size_t)ks * kFRingBytes + 256 * 4; }
 
@@ -370,6 +480,24 @@ int launch_split_fleet(const SplitFleetArgs& a, const FleetConfig& c, cudaStream
                    : launch_fleet_k<1, false>(a, c.warps, c.grid, st);
   return a.route ? launch_fleet_k<2, true>(a, c.warps, c.grid, st)
                  : launch_fleet_k<2, false>(a, c.warps, c.grid, st);
+}
+
+bool fleet_rescue_supported(int n) { return fleet_rescue_per_warp(n) <= 200u * 1024u; }
+
+int launch_split_fleet_rescue(const SplitFleetArgs& a, cudaStream_t st) {
+  const size_t per = fleet_rescue_per_warp(a.n);
+  int wpb = (int)std::min<size_t>(kFRescueWarps, std::max<size_t>(1, (96u * 1024u) / per));
+  if (wpb > a.nslots) wpb = (int)a.nslots;
+  const size_t smem = (size_t)wpb * per;
+  // one scratch slot per warp: wpb * grid <= nslots
+  const int grid = (int)std::max<int64_t>(1, a.nslots / wpb);
+  auto k = split_fleet_rescue_kernel;
+  if (smem > 48u * 1024u) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  k<<<grid, wpb * 32, smem, st>>>(a);
+  return (int)cudaGetLastError();
 }
 
 int launch_split_fleet_plain(const SplitFleetArgs& a, cudaStream_t st) {
