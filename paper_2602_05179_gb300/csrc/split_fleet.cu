@@ -337,21 +337,32 @@ __global__ void __launch_bounds__(256) split_fleet_plain_kernel(SplitFleetArgs a
 // Recomputation of the flagged scenarios, one warp per scenario.  Layer k
 // depends only on layer k - 1, so within a layer every position is
 // independent: lane l takes positions i = 1 + l, 33 + l, ... and scans its
-// window p = i - 1, i - 2, ... while the route load (from prefix loads in
-// shared memory) stays within Q.  K_{k-1} and K_k sit in shared memory beside
-// the prefix loads; the FP32 operations, the order of p and the tie rules are
-// split_fleet_plain_kernel's, so the results are its bits, and the route
-// deltas go to the same per-slot scratch for the same backtrack.
+// window p = i - 1 down to pmin(i), the smallest p whose route p+1..i fits Q
+// (the same for every layer: found once per scenario by a binary search of
+// the prefix loads).  K_{k-1} and K_k sit in shared memory, and the tour's
+// a_{p+1} and ce_i once per CTA; the FP32 operations, the order of p and the
+// tie rules are split_fleet_plain_kernel's, so the results are its bits, and
+// the route deltas go to the same per-slot scratch for the same backtrack.
 constexpr int kFRescueWarps = 8;
-__host__ __device__ inline size_t fleet_rescue_per_warp(int n) { return (size_t)3 * 4 * ((size_t)n + 1); }
+// per warp: K_{k-1}, K_k, prefix loads L and window starts pmin, [n+1] each
+__host__ __device__ inline size_t fleet_rescue_per_warp(int n) { return (size_t)4 * 4 * ((size_t)n + 1); }
+__host__ __device__ inline size_t fleet_rescue_head(int n) { return ((size_t)8 * (size_t)n + 15) & ~(size_t)15; }
 
 __global__ void __launch_bounds__(kFRescueWarps * 32) split_fleet_rescue_kernel(SplitFleetArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int n = a.n, Q = a.Q, K = a.K;
-  float* Kp = reinterpret_cast<float*>(smem + (size_t)wib * fleet_rescue_per_warp(n));
+  float* as = reinterpret_cast<float*>(smem);  // a_{p+1} at [p], ce_i at [n + i - 1]
+  float* ces = as + n;
+  float* Kp = reinterpret_cast<float*>(smem + fleet_rescue_head(n) + (size_t)wib * fleet_rescue_per_warp(n));
   float* Kc = Kp + (n + 1);
   int32_t* L = reinterpret_cast<int32_t*>(Kc + (n + 1));
+  int32_t* pmin = L + (n + 1);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    as[k] = a.rec[k].a;
+    ces[k] = a.rec[k].ce;
+  }
+  __syncthreads();
   const int64_t slot = (int64_t)blockIdx.x * wpb + wib;  // < nslots (the launch sees to it)
   uint16_t* P = a.pscratch ? a.pscratch + slot * (int64_t)K * n : nullptr;
   const int64_t count = (int64_t)*a.fb_count;
@@ -380,6 +391,19 @@ __global__ void __launch_bounds__(kFRescueWarps * 32) split_fleet_rescue_kernel(
       carry += __shfl_sync(0xffffffffu, v, 31);
     }
     const bool infeasible0 = __any_sync(0xffffffffu, over);
+    __syncwarp();
+    // pmin(i): L is non-decreasing, so the feasible p < i form [pmin, i - 1]
+    // (pmin = i: none; only with a demand above Q, which makes the scenario
+    // infeasible anyway)
+    for (int i = 1 + lane; i <= n; i += 32) {
+      const int Li = L[i];
+      int lo = 0, hi = i;  // smallest p in [0, i) with Li - L[p] <= Q, else i
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (Li - L[mid] <= Q) hi = mid; else lo = mid + 1;
+      }
+      pmin[i] = lo;
+    }
     for (int i = lane; i <= n; i += 32) Kp[i] = i == 0 ? 0.f : CUDART_INF_F;
     __syncwarp();
     float* kp = Kp;
@@ -389,18 +413,18 @@ __global__ void __launch_bounds__(kFRescueWarps * 32) split_fleet_rescue_kernel(
     for (int k = 1; k <= K && !infeasible0; ++k) {
       if (lane == 0) kc[0] = CUDART_INF_F;
       for (int i = 1 + lane; i <= n; i += 32) {
-        const int Li = L[i];
+        const int pm = pmin[i];
         float bv = CUDART_INF_F;
         int bp = -1;
-        for (int p = i - 1; p >= 0; --p) {
-          if (Li - L[p] > Q) break;
-          const float psi = __fadd_rn(kp[p], __ldg(&a.rec[p].a));
+#pragma unroll 4
+        for (int p = i - 1; p >= pm; --p) {
+          const float psi = __fadd_rn(kp[p], as[p]);
           if (psi <= bv) {  // p runs downwards: the smallest p on ties
             bv = psi;
             bp = p;
           }
         }
-        kc[i] = bp < 0 ? CUDART_INF_F : __fadd_rn(bv, __ldg(&a.rec[i - 1].ce));
+        kc[i] = bp < 0 ? CUDART_INF_F : __fadd_rn(bv, ces[i - 1]);
         if (P) P[(int64_t)(k - 1) * n + (i - 1)] = (uint16_t)(bp < 0 ? 0 : i - bp);
       }
       __syncwarp();  // layer k complete before it is read
@@ -419,8 +443,7 @@ __global__ void __launch_bounds__(kFRescueWarps * 32) split_fleet_rescue_kernel(
       if (infeasible) atomicOr(a.status, SDP_FLAG_INFEASIBLE);
     }
     if (a.route) {
-      __threadfence_block();  // the route deltas of every lane, for lane 0's backtrack
-      __syncwarp();
+      __syncwarp();  // the route deltas of every lane, for lane 0's backtrack
       uint8_t* ro = a.route + s * n;
       if (infeasible) {
         for (int m = lane; m < n; m += 32) ro[m] = 0xFFu;
@@ -482,13 +505,13 @@ int launch_split_fleet(const SplitFleetArgs& a, const FleetConfig& c, cudaStream
                  : launch_fleet_k<2, false>(a, c.warps, c.grid, st);
 }
 
-bool fleet_rescue_supported(int n) { return fleet_rescue_per_warp(n) <= 200u * 1024u; }
+bool fleet_rescue_supported(int n) { return fleet_rescue_head(n) + fleet_rescue_per_warp(n) <= 200u * 1024u; }
 
 int launch_split_fleet_rescue(const SplitFleetArgs& a, cudaStream_t st) {
   const size_t per = fleet_rescue_per_warp(a.n);
   int wpb = (int)std::min<size_t>(kFRescueWarps, std::max<size_t>(1, (96u * 1024u) / per));
   if (wpb > a.nslots) wpb = (int)a.nslots;
-  const size_t smem = (size_t)wpb * per;
+  const size_t smem = fleet_rescue_head(a.n) + (size_t)wpb * per;
   // one scratch slot per warp: wpb * grid <= nslots
   const int grid = (int)std::max<int64_t>(1, a.nslots / wpb);
   auto k = split_fleet_rescue_kernel;
