@@ -643,9 +643,10 @@ def op_adjoint(c, out):
 
 def op_soft(c, out):
     """Soft-capacity Split: the bench workload (n=500, Q=200, S=10^6,
-    U{1..30}) with 10 per unit of route load above Q; DEQUE (hard window in
-    the deque, expired entries as one running minimum) against PLAIN (every
-    pair (p, i) relaxed), the latter on the first 65,536 scenarios."""
+    U{1..30}) with 10 per unit of route load above Q; the pipelined kernel
+    (AUTO: hard window in the deque, expired entries as one running minimum),
+    beside the DEQUE soft kernel (the same recursion and bits) and PLAIN
+    (every pair (p, i) relaxed), the latter on the first 65,536 scenarios."""
     import torch
     spec = c.wl.SPLIT_C2
     beta = 10.0
@@ -653,10 +654,15 @@ def op_soft(c, out):
     t = torch.from_numpy(tour).to(c.dev)
     cc = torch.from_numpy(xy).to(c.dev)
     q = c.wl.split_demands_device(spec, c.dev)
-    fn = lambda: c.api.split_eval(t, spec.Q, q, coords=cc, preds="u16", algo="deque",
+    fn = lambda: c.api.split_eval(t, spec.Q, q, coords=cc, preds="u16", algo="pipe",
                                   overload_penalty=beta)
     ms, kms = _timed(fn, c.steps or 20)
     r = fn()
+    fnd = lambda: c.api.split_eval(t, spec.Q, q, coords=cc, preds="u16", algo="deque",
+                                   overload_penalty=beta)
+    dms, dkms = _timed(fnd, c.steps or 20)
+    rd = fnd()
+    same = bool(torch.equal(r["cost"], rd["cost"]) and torch.equal(r["pred"], rd["pred"]))
     n, S = spec.n, spec.S
     byts = S * n * 4 + S * 4 + S * n * 2
     sub = 65536
@@ -665,8 +671,10 @@ def op_soft(c, out):
                                    overload_penalty=beta)
     pms, _ = _timed(fnp, 2, warmup=1, events=False)
     line = {"value": S / (ms / 1e3), "unit": "scenarios/s", "ms_per_step": ms,
-            "kernel_ms": kms, "kernel": "split_tmem_soft_kernel",
+            "kernel_ms": kms, "kernel": "split_pipe_kernel (soft)",
             "roofline": c.hbm_roof(byts, kms),
+            "vs_deque": {"kernel": "split_tmem_soft_kernel", "ms_per_step": dms, "kernel_ms": dkms,
+                         "speedup": dkms / kms, "bit_identical": same},
             "vs_plain": {"plain_ms_per_65536": pms, "plain_scenarios_per_s": sub / (pms / 1e3),
                          "speedup": (S / (ms / 1e3)) / (sub / (pms / 1e3))}}
     if c.checks:

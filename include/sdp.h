@@ -95,8 +95,9 @@ extern "C" {
                              tile slots that stays in L2 (no pre-pass over
                              HBM), with 23 DP warps per SM; predecessors
                              leave through a shared-memory transpose as row
-                             segments.  Needs hard capacity, 1 <= n <= 1024,
-                             Q <= 32767 and 16-byte aligned demands; the
+                             segments.  Hard or soft capacity; needs
+                             1 <= n <= 1024, Q <= 32767 and 16-byte aligned
+                             demands; the
                              workspace grows by about
                              SMs * 32 * 32 * ceil32(n * qb) bytes (qb = 1 for
                              Q <= 254, else 2): 78 MB at n = 500 on 152 SMs */
@@ -193,8 +194,11 @@ typedef struct sdp_split_args {
  * (tensor-memory staging, rows of at most 512 bytes) keeps the hard window in
  * its deque and the entries that left it as one running minimum of
  * psi(p) - beta L(p) (with equal slopes, an expired entry's penalised cost
- * is that value plus beta (L(i) - Q)), O(1) per position.  AUTO takes DEQUE
- * when it applies, else PLAIN; STREAM, plans and the adjoint take HARD only
+ * is that value plus beta (L(i) - Q)), O(1) per position; PIPE runs the same
+ * recursion with the same FP32 operations (the DEQUE soft kernel's bits) and
+ * sends a scenario whose prefix load reaches 2^16, or that holds a demand
+ * above 255 (Q <= 254) or 32767, to PLAIN.  AUTO takes PIPE where it applies,
+ * else DEQUE, else PLAIN; STREAM, plans and the adjoint take HARD only
  * (SDP_ERR_UNSUPPORTED). */
 #define SDP_CAPACITY_HARD 0
 #define SDP_CAPACITY_SOFT 1

@@ -260,7 +260,7 @@ int auto_algo_no_pipe(const sdp_split_args* a) {
 }
 
 bool pipe_ok(const sdp_split_args* a) {
-  if (a->capacity_mode == SDP_CAPACITY_SOFT || !pipe_supported(a->n, a->Q)) return false;
+  if (!pipe_supported(a->n, a->Q)) return false;
   if (a->n > 0 && a->S > 0 && !is_host_ptr(a->demands) &&
       (reinterpret_cast<uintptr_t>(a->demands) & 15) != 0)
     return false;
@@ -414,8 +414,8 @@ int check_split(const sdp_split_args* a, bool need_cost) {
   if (a->capacity_mode == SDP_CAPACITY_SOFT) {
     if (!(a->overload_penalty >= 0.f) || a->overload_penalty == INFINITY)
       return fail(SDP_ERR_INVALID_ARG, "overload_penalty must be finite and >= 0");
-    if (a->algo == SDP_ALGO_STREAM || a->algo == SDP_ALGO_PIPE)
-      return fail(SDP_ERR_UNSUPPORTED, "soft capacity runs on PLAIN or DEQUE");
+    if (a->algo == SDP_ALGO_STREAM)
+      return fail(SDP_ERR_UNSUPPORTED, "soft capacity runs on PLAIN, DEQUE or PIPE");
     if (a->algo == SDP_ALGO_DEQUE && !soft_deque_ok(a))
       return fail(SDP_ERR_UNSUPPORTED,
                   "soft-capacity DEQUE needs rows of at most 512 bytes and warps_per_cta = 0");
@@ -494,6 +494,7 @@ int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
     pa.demands = a->demands; pa.cost = cost; pa.pred = pred; pa.pred_dtype = a->pred_dtype;
     pa.qt = w.qt; pa.stride = pipe_row_stride(a->n, a->Q); pa.counter = w.counter;
     pa.fb_count = w.fb_count; pa.fb_list1 = w.fb_list; pa.status = status;
+    pa.soft = a->capacity_mode == SDP_CAPACITY_SOFT ? 1 : 0; pa.beta = a->overload_penalty;
     const uint64_t stall = fault_stall_ns();
     pa.wait_ns = stall ? stall : kWaitLimitNs;
     pa.stall = stall ? 1 : 0;

@@ -98,6 +98,8 @@ constexpr uint32_t kRingBytes = (uint32_t)kRing * 256u;  // 32 lanes x 8 bytes p
 constexpr uint32_t kRingMask = (uint32_t)(kRing - 1) << 8;
 constexpr uint32_t kOutBytes = 32u * 32u;      // predecessor stage per warp: 32 rows x 32 bytes
 constexpr int kColsStride = kPipeMaxN + 8;     // uint16 entries per column table
+template <typename QT>
+__host__ __device__ constexpr int soft_max() { return sizeof(QT) == 1 ? 255 : 32767; }
 constexpr int kCheckEvery = 2;                 // steps between ring tests (lean step)
 constexpr uint32_t kMaxAtCheck = 14u;          // entries allowed at a test (+2 pushes <= 16)
 static_assert(kMaxAtCheck + kCheckEvery <= (uint32_t)kRing && 16 % kCheckEvery == 0,
@@ -145,6 +147,12 @@ struct Lane {
   uint32_t fent;        // front entry: L(p) << 16 | p
   float K, fpsi, bpsi;
   bool ovf;             // the deque outgrew the ring: recompute the scenario
+  // soft capacity: the best expired entry, c = psi(p) - beta L(p), and its
+  // entry; won: the expired candidate is position i's minimum; ovfL: the
+  // prefix load passed 2^16, where the entries' L(p) no longer hold it
+  float cmin;
+  uint32_t cent;
+  bool won, ovfL;
 
   // rings start on 4 KB and a lane's entry is its 8 bytes of a 256-byte
   // slot, so the slot offset and the lane base share no bits: one LOP3
@@ -157,6 +165,9 @@ struct Lane {
     fpsi = CUDART_INF_F;  // the first step restarts the deque at p = 0
     bpsi = -CUDART_INF_F;
     ovf = false;
+    cmin = CUDART_INF_F;
+    cent = 0u;
+    won = ovfL = false;
   }
   // position i: demand qh = q_i << 16 and record (a_i, ce_i); no demand
   // above Q in the tile
@@ -195,6 +206,102 @@ struct Lane {
       fpsi = __uint_as_float(e.x);
       fent = e.y;
     }
+  }
+  // Soft capacity (a route pays beta per unit of load above Q; every split
+  // allowed).  An entry leaving from the front joins the expired set, whose
+  // best candidate at position i is cmin + beta (L(i) - Q), cmin the least
+  // psi(p) - beta L(p) (entries expire in increasing p: "<" keeps the
+  // smallest p); an entry leaving from the back is dominated in both regimes.
+  // K(i) = min(window minimum, that candidate) + ce_i, ties to the expired
+  // entry (the smaller p): the FP32 operations of the DEQUE soft kernel.
+  __device__ __forceinline__ void soft_best(float ce, int Q, float beta) {
+    float best = fpsi;
+    won = false;
+    if (cmin < CUDART_INF_F) {
+      const float c2 = __fadd_rn(__fmul_rn(beta, (float)((int)(Lent >> 16) - Q)), cmin);
+      if (c2 <= best) {
+        best = c2;
+        won = true;
+      }
+    }
+    K = __fadd_rn(best, ce);
+  }
+  __device__ __forceinline__ void expire_front(float beta) {
+    const float c = __fsub_rn(fpsi, __fmul_rn(beta, (float)(fent >> 16)));
+    if (c < cmin) {
+      cmin = c;
+      cent = fent;
+    }
+  }
+  // lean form: no demand above Q in the tile, so the newest entry stays
+  __device__ __forceinline__ void step_soft(uint32_t qh, float a, float ce, uint32_t Qc, int Q,
+                                            float beta) {
+    const float psi = __fadd_rn(K, a);
+    const uint32_t ent = Lent;
+    Lent += qh + 1u;
+    ovfL |= Lent < ent;
+    if (psi < fpsi) {
+      tail = head;
+      fpsi = psi;
+      fent = ent;
+      bpsi = -CUDART_INF_F;
+    }
+    while (bpsi > psi) {
+      tail -= 256u;
+      bpsi = lds_f32(at(tail - 256u));
+    }
+    sts_u2(at(tail), __float_as_uint(psi), ent);
+    tail += 256u;
+    bpsi = psi;
+    while (Lent - fent > Qc) {
+      expire_front(beta);
+      head += 256u;
+      const uint2 e = lds_u2(at(head));
+      fpsi = __uint_as_float(e.x);
+      fent = e.y;
+    }
+    soft_best(ce, Q, beta);
+  }
+  // checked form (Lent = L(i-1) << 16): a demand above Q expires the newest
+  // entry too, and an emptied window reads +inf
+  __device__ __forceinline__ void step_soft_chk(int i, uint32_t qh, float a, float ce, uint32_t Qc,
+                                                int Q, float beta) {
+    const float psi = __fadd_rn(K, a);
+    const uint32_t ent = Lent | (uint32_t)(i - 1);
+    while (bpsi > psi) {
+      tail -= 256u;
+      bpsi = tail == head ? -CUDART_INF_F : lds_f32(at(tail - 256u));
+    }
+    if (tail == head) {
+      fpsi = psi;
+      fent = ent;
+    }
+    if (tail - head >= kRingBytes) {  // full: flagged, restart at the new entry
+      ovf = true;
+      head = tail;
+      fpsi = psi;
+      fent = ent;
+    }
+    sts_u2(at(tail), __float_as_uint(psi), ent);
+    tail += 256u;
+    bpsi = psi;
+    const uint32_t Lp = Lent;
+    Lent += qh;
+    ovfL |= Lent < Lp;
+    while (head != tail && ((Lent | 0xFFFFu) - fent) > Qc) {
+      expire_front(beta);
+      head += 256u;
+      if (head != tail) {
+        const uint2 e = lds_u2(at(head));
+        fpsi = __uint_as_float(e.x);
+        fent = e.y;
+      }
+    }
+    if (head == tail) {
+      fpsi = CUDART_INF_F;
+      bpsi = -CUDART_INF_F;
+    }
+    soft_best(ce, Q, beta);
   }
   // position i of a tile with a demand above Q (Lent = L(i-1) << 16 here)
   __device__ __forceinline__ void step_chk(int i, uint32_t qh, float a, float ce, uint32_t Qc,
@@ -334,10 +441,11 @@ struct PredStage {
 };
 
 // One 32-scenario tile: lane l runs scenario s0 + l over positions 1..n from
-// its tour-ordered row.  CHECK: the tile has a demand above Q.
-template <typename QT, typename PT, bool PRED, bool CHECK, typename REC>
-__device__ __forceinline__ void pipe_tile(int n, int Q, const unsigned char* qrow, uint32_t ring,
-                                          const REC rec, int lane, PredStage<PT>& ps,
+// its tour-ordered row.  CHECK: the tile has a demand above Q.  SOFT: soft
+// capacity with penalty beta per unit of route load above Q.
+template <typename QT, typename PT, bool PRED, bool CHECK, bool SOFT, typename REC>
+__device__ __forceinline__ void pipe_tile(int n, int Q, float beta, const unsigned char* qrow,
+                                          uint32_t ring, const REC rec, int lane, PredStage<PT>& ps,
                                           float* K_out, uint32_t* first_inf_out, bool* bad) {
   constexpr int E = 16;                    // positions per block
   constexpr int V = (int)sizeof(QT);       // 16-byte vectors per block
@@ -353,8 +461,25 @@ __device__ __forceinline__ void pipe_tile(int n, int Q, const unsigned char* qro
 #pragma unroll
   for (int v = 0; v < V; ++v) c[v] = ld_cg_v4(src + v);
   auto pred_of = [&](int i) -> uint32_t {
-    if (CHECK && (uint32_t)i >= first_inf) return 0xFFFFFFFFu;
-    return sizeof(PT) == 2 ? st.fent : (st.fent & 0xFFFFu);
+    if (!SOFT && CHECK && (uint32_t)i >= first_inf) return 0xFFFFFFFFu;
+    const uint32_t e = (SOFT && st.won) ? st.cent : st.fent;
+    return sizeof(PT) == 2 ? e : (e & 0xFFFFu);
+  };
+  // position i; test: the lean step's ring test is due
+  auto do_step = [&](int i, uint32_t qh, float2 r, bool test) {
+    if (SOFT) {
+      if (CHECK) {
+        st.step_soft_chk(i, qh, r.x, r.y, Qc, Q, beta);
+      } else {
+        st.step_soft(qh, r.x, r.y, Qc, Q, beta);
+        if (test) st.check();
+      }
+    } else if (CHECK) {
+      st.step_chk(i, qh, r.x, r.y, Qc, Qh, n, first_inf);
+    } else {
+      st.step(qh, r.x, r.y, Qc);
+      if (test) st.check();
+    }
   };
   for (int b = 0; b < nblk; ++b) {
     const int bn = min(b + 1, last);
@@ -366,12 +491,7 @@ __device__ __forceinline__ void pipe_tile(int n, int Q, const unsigned char* qro
       const int i = b * E + u + 1;
       const float2 r = rec(i - 1);
       const uint32_t qh = q_at<QT>(c, u);
-      if (CHECK) {
-        st.step_chk(i, qh, r.x, r.y, Qc, Qh, n, first_inf);
-      } else {
-        st.step(qh, r.x, r.y, Qc);
-        if (u % kCheckEvery == kCheckEvery - 1) st.check();
-      }
+      do_step(i, qh, r, u % kCheckEvery == kCheckEvery - 1);
       if (PRED) {
         ps.put(u % W, pred_of(i));
         if (u % W == W - 1) ps.flush(i - W + 1, W);
@@ -386,12 +506,7 @@ __device__ __forceinline__ void pipe_tile(int n, int Q, const unsigned char* qro
     const int u = i - i1;
     const float2 r = rec(i - 1);
     const uint32_t qh = q_at<QT>(c, u);
-    if (CHECK) {
-      st.step_chk(i, qh, r.x, r.y, Qc, Qh, n, first_inf);
-    } else {
-      st.step(qh, r.x, r.y, Qc);
-      st.check();
-    }
+    do_step(i, qh, r, true);
     if (PRED) {
       ps.put(u % W, pred_of(i));
       if (u % W == W - 1 || i == n) ps.flush(i - u % W, u % W + 1);
@@ -399,16 +514,17 @@ __device__ __forceinline__ void pipe_tile(int n, int Q, const unsigned char* qro
   }
   *K_out = st.K;
   *first_inf_out = first_inf;
-  *bad = st.ovf;
+  *bad = st.ovf || (SOFT && st.ovfL);
 }
 
 // ------------------------------------------------------------------ kernel
-template <typename QT, typename PT, bool PRED, bool BATCH>
+template <typename QT, typename PT, bool PRED, bool BATCH, bool SOFT>
 __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full_bar[kNStage], empty_bar[kNStage];
   __shared__ StageMeta smeta[kNStage];
   __shared__ uint32_t slot_ready[kSlots], slot_free[kSlots], slot_inf[kSlots];
+  __shared__ uint32_t slot_fb[kSlots];  // soft: rows with a demand the staging type cannot hold
   __shared__ uint32_t item_cnt[kSlots], item_need[kSlots];
   __shared__ int32_t slot_b[kSlots];
   __shared__ int64_t slot_s0[kSlots];
@@ -462,6 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   const int64_t groups = gpt * a.B;
 
   constexpr int PER = 4 / (int)sizeof(QT);  // demands per 32-bit slot word
+  constexpr int kSoftMax = soft_max<QT>();
   auto full_of = [&](int64_t x) -> uint32_t { return full0 + 8u * (uint32_t)(x % kNStage); };
   auto empty_of = [&](int64_t x) -> uint32_t { return empty0 + 8u * (uint32_t)(x % kNStage); };
   auto par_of = [&](int64_t x) -> uint32_t { return (uint32_t)(x / kNStage) & 1u; };
@@ -530,6 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
             }
           }
           slot_inf[slot] = 0u;
+          slot_fb[slot] = 0u;
           slot_b[slot] = b;
           slot_s0[slot] = s0;
           item_cnt[slot] = 0u;
@@ -661,16 +779,23 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
                        ? __byte_perm(__byte_perm(v[0], v[1 % PER], 0x0040),
                                      __byte_perm(v[2 % PER], v[3 % PER], 0x0040), 0x5410)
                        : __byte_perm(v[0], v[1 % PER], 0x5410);
-          } else {  // a demand above Q or below 0: clamp to [0, Q+1]
-            bool inf = false;
+          } else {
+            // a demand above Q or below 0.  Hard capacity: clamp to
+            // [0, Q+1] (the tile takes the checked step, the scenario is
+            // infeasible).  Soft: kept exactly for the checked step up to
+            // kSoftMax (so that Q + q < 2^16 in the front test); beyond it
+            // the scenario goes to the plain kernel.
+            bool inf = false, big = false;
             word = 0u;
 #pragma unroll
             for (int e = 0; e < PER; ++e) {
               inf |= v[e] > Q;
               mn_all = min(mn_all, v[e]);
-              word |= (uint32_t)min(max(v[e], 0), Q + 1) << (e * 8 * (int)sizeof(QT));
+              big |= SOFT && v[e] > kSoftMax;
+              word |= (uint32_t)min(max(v[e], 0), SOFT ? kSoftMax : Q + 1) << (e * 8 * (int)sizeof(QT));
             }
             if (inf) atomicOr(&slot_inf[slot], 1u << (mt.rbase + r));
+            if (big) atomicOr(&slot_fb[slot], 1u << (mt.rbase + r));
           }
           *o = word & wmask[j];
         }
@@ -730,6 +855,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     const int b = slot_b[slot];
     const int64_t s0 = slot_s0[slot];
     const uint32_t tf = slot_inf[slot];
+    const uint32_t tfb = SOFT ? slot_fb[slot] : 0u;
     const int n = BATCH ? a.n[b] : a.n1;
     const int rows = (int)imin64(32, S - s0);
     const bool live = lane < rows;
@@ -747,19 +873,19 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     if (BATCH) {
       const GlobalRec2 rec{a.rec + a.rec_off[b]};
       if (tf)
-        pipe_tile<QT, PT, PRED, true>(n, Q, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
+        pipe_tile<QT, PT, PRED, true, false>(n, Q, 0.f, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
       else
-        pipe_tile<QT, PT, PRED, false>(n, Q, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
+        pipe_tile<QT, PT, PRED, false, false>(n, Q, 0.f, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
     } else {
       const SmemRec2 rec{smem_u32(rec2)};
       if (tf)
-        pipe_tile<QT, PT, PRED, true>(n, Q, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
+        pipe_tile<QT, PT, PRED, true, SOFT>(n, Q, a.beta, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
       else
-        pipe_tile<QT, PT, PRED, false>(n, Q, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
+        pipe_tile<QT, PT, PRED, false, SOFT>(n, Q, a.beta, qrow, ring, rec, lane, ps, &K, &first_inf, &bad);
     }
     __syncwarp();  // every lane is done with the slot
     if (lane == 0) st_release_shared(&slot_free[slot], li + 1);
-    bad = bad && live;
+    bad = (bad || ((tfb >> lane) & 1u)) && live;
     if (live) {
       const int64_t g = BATCH ? (int64_t)b * S + s0 + lane : s0 + lane;
       if (bad) {
@@ -772,7 +898,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
         a.cost[g] = first_inf <= (uint32_t)n ? CUDART_INF_F : (float)((double)K + a.Dn[b]);
       }
     }
-    any_inf |= tf;
+    if (!SOFT) any_inf |= tf;
     any_fb |= __ballot_sync(0xffffffffu, bad);
   }
   if (lane == 0) {
@@ -789,9 +915,9 @@ size_t pipe_smem(const PipeArgs& a, bool pred) {
          (a.batched ? 2 * (size_t)kColsStride : (size_t)n + 8) * sizeof(uint16_t);
 }
 
-template <typename QT, typename PT, bool PRED, bool BATCH>
+template <typename QT, typename PT, bool PRED, bool BATCH, bool SOFT = false>
 int launch_k(const PipeArgs& a, cudaStream_t st) {
-  auto k = split_pipe_kernel<QT, PT, PRED, BATCH>;
+  auto k = split_pipe_kernel<QT, PT, PRED, BATCH, SOFT>;
   const size_t smem = pipe_smem(a, PRED);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
@@ -802,6 +928,11 @@ int launch_k(const PipeArgs& a, cudaStream_t st) {
 template <typename QT>
 int launch_q(const PipeArgs& a, cudaStream_t st) {
   if (a.batched) return launch_k<QT, uint16_t, false, true>(a, st);
+  if (a.soft) {  // one tour only
+    if (!a.pred) return launch_k<QT, uint16_t, false, false, true>(a, st);
+    if (a.pred_dtype == SDP_PRED_U16) return launch_k<QT, uint16_t, true, false, true>(a, st);
+    return launch_k<QT, int32_t, true, false, true>(a, st);
+  }
   if (!a.pred) return launch_k<QT, uint16_t, false, false>(a, st);
   if (a.pred_dtype == SDP_PRED_U16) return launch_k<QT, uint16_t, true, false>(a, st);
   return launch_k<QT, int32_t, true, false>(a, st);

@@ -33,7 +33,7 @@ def _case(seed, n, S, qlo, qhi, dist_mode=False):
     return tour, xy, dist, q
 
 
-@pytest.mark.parametrize("algo", ["plain", "deque"])
+@pytest.mark.parametrize("algo", ["plain", "deque", "pipe"])
 @pytest.mark.parametrize("beta", [0.0, 0.7, 5.0, 60.0])
 def test_soft_c1_vs_oracle(algo, beta):
     """n=50, Q=100, S=1000 Poisson(10) demands (the small Split workload)."""
@@ -51,7 +51,7 @@ def test_soft_c1_vs_oracle(algo, beta):
     assert sdp().status() & (sdp().FLAG_INFEASIBLE | sdp().FLAG_DEVICE_CHECK) == 0
 
 
-@pytest.mark.parametrize("algo", ["plain", "deque"])
+@pytest.mark.parametrize("algo", ["plain", "deque", "pipe"])
 @pytest.mark.parametrize("case", [
     # (seed, n, S, Q, qlo, qhi, beta, dist)
     (1, 1, 33, 10, 1, 25, 3.0, False),       # n = 1, demands above Q
@@ -75,7 +75,8 @@ def test_soft_edge_cases(algo, case):
     assert sdp().status() & sdp().FLAG_INFEASIBLE == 0
 
 
-def test_soft_staging_overflow_goes_to_plain():
+@pytest.mark.parametrize("algo", ["deque", "pipe"])
+def test_soft_staging_overflow_goes_to_plain(algo):
     """Q <= 254 stages demands as uint8: a row holding a demand of 300 cannot
     be staged and is recomputed by the plain kernel."""
     tour, xy, _, q = _case(11, 40, 70, 1, 30)
@@ -83,11 +84,67 @@ def test_soft_staging_overflow_goes_to_plain():
     q[64, 0] = 254
     Q, beta = 100, 3.0
     orc = oracle.split_soft(tour, Q, beta, q, coords=xy, want_margin=True)
-    r = sdp().split_eval(_cuda(tour), Q, _cuda(q), coords=_cuda(xy), preds="i32", algo="deque",
+    r = sdp().split_eval(_cuda(tour), Q, _cuda(q), coords=_cuda(xy), preds="i32", algo=algo,
                          overload_penalty=beta)
     torch.cuda.synchronize()
     assert sdp().status() & sdp().FLAG_FALLBACK
     check_split(r["cost"], r["pred"], orc, min_checked=0.0)
+
+
+@pytest.mark.parametrize("preds", ["u16", "i32", None])
+@pytest.mark.parametrize("case", [
+    # (seed, n, S, Q, qlo, qhi, beta)
+    (21, 50, 300, 40, 1, 20, 5.0),
+    (22, 301, 250, 120, 1, 30, 0.7),       # ragged tail, several tiles
+    (23, 500, 160, 200, 1, 30, 10.0),      # the benchmark's shape
+    (24, 200, 96, 100, 0, 160, 2.0),       # demands above Q (checked step), zeros
+    (25, 256, 70, 300, 1, 200, 3.0),       # uint16 rows
+    (26, 97, 64, 60, 1, 20, 0.0),          # beta = 0
+])
+def test_soft_pipe_bit_identical_to_deque(case, preds):
+    """The pipelined soft step does the DEQUE soft kernel's FP32 operations:
+    where neither recomputes a scenario, costs and predecessors are the same
+    bits."""
+    seed, n, S, Q, qlo, qhi, beta = case
+    tour, xy, _, q = _case(seed, n, S, qlo, qhi)
+    args = (_cuda(tour), Q, _cuda(q))
+    sdp().status()
+    r = sdp().split_eval(*args, coords=_cuda(xy), preds=preds, algo="pipe", overload_penalty=beta)
+    d = sdp().split_eval(*args, coords=_cuda(xy), preds=preds, algo="deque", overload_penalty=beta)
+    torch.cuda.synchronize()
+    assert sdp().status() & (sdp().FLAG_FALLBACK | sdp().FLAG_DEVICE_CHECK | sdp().FLAG_INFEASIBLE) == 0
+    assert torch.equal(r["cost"], d["cost"])
+    if preds:
+        assert torch.equal(r["pred"], d["pred"])
+    assert float(r["mean"]) == float(d["mean"])
+
+
+def test_soft_pipe_prefix_load_past_16_bits():
+    """Total demands beyond 2^16: the pipelined kernel's entries keep L(p)
+    modulo 2^16, so those scenarios are recomputed by the plain kernel; the
+    results stay the oracle's within tolerance."""
+    n, S, Q, beta = 900, 64, 400, 2.0
+    tour, xy, _, q = _case(31, n, S, 40, 140)
+    q[::2] //= 4  # half the scenarios stay below 2^16 in total
+    assert (q.sum(1) >= 65536).any() and (q.sum(1) < 65536).any()
+    orc = oracle.split_soft(tour, Q, beta, q, coords=xy, want_margin=True)
+    sdp().status()
+    r = sdp().split_eval(_cuda(tour), Q, _cuda(q), coords=_cuda(xy), preds="i32", algo="pipe",
+                         overload_penalty=beta)
+    torch.cuda.synchronize()
+    assert sdp().status() & sdp().FLAG_FALLBACK
+    check_split(r["cost"], r["pred"], orc, min_checked=0.0)
+
+
+def test_soft_auto_takes_pipe():
+    api = sdp()
+    tour, xy, _, q = _case(41, 400, 500, 1, 30)
+    args = (_cuda(tour), 150, _cuda(q))
+    r = api.split_eval(*args, coords=_cuda(xy), preds="u16", overload_penalty=4.0)
+    assert api.last_launch()[0] == 32
+    d = api.split_eval(*args, coords=_cuda(xy), preds="u16", algo="deque", overload_penalty=4.0)
+    torch.cuda.synchronize()
+    assert torch.equal(r["cost"], d["cost"]) and torch.equal(r["pred"], d["pred"])
 
 
 def test_soft_equals_hard_without_overflow():
@@ -112,8 +169,9 @@ def test_soft_rejections():
         with pytest.raises(api.SdpError) as e:
             api.split_eval(t, 50, qd, coords=c, **kw)
         assert e.value.code == code
-    # AUTO takes PLAIN for rows the deque cannot stage
+    # AUTO takes the pipelined kernel for rows the deque cannot stage
     r = api.split_eval(t, 50, qd, coords=c, overload_penalty=1.0, preds="i32")
+    assert api.last_launch()[0] == 32
     torch.cuda.synchronize()
     orc = oracle.split_soft(tour, 50, 1.0, q, coords=xy, want_margin=True)
     check_split(r["cost"], r["pred"], orc, min_checked=0.0)
