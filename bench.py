@@ -830,7 +830,7 @@ def op_saa(c, out):
     q = c.wl.split_demands_device(spec, c.dev)
     cache = os.path.join(tempfile.gettempdir(), "sdp_autotune_cache.txt")
     s = c.api.SaaSearch(t, cc, q, spec.Q, c.wl.SAA_B, seed=spec.seed)
-    s.autotune(cache)
+    shape = s.autotune(cache)
     warm = 3
     s.run(warm)  # warm-up: graph capture, first moves
     torch.cuda.synchronize()
@@ -861,7 +861,8 @@ def op_saa(c, out):
             "arcs_per_s": arcs / (ms / 1e3), "arcs": arcs,
             "roofline": c.alu_roof(2 * arcs, ms / iters * iters),
             "best_mean_first": float(tr[0]), "best_mean_last": float(tr[-1]),
-            "improving_iterations": int((acc >= 0).sum())}
+            "improving_iterations": int((acc >= 0).sum()),
+            "launch": shape}
     line["roofline"]["note"] = "whole iterations (moves, plan replay, selection) timed"
     if c.checks:
         import oracle

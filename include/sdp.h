@@ -454,6 +454,11 @@ size_t sdp_saa_search_desc_size(void);
  * overflow on later, better tours (longer monotone runs in the deque), whose
  * scenarios then go to the plain fallback.  Overwrites the last means. */
 int sdp_saa_search_autotune(sdp_saa_search* s, void* stream, const char* cache_path);
+/* Launch shape of the search's plan (as sdp_plan_info and
+ * sdp_plan_scenarios_per_lane report it for a plan; any pointer may be NULL).
+ * Host-side only.  Errors: SDP_ERR_INVALID_ARG (s NULL). */
+int sdp_saa_search_plan_info(const sdp_saa_search* s, int32_t* warps_per_cta, int32_t* ring,
+                             int32_t* ctas, int32_t* scenarios_per_lane);
 void sdp_saa_search_destroy(sdp_saa_search* s);
 
 /* ------------------------------------------------------------ Reinsertion */

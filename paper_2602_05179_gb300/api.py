@@ -113,6 +113,7 @@ def _load():
             "sdp_saa_search_run": ([P, i32, P, P, P], i32),
             "sdp_saa_search_state": ([P, P, P, P], i32),
             "sdp_saa_search_autotune": ([P, P, ctypes.c_char_p], i32),
+            "sdp_saa_search_plan_info": ([P, P, P, P, P], i32),
             "sdp_saa_search_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
@@ -610,6 +611,15 @@ class SaaSearch:
     def autotune(self, cache_path=None, stream=None):
         cp = cache_path.encode() if cache_path else None
         _check(self._lib.sdp_saa_search_autotune(self._h, _stream(stream), cp))
+        return self.info()
+
+    def info(self):
+        """Launch shape of the search's plan (see SplitPlan.info)."""
+        w, r, c, ns = (ctypes.c_int32() for _ in range(4))
+        _check(self._lib.sdp_saa_search_plan_info(self._h, ctypes.byref(w), ctypes.byref(r),
+                                                  ctypes.byref(c), ctypes.byref(ns)))
+        return {"warps_per_cta": w.value, "ring": r.value, "ctas": c.value,
+                "scenarios_per_lane": ns.value}
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

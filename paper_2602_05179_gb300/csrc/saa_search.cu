@@ -313,4 +313,12 @@ int sdp_saa_search_autotune(sdp_saa_search* s, void* stream, const char* cache_p
   return plan_autotune(s->plan, stream, cache_path, 16);
 }
 
+int sdp_saa_search_plan_info(const sdp_saa_search* s, int32_t* warps_per_cta, int32_t* ring,
+                             int32_t* ctas, int32_t* scenarios_per_lane) {
+  if (!s) return sfail(SDP_ERR_INVALID_ARG, "search is NULL");
+  const int rc = sdp_plan_info(s->plan, warps_per_cta, ring, ctas, nullptr);
+  if (rc) return rc;
+  return scenarios_per_lane ? sdp_plan_scenarios_per_lane(s->plan, scenarios_per_lane) : SDP_OK;
+}
+
 }  // extern "C"

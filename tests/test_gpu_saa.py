@@ -157,7 +157,11 @@ def test_autotune_keeps_the_trajectory(tmp_path):
     args = (_cuda(tour0), _cuda(xy), _cuda(q), 50, 128)
     a = sdp().SaaSearch(*args, seed=21)
     b = sdp().SaaSearch(*args, seed=21)
-    b.autotune(str(tmp_path / "cache.txt"))
+    shape = b.autotune(str(tmp_path / "cache.txt"))
+    # the search's plan reports the shape the autotune chose (deque rings of
+    # 16 entries only, or one of the producer/consumer kernels)
+    assert shape == b.info() and shape["ring"] == 16
+    assert shape["warps_per_cta"] in (-2, -1, 0, 1, 2, 4, 8) and shape["scenarios_per_lane"] in (1, 2)
     sdp().status()
     ta, aa = a.run(6)
     tb, ab = b.run(6)
