@@ -88,10 +88,11 @@ constexpr int kNStage = 2;                     // stages (copies in flight per C
 // CTAs' tile counts differ by one at most and every DP warp of the launch
 // gets within a tile of the same share (groups of 16 left 208 tiles on most
 // CTAs, 9.04 rounds of 23 warps, where the mean is 8.94: 1.204 -> 1.174 ms
-// at n = 500, S = 10^6); a batched plan claims 16, since every group may
-// change the tour, and a new tour waits for the chunks in flight.
+// at n = 500, S = 10^6); a batched plan claims 4, since every group may
+// change the tour (4096 tours, n 20..1000, S = 4096: groups of 64 / 32 / 16
+// / 8 / 4 took 19.07 / 18.73 / 18.55 / 18.47 / 18.40 ms).
 constexpr int kGroupOne = 1;
-constexpr int kGroupBatch = 16;
+constexpr int kGroupBatch = 4;
 __host__ __device__ constexpr int pipe_group(bool batched) { return batched ? kGroupBatch : kGroupOne; }
 constexpr int kRing = 16;                      // deque entries per lane
 constexpr uint32_t kRingBytes = (uint32_t)kRing * 256u;  // 32 lanes x 8 bytes per entry
