@@ -722,7 +722,9 @@ def op_fleet(c, out):
     line = {"value": S / (ms / 1e3), "unit": "scenarios/s", "ms_per_step": ms, "kernel_ms": kms,
             "kernel": "split_fleet_kernel (one warp per scenario, route counts across lanes)",
             "max_routes": K, "feasible_frac": float(fin.float().mean()),
-            "plain_fallback_used": fell_back,
+            "flagged_recomputed": fell_back,
+            "recompute": "scenarios whose deques outgrow the ring: split_fleet_rescue_kernel, one warp "
+                         "per scenario, inside ms_per_step (the roofline is the main kernel's)",
             "layer_relaxations_per_s": rel / (kms / 1e3),
             "roofline": c.alu_roof(2 * rel, kms),
             "vs_plain": {"path": "one thread per scenario, every feasible p of every layer",
