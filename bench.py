@@ -570,15 +570,21 @@ def op_routes(c, out):
     rcost = torch.from_numpy(rcost_h).to(c.dev)
     K = int(rcost.shape[1])
 
-    def run():
+    def run(algo="auto"):
         return c.api.reinsert_eval(rr.T, rr.U, rr.I0, rr.h, rr.p, rr.unit_cost, None, cons,
-                                   route_cost=rcost, route_cap=cap)
+                                   route_cost=rcost, route_cap=cap, algo=algo)
     ms, kms = _timed(run, c.steps or 10)
     r = run()
+    wms, wkms = _timed(lambda: run("warp"), c.steps or 10)
+    rw = run("warp")
+    same = all(bool(torch.equal(r[k], rw[k])) for k in ("value", "policy"))
     rel = float(rr.U + 1) * rr.T * (K + 1) * rr.S  # (state, action) pairs
     line = {"value": rel / (ms / 1e3), "unit": "relaxations/s",
             "scenarios_per_s": rr.S / (ms / 1e3), "ms_per_step": ms, "kernel_ms": kms,
-            "kernel": "reinsert_routes_kernel", "roofline": c.alu_roof(2 * rel, kms)}
+            "kernel": "reinsert_lane_kernel (route options, one scenario per lane)",
+            "roofline": c.alu_roof(2 * rel, kms),
+            "vs_warp": {"kernel": "reinsert_routes_kernel (one scenario per warp)", "ms_per_step": wms,
+                        "kernel_ms": wkms, "speedup": wkms / kms, "bit_identical": same}}
     if c.checks:
         import oracle
         rows = sample_rows(rr.S, 500, 13)

@@ -473,7 +473,8 @@ void sdp_saa_search_destroy(sdp_saa_search* s);
  * delivery; value = C_0(I0); policy = decisions along the optimal path. */
 /* Reinsertion kernels */
 #define SDP_REINSERT_AUTO 0  /* LANE where it applies (measured faster at
-                                T = 60, U = 200), else WARP */
+                                T = 60, U = 200, with and without route
+                                options), else WARP */
 #define SDP_REINSERT_WARP 1  /* one warp per scenario, states across lanes */
 #define SDP_REINSERT_LANE 2  /* one lane per scenario, its cost-to-go in shared
                                 memory (up to 8 warps per SM); needs U <= 255;
@@ -510,7 +511,9 @@ typedef struct sdp_reinsert_args {
                                  "Instantiation B").  policy_out then holds
                                  0 (no delivery) or r + 1; `fixed` is not
                                  read.  Needs U <= 255, K <= 64, no
-                                 end_cost_table, algo AUTO or WARP. */
+                                 end_cost_table; LANE takes K <= 8 (the
+                                 same bits as WARP), AUTO takes LANE there
+                                 and WARP beyond. */
   const float* route_cost;    /* [T*K] */
   const int32_t* route_cap;   /* [S*T*K] */
 } sdp_reinsert_args;

@@ -401,12 +401,21 @@ __global__ void __launch_bounds__(512) reinsert_routes_kernel(ReinsertArgs a) {
 // Needs U < 256; up to eight warps (one CTA) per SM, 32 KC x 128 bytes of
 // shared memory each.
 constexpr int kLaneWarps = 8;
+constexpr int kLaneMaxRoutes = 8;  // route options the lane kernel takes
 template <int M>
 struct IntTag {
   static constexpr int value = M;
 };
 
-template <int KC, bool TABLE, bool UNIT>
+// RK > 0: route options (at most RK of them, K = a.n_routes), linear end
+// costs: the delivery from state I rides the cheapest route whose residual
+// capacity in the lane's scenario holds U - I, F_t(I) = min over those of
+// rcost[t][r] (the test is I >= U - cap[t][r], one compare per route against
+// an immediate per row), dv(I) = F_t(I) + G_{t+1}(U - d_t) (+ c (U - I)): the
+// FP32 operations of reinsert_routes_kernel, so its bits.  The backtrack
+// recomputes the route of each delivery (the cheapest, the first on ties)
+// and writes r + 1 to the policy.
+template <int KC, bool TABLE, bool UNIT, int RK = 0>
 __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(ReinsertArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NI = 32 * KC;  // rows
@@ -419,7 +428,9 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
   float* ztab = etab + NI;
   float* ptab = ztab + 32;
   float* fixed_sm = ptab + 36;
-  const size_t off = (((size_t)NI + 32 + 36 + (size_t)T) * 4 + 15) & ~(size_t)15;
+  float* rcost_sm = fixed_sm + T;  // RK > 0: route costs [T][K]
+  const int K = RK > 0 ? a.n_routes : 0;
+  const size_t off = (((size_t)NI + 32 + 36 + (size_t)T + (size_t)T * K) * 4 + 15) & ~(size_t)15;
   float* Gl = reinterpret_cast<float*>(smem + off) + (size_t)warp * NI * 32 + lane;
   const float h = a.h, p = a.p, c = a.c;
   for (int r = threadIdx.x; r < NI; r += blockDim.x) {
@@ -428,7 +439,9 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
   }
   for (int m = threadIdx.x; m < 32; m += blockDim.x) ztab[m] = 0.f;
   for (int m = threadIdx.x; m < 36; m += blockDim.x) ptab[m] = __fmul_rn(p, (float)m);
-  for (int t = threadIdx.x; t < T; t += blockDim.x) fixed_sm[t] = __ldg(a.fixed + t);
+  if (RK == 0)
+    for (int t = threadIdx.x; t < T; t += blockDim.x) fixed_sm[t] = __ldg(a.fixed + t);
+  for (int i = threadIdx.x; i < T * K; i += blockDim.x) rcost_sm[i] = __ldg(a.route_cost + i);
   __syncthreads();
 
   const int64_t slot = (int64_t)blockIdx.x * nwarps + warp;
@@ -446,18 +459,20 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
     uint32_t pw;     // policy bytes of the current 4-day group
     int d;           // consumption of day t
     const int32_t* crow;
+    const int32_t* caps;  // RK > 0: the scenario's route capacities [T][K]
     uint8_t* prow;
     const uint32_t* words;
     bool live;
   } bt;
   bt.t = T;  // nothing to backtrack yet
-  bt.I = 0; bt.w = 0u; bt.pw = 0u; bt.d = 0; bt.crow = a.cons; bt.prow = nullptr;
+  bt.I = 0; bt.w = 0u; bt.pw = 0u; bt.d = 0; bt.crow = a.cons; bt.caps = a.route_cap; bt.prow = nullptr;
   bt.words = nullptr; bt.live = false;
   auto bt_start = [&](const int32_t* crow, int64_t s, bool live, const uint32_t* words) {
     bt.I = a.I0;
     bt.t = 0;
     bt.pw = 0u;
     bt.crow = crow;
+    if (RK > 0) bt.caps = a.route_cap + s * (int64_t)T * K;
     bt.prow = a.policy + s * T;
     bt.words = words;
     bt.live = live;
@@ -467,14 +482,26 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
   auto bt_day = [&]() {
     const int t = bt.t;
     const int dec = (int)((bt.w >> ((bt.I + P) & 31)) & 1u);
+    int pv = RK > 0 ? 0 : dec;
+    if (RK > 0 && dec) {  // the cheapest route that holds U - I, the first on ties
+      const int q = U - bt.I;
+      float best = CUDART_INF_F;
+      for (int r = 0; r < K; ++r) {
+        const float fr = rcost_sm[t * K + r];
+        if (__ldg(bt.caps + t * K + r) >= q && fr < best) {
+          best = fr;
+          pv = r + 1;
+        }
+      }
+    }
     if (pol4) {
-      bt.pw |= (uint32_t)dec << (8 * (t & 3));
+      bt.pw |= (uint32_t)pv << (8 * (t & 3));
       if ((t & 3) == 3) {
         if (bt.live) *reinterpret_cast<uint32_t*>(bt.prow + (t - 3)) = bt.pw;
         bt.pw = 0u;
       }
     } else if (bt.live) {
-      bt.prow[t] = (uint8_t)dec;
+      bt.prow[t] = (uint8_t)pv;
     }
     bt.I = max((dec ? U : bt.I) - bt.d, 0);
     bt.t = t + 1;
@@ -490,6 +517,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
     const int64_t s0 = tile * 32;
     const bool live = lane < a.S - s0;
     const int32_t* crow = a.cons + (s0 + (live ? lane : 0)) * T;
+    const int32_t* caprow = RK > 0 ? a.route_cap + (s0 + (live ? lane : 0)) * (int64_t)T * K : nullptr;
     auto cons_at = [&](int t) -> int {
       const int d = __ldg(crow + t);
       neg |= live && d < 0;
@@ -501,6 +529,10 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
     uint32_t* dwp = dw ? dw + 32 * (int64_t)parity * T * KC : nullptr;
 
     int d_next = cons_at(T - 1);
+    int capn[RK > 0 ? RK : 1];  // the capacities of the next day processed
+#pragma unroll
+    for (int r = 0; r < (RK > 0 ? RK : 1); ++r)
+      capn[r] = (RK > 0 && r < K) ? __ldg(caprow + (T - 1) * K + r) : 0;
     for (int t = T - 1; t >= 0; --t) {
       const int d = d_next;
       if (t > 0) d_next = cons_at(t - 1);  // one day ahead
@@ -511,8 +543,19 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
       // G_{t+1}(j), j < 0: table e(0) + C(0) = G(0); linear C(0) + p (-j)
       auto gneg = [&](int mj) -> float { return TABLE ? G0 : __fadd_rn(C0, __fmul_rn(p, (float)mj)); };
       const float gUd = d <= U ? Gl[32 * (U + P - d)] : gneg(d - U);
-      const float ft = fixed_sm[t];
+      const float ft = RK > 0 ? 0.f : fixed_sm[t];
       const float base = __fadd_rn(ft, gUd);
+      // route r holds the refill from state I iff I >= thr[r] = U - cap[t][r]
+      int thr[RK > 0 ? RK : 1];
+      float cr[RK > 0 ? RK : 1];
+      if (RK > 0) {
+#pragma unroll
+        for (int r = 0; r < RK; ++r) {
+          thr[r] = r < K ? U - capn[r] : 0x3FFFFFFF;
+          cr[r] = r < K ? rcost_sm[t * K + r] : CUDART_INF_F;
+          if (t > 0 && r < K) capn[r] = __ldg(caprow + (t - 1) * K + r);  // one day ahead
+        }
+      }
       const float* et = last ? ztab : etab;
       const int dmax = __reduce_max_sync(0xffffffffu, d);
       // rows below state 0 that this day reads at immediate offsets:
@@ -545,6 +588,10 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
           for (int j = 0; j < 32; ++j) v[j] = Gd[32 * (32 * k + j)];
         }
         const float4* e4 = reinterpret_cast<const float4*>(et + (last ? 0 : 32 * k));
+        // row 32 k + j is state I = 32 k + j - P: route r fits iff j >= tk[r]
+        int tk[RK > 0 ? RK : 1];
+#pragma unroll
+        for (int r = 0; r < (RK > 0 ? RK : 1); ++r) tk[r] = RK > 0 ? thr[r] + P - 32 * k : 0;
         // four partial words: short dependency chains for the bit ORs
         uint32_t w4[4] = {0u, 0u, 0u, 0u};
         float* Gk = Gl + 32 * 32 * k;
@@ -556,7 +603,16 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
           for (int u = 3; u >= 0; --u) {
             const int j = 4 * q4 + u;
             float dv = base;
-            if (UNIT) dv = __fadd_rn(base, __fmul_rn(c, (float)(U + P - 32 * k) - (float)j));
+            if (RK > 0) {
+              float F = CUDART_INF_F;
+#pragma unroll
+              for (int r = 0; r < RK; ++r)
+                if (j >= tk[r]) F = fminf(F, cr[r]);
+              dv = __fadd_rn(F, gUd);
+              if (UNIT) dv = __fadd_rn(dv, __fmul_rn(c, (float)(U + P - 32 * k) - (float)j));
+            } else if (UNIT) {
+              dv = __fadd_rn(base, __fmul_rn(c, (float)(U + P - 32 * k) - (float)j));
+            }
             const bool dec = dv < v[j];
             const float C = dec ? dv : v[j];
             Gk[32 * j] = __fadd_rn(es[u], C);
@@ -590,7 +646,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32, 1) reinsert_lane_kernel(Reins
       }
       // at I = U delivering is q = 0: no delivery, C = G_{t+1}(U - d).  The
       // comparison chose it unless f_t < 0.
-      if (ft < 0.f) Gl[32 * (U + P)] = __fadd_rn(et[last ? 0 : U + P], gUd);
+      if (RK > 0 || ft < 0.f) Gl[32 * (U + P)] = __fadd_rn(et[last ? 0 : U + P], gUd);
     }
     // the previous tile's path ends before this tile's starts
     while (bt.t < T) bt_day();
@@ -650,12 +706,13 @@ int by_kc(const ReinsertArgs& a, cudaStream_t st) {
   }
 }
 
-template <int KC, bool TABLE, bool UNIT>
+template <int KC, bool TABLE, bool UNIT, int RK = 0>
 int launch_lane_kc(const ReinsertArgs& a, cudaStream_t st) {
-  auto k = reinsert_lane_kernel<KC, TABLE, UNIT>;
-  const int warps = reinsert_lane_warps(a.T, a.U, TABLE);
+  auto k = reinsert_lane_kernel<KC, TABLE, UNIT, RK>;
+  const int nr = RK > 0 ? a.n_routes : 0;
+  const int warps = reinsert_lane_warps(a.T, a.U, TABLE, nr);
   if (warps < 1) return (int)cudaErrorInvalidValue;
-  const size_t smem = reinsert_lane_smem_for(a.T, a.U, TABLE, warps);
+  const size_t smem = reinsert_lane_smem_for(a.T, a.U, TABLE, warps, nr);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int64_t tiles = (a.S + 31) / 32;
@@ -702,40 +759,41 @@ int routes_by_kc(const ReinsertArgs& a, cudaStream_t st) {
   }
 }
 
-template <bool TABLE, bool UNIT>
+template <bool TABLE, bool UNIT, int RK = 0>
 int lane_by_kc(const ReinsertArgs& a, cudaStream_t st) {
   switch ((a.U + 1 + 31) / 32) {
-    case 1: return launch_lane_kc<1, TABLE, UNIT>(a, st);
-    case 2: return launch_lane_kc<2, TABLE, UNIT>(a, st);
-    case 3: return launch_lane_kc<3, TABLE, UNIT>(a, st);
-    case 4: return launch_lane_kc<4, TABLE, UNIT>(a, st);
-    case 5: return launch_lane_kc<5, TABLE, UNIT>(a, st);
-    case 6: return launch_lane_kc<6, TABLE, UNIT>(a, st);
-    case 7: return launch_lane_kc<7, TABLE, UNIT>(a, st);
-    default: return launch_lane_kc<8, TABLE, UNIT>(a, st);
+    case 1: return launch_lane_kc<1, TABLE, UNIT, RK>(a, st);
+    case 2: return launch_lane_kc<2, TABLE, UNIT, RK>(a, st);
+    case 3: return launch_lane_kc<3, TABLE, UNIT, RK>(a, st);
+    case 4: return launch_lane_kc<4, TABLE, UNIT, RK>(a, st);
+    case 5: return launch_lane_kc<5, TABLE, UNIT, RK>(a, st);
+    case 6: return launch_lane_kc<6, TABLE, UNIT, RK>(a, st);
+    case 7: return launch_lane_kc<7, TABLE, UNIT, RK>(a, st);
+    default: return launch_lane_kc<8, TABLE, UNIT, RK>(a, st);
   }
 }
 }  // namespace
 
-size_t reinsert_lane_smem_for(int T, int U, bool /*table*/, int warps) {
+size_t reinsert_lane_smem_for(int T, int U, bool /*table*/, int warps, int n_routes) {
   const int NI = 32 * ((U + 1 + 31) / 32);
-  return ((((size_t)NI + 32 + 36 + (size_t)T) * 4 + 15) & ~(size_t)15) +
+  return ((((size_t)NI + 32 + 36 + (size_t)T + (size_t)T * n_routes) * 4 + 15) & ~(size_t)15) +
          (size_t)warps * NI * 32 * 4;
 }
 
 // Warps per CTA (one CTA per SM): as many as the shared memory holds, up to 8.
-int reinsert_lane_warps(int T, int U, bool table) {
+int reinsert_lane_warps(int T, int U, bool table, int n_routes) {
   int w = kLaneWarps;
-  while (w > 0 && reinsert_lane_smem_for(T, U, table, w) > 227 * 1024) --w;
+  while (w > 0 && reinsert_lane_smem_for(T, U, table, w, n_routes) > 227 * 1024) --w;
   return w;
 }
 
-bool reinsert_lane_supported(int T, int U) {
-  return U >= 0 && U < 256 && T >= 1 && T <= 4096 && reinsert_lane_warps(T, U, true) >= 4;
+bool reinsert_lane_supported(int T, int U, int n_routes) {
+  return U >= 0 && U < 256 && T >= 1 && T <= 4096 && n_routes >= 0 && n_routes <= kLaneMaxRoutes &&
+         reinsert_lane_warps(T, U, true, n_routes) >= 4;
 }
 
 size_t reinsert_lane_smem(int T, int U, bool table) {
-  return reinsert_lane_smem_for(T, U, table, reinsert_lane_warps(T, U, table));
+  return reinsert_lane_smem_for(T, U, table, reinsert_lane_warps(T, U, table, 0), 0);
 }
 
 size_t reinsert_lane_scratch_bytes(int T, int U) {
@@ -748,6 +806,13 @@ int launch_reinsert(const ReinsertArgs& a, cudaStream_t st) {
   const bool unit = a.c != 0.f;
   if (a.n_routes > 0) {  // route options: U <= 255, linear end costs (checked by the caller)
     if (a.U > 255 || a.table) return (int)cudaErrorInvalidValue;
+    // AUTO takes the lane kernel where it applies (up to 8 routes)
+    if ((a.algo == SDP_REINSERT_LANE || a.algo == SDP_REINSERT_AUTO) &&
+        reinsert_lane_supported(a.T, a.U, a.n_routes)) {
+      if (a.n_routes <= 4)
+        return unit ? lane_by_kc<false, true, 4>(a, st) : lane_by_kc<false, false, 4>(a, st);
+      return unit ? lane_by_kc<false, true, 8>(a, st) : lane_by_kc<false, false, 8>(a, st);
+    }
     return unit ? routes_by_kc<true>(a, st) : routes_by_kc<false>(a, st);
   }
   // AUTO takes LANE where it applies: at T = 60, U = 200, S = 10^6 it runs in
@@ -756,7 +821,7 @@ int launch_reinsert(const ReinsertArgs& a, cudaStream_t st) {
   // shuffle and a select cost what the shared load and store they replace
   // do, and WARP is issue-bound at 82%, not bound by shared memory)
   if ((a.algo == SDP_REINSERT_LANE || a.algo == SDP_REINSERT_AUTO) &&
-      reinsert_lane_supported(a.T, a.U)) {
+      reinsert_lane_supported(a.T, a.U, 0)) {
     if (a.table) return unit ? lane_by_kc<true, true>(a, st) : lane_by_kc<true, false>(a, st);
     return unit ? lane_by_kc<false, true>(a, st) : lane_by_kc<false, false>(a, st);
   }

@@ -982,8 +982,9 @@ namespace {
 // the lane kernel keeps its decision bits in the workspace when the policy
 // is wanted
 bool reinsert_uses_lane(const sdp_reinsert_args* a) {
-  return (a->algo == SDP_REINSERT_LANE || a->algo == SDP_REINSERT_AUTO) && a->n_routes == 0 &&
-         reinsert_lane_supported(a->T, a->U);
+  return (a->algo == SDP_REINSERT_LANE || a->algo == SDP_REINSERT_AUTO) &&
+         !(a->n_routes > 0 && a->end_cost_table) &&
+         reinsert_lane_supported(a->T, a->U, a->n_routes);
 }
 size_t reinsert_scratch_bytes(const sdp_reinsert_args* a) {
   return (reinsert_uses_lane(a) && a->policy_out && a->S > 0)
@@ -1009,13 +1010,12 @@ int sdp_reinsert_eval(const sdp_reinsert_args* a, void* stream) {
   if (a->n_routes > 0) {
     if (a->U > 255) return fail(SDP_ERR_UNSUPPORTED, "route options need U <= 255");
     if (a->end_cost_table) return fail(SDP_ERR_UNSUPPORTED, "route options take linear end costs");
-    if (a->algo == SDP_REINSERT_LANE)
-      return fail(SDP_ERR_UNSUPPORTED, "route options run on the warp kernel");
     if (a->S > 0 && (!is_device_ptr(a->route_cost) || !is_device_ptr(a->route_cap)))
       return fail(SDP_ERR_INVALID_ARG, "route_cost / route_cap must be device pointers");
   }
-  if (a->algo == SDP_REINSERT_LANE && !reinsert_lane_supported(a->T, a->U))
-    return fail(SDP_ERR_UNSUPPORTED, "SDP_REINSERT_LANE needs U <= 255 and its shared memory to fit");
+  if (a->algo == SDP_REINSERT_LANE && !reinsert_lane_supported(a->T, a->U, a->n_routes))
+    return fail(SDP_ERR_UNSUPPORTED,
+                "SDP_REINSERT_LANE needs U <= 255, at most 8 route options and its shared memory to fit");
   const int kc = a->U + 1 <= 256 ? (a->U + 1 + 31) / 32 : (a->U + 1 <= 512 ? 16 : 32);
   const int64_t words = (int64_t)a->T * ((kc + 7) & ~7);
   if (words > 4096)

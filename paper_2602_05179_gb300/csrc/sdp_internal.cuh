@@ -382,10 +382,10 @@ struct ReinsertArgs {
 int launch_reinsert(const ReinsertArgs& a, cudaStream_t st);
 // one-scenario-per-lane kernel: shapes it runs, its shared memory and the
 // decision scratch it needs when the policy is wanted
-bool reinsert_lane_supported(int T, int U);
+bool reinsert_lane_supported(int T, int U, int n_routes);
 size_t reinsert_lane_smem(int T, int U, bool table);
-size_t reinsert_lane_smem_for(int T, int U, bool table, int warps);
-int reinsert_lane_warps(int T, int U, bool table);
+size_t reinsert_lane_smem_for(int T, int U, bool table, int warps, int n_routes);
+int reinsert_lane_warps(int T, int U, bool table, int n_routes);
 size_t reinsert_lane_scratch_bytes(int T, int U);
 
 int num_sms();

@@ -48,7 +48,8 @@ def _routes_policy_check(gp, orc, cons, U, I0):
     (4, 20, 0, 0, 33, 2, 3.0, 0.0, 0, 5),      # U = 0: nothing to deliver
     (5, 8, 255, 255, 37, 8, 20.0, 1.5, 100, 255),  # the largest U, I0 = U
 ])
-def test_routes_vs_oracle(case):
+@pytest.mark.parametrize("algo", ["warp", "lane"])
+def test_routes_vs_oracle(case, algo):
     seed, T, U, I0, S, K, lam, c, clo, chi = case
     rng = np.random.default_rng(seed)
     cons = rng.poisson(lam, size=(S, T)).astype(np.int32)
@@ -57,7 +58,7 @@ def test_routes_vs_oracle(case):
     o = oracle.reinsert_routes(T, U, I0, 1.0, 20.0, c, rcost, cap, cons, want_value0=True,
                                want_margin=True)
     r = sdp().reinsert_eval(T, U, I0, 1.0, 20.0, c, None, _cuda(cons), value0=True,
-                            route_cost=_cuda(rcost), route_cap=_cuda(cap))
+                            route_cost=_cuda(rcost), route_cap=_cuda(cap), algo=algo)
     torch.cuda.synchronize()
     check_reinsert(r["value"], None, o, cons, U, I0)
     np.testing.assert_allclose(r["value0"].cpu().double().numpy(), o["value0"], rtol=1e-5,
@@ -84,17 +85,54 @@ def test_one_roomy_route_is_the_two_action_kernel():
             assert torch.equal(a[key], b[key]), key
 
 
+@pytest.mark.parametrize("case", [
+    # seed, T, U, I0, S, K, lam, unit_cost, cap_lo, cap_hi
+    (11, 60, 200, 100, 1000, 4, 8.0, 0.0, 0, 250),   # the route workload's shape
+    (12, 17, 90, 33, 97, 1, 6.0, 0.5, 0, 120),       # one route, ragged S
+    (13, 33, 63, 5, 64, 7, 15.0, 0.0, -5, 80),       # negative capacities (never usable)
+    (14, 12, 255, 0, 40, 8, 40.0, 2.0, 0, 300),      # the largest U, consumption above 32
+    (15, 5, 31, 31, 33, 3, 2.0, 0.0, 0, 31),         # U + 1 = 32, I0 = U
+])
+def test_routes_lane_bit_identical_to_warp(case):
+    """The lane kernel's route minimum does the warp kernel's FP32 operations:
+    values, C_0 tables and policies (r + 1 of the route taken) are the same."""
+    seed, T, U, I0, S, K, lam, c, clo, chi = case
+    rng = np.random.default_rng(seed)
+    cons = rng.poisson(lam, size=(S, T)).astype(np.int32)
+    rcost = rng.uniform(5, 50, (T, K)).astype(np.float32)
+    cap = rng.integers(clo, chi + 1, size=(S, T, K)).astype(np.int32)
+    kw = dict(value0=True, route_cost=_cuda(rcost), route_cap=_cuda(cap))
+    w = sdp().reinsert_eval(T, U, I0, 1.0, 20.0, c, None, _cuda(cons), algo="warp", **kw)
+    ln = sdp().reinsert_eval(T, U, I0, 1.0, 20.0, c, None, _cuda(cons), algo="lane", **kw)
+    au = sdp().reinsert_eval(T, U, I0, 1.0, 20.0, c, None, _cuda(cons), **kw)
+    torch.cuda.synchronize()
+    for key in ("value", "value0", "policy"):
+        assert torch.equal(w[key], ln[key]), key
+        assert torch.equal(au[key], ln[key]), key
+    assert float(w["mean"]) == float(ln["mean"])
+
+
 def test_routes_rejections():
     api = sdp()
     cons = torch.ones((4, 10), dtype=torch.int32, device="cuda")
     rc = torch.ones((10, 2), dtype=torch.float32, device="cuda")
     cap = torch.ones((4, 10, 2), dtype=torch.int32, device="cuda")
     tab = torch.ones(11, dtype=torch.float32, device="cuda")
-    for kw, U, code in ((dict(algo="lane"), 10, -5), (dict(table=tab), 10, -5), ({}, 300, -5)):
+    for kw, U, code in ((dict(table=tab), 10, -5), ({}, 300, -5)):
         with pytest.raises(api.SdpError) as e:
             api.reinsert_eval(10, U, 0, 1.0, 1.0, 0.0, None, cons, route_cost=rc, route_cap=cap,
                               **kw)
         assert e.value.code == code
+    # the lane kernel takes up to 8 route options; AUTO runs more on the warp kernel
+    rc9 = torch.ones((10, 9), dtype=torch.float32, device="cuda")
+    cap9 = torch.ones((4, 10, 9), dtype=torch.int32, device="cuda")
+    with pytest.raises(api.SdpError) as e:
+        api.reinsert_eval(10, 10, 0, 1.0, 1.0, 0.0, None, cons, route_cost=rc9, route_cap=cap9,
+                          algo="lane")
+    assert e.value.code == -5
+    r = api.reinsert_eval(10, 10, 0, 1.0, 1.0, 0.0, None, cons, route_cost=rc9, route_cap=cap9)
+    torch.cuda.synchronize()
+    assert torch.isfinite(r["value"]).all()
 
 
 def test_routes_full_size_sampled():
