@@ -136,6 +136,26 @@ def test_soft_pipe_prefix_load_past_16_bits():
     check_split(r["cost"], r["pred"], orc, min_checked=0.0)
 
 
+def test_soft_host_demands_chunked():
+    """Soft capacity with demands in pinned host memory (copied in 65,536-
+    scenario chunks behind the evaluation, the last one ragged): the same
+    bits as the call on device demands, whichever kernel AUTO runs."""
+    rng = np.random.default_rng(51)
+    n, S, Q, beta = 40, 140_003, 60, 3.0
+    xy = rng.uniform(0, 100, (n + 1, 2)).astype(np.float32)
+    tour = (rng.permutation(n) + 1).astype(np.int32)
+    q = rng.integers(1, 25, size=(S, n)).astype(np.int32)
+    q[11, 5] = 90  # above Q: allowed, it pays the penalty
+    t, c = _cuda(tour), _cuda(xy)
+    ref = sdp().split_eval(t, Q, _cuda(q), coords=c, preds="u16", overload_penalty=beta)
+    r = sdp().split_eval(t, Q, torch.from_numpy(q).pin_memory(), coords=c, preds="u16",
+                         overload_penalty=beta)
+    torch.cuda.synchronize()
+    assert torch.equal(r["cost"], ref["cost"]) and torch.equal(r["pred"], ref["pred"])
+    assert float(r["mean"]) == float(ref["mean"])
+    assert sdp().status() & sdp().FLAG_INFEASIBLE == 0
+
+
 def test_soft_auto_takes_pipe():
     api = sdp()
     tour, xy, _, q = _case(41, 400, 500, 1, 30)
