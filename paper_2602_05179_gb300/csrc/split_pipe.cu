@@ -12,14 +12,16 @@
 //   producers (1 issuing + 8 narrowing warps): the issuing warp claims work,
 //     sets up slots and feeds TMA bulk copies (cp.async.bulk, two 32 KB
 //     stages with full / empty mbarriers, L2 evict-first: every demand is read
-//     once) of R contiguous int32 demand rows into shared memory; the warps narrow them
-//     to uint8 (Q <= 254) or uint16, clamp them to [0, Q+1], permute them
-//     into tour order and write them to the CTA's ring of kSlots tile slots
-//     (32 rows of `stride` bytes each) in global memory.  The ring of all
-//     SMs (about 78 MB at n = 500) stays in L2, so the tour-ordered rows are
-//     written and read back without a DRAM round trip.  A slot is published
-//     through a shared counter (release / acquire) after a CTA-scope fence;
-//     its readers are warps of the same CTA.
+//     once) of R contiguous int32 demand rows into shared memory; the
+//     narrowing warps narrow them to uint8 (Q <= 254) or uint16 (hard
+//     capacity: clamped to [0, Q+1]; soft: kept exactly up to the staging
+//     type's range), permute them into tour order and write them to the
+//     CTA's ring of tile slots (up to kSlots, 32 rows of `stride` bytes
+//     each) in global memory.  The ring of all SMs (about 80 MB at n = 500)
+//     stays mostly in L2, so the tour-ordered rows are written and read back
+//     largely without a DRAM round trip.  A slot is published through a
+//     shared counter (release / acquire) by the narrowing warp that completes
+//     the item; its readers are warps of the same CTA.
 //   DP warps (23): claim the CTA's items in order from a shared counter, one
 //     32-scenario tile per warp, one scenario per lane; each lane reads its
 //     tour-ordered row 16 positions at a time (one block ahead, from L2)
@@ -27,8 +29,9 @@
 //     shared-memory transpose and leave as 32-byte row segments (the
 //     per-lane stores of one word per row that this replaces took 1.8 ms of a
 //     1.0 ms kernel's time at n = 496 through their 32 sector requests each).
-//   Work: groups of kGroup consecutive tiles of one tour, claimed from a
-//     global counter longest tour first, so the load balances itself.
+//   Work: groups of consecutive tiles of one tour (one tile for a single
+//     tour, 4 in a batched plan), claimed from a global counter, longest tour
+//     first, so the load balances itself.
 //
 // DP (Eq. eqdpA in the K-form of sdp_internal.cuh): K(i) = min over the
 // capacity window of psi(p) + ce_i, psi(p) = K(p) + a_{p+1}, with the window
@@ -56,7 +59,8 @@
 //     scenarios, which a test every 4 steps at 12 entries flagged.)
 // Tiles with a demand above Q (flagged by the producers) take a checked step
 // with emptiness tests, the first infeasible position recorded and an exact
-// ring test at every push.
+// ring test at every push.  Soft capacity (one tour) runs the same deque with
+// the expired entries' running minimum (Lane::step_soft / step_soft_chk).
 #include <math_constants.h>
 
 #include "async_copy.cuh"
