@@ -940,13 +940,17 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
 
 
 def kernel_rev(algo="pipe"):
-    """Hash of the DP kernel source, to tell whether stored ncu counters still
-    describe the kernel being timed."""
+    """Hash of the DP kernel source's code (comments and blank lines left
+    out), to tell whether stored ncu counters still describe the kernel being
+    timed."""
     import hashlib
+    import re
     name = {"pipe": "split_pipe.cu", "stream": "split_stream.cu"}.get(algo, "split_deque.cu")
     src = os.path.join(ROOT, "paper_2602_05179_gb300", "csrc", name)
-    with open(src, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(src) as f:
+        code = re.sub(r"//[^\n]*", "", f.read())
+    code = "\n".join(line.rstrip() for line in code.splitlines() if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 if __name__ == "__main__":
