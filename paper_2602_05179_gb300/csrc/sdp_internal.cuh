@@ -286,6 +286,7 @@ struct PipeArgs {
   int pred_dtype;
   unsigned char* qt;           // slot ring, pipe_ring_bytes
   int nslot;                   // slots per CTA (set by launch_split_pipe)
+  int n_max;                   // batched: the longest tour
   int soft;                    // one tour: soft capacity, beta per unit of route load above Q
   float beta;
   int64_t stride;              // bytes per slot row (pipe_row_stride of the longest tour)

@@ -158,6 +158,7 @@ int enqueue(sdp_plan* p, cudaStream_t st, uint32_t* status, bool with_events) {
     pa.n = p->d_n; pa.dem_off = p->d_dem_off; pa.rec_off = p->d_rec_off; pa.order = p->d_order;
     pa.rec = p->d_rec; pa.Dn = p->d_Dn; pa.demands = p->demands; pa.cost = p->costs;
     pa.qt = p->d_pq; pa.stride = pipe_row_stride(p->n_max, p->Q); pa.counter = p->d_counter;
+    pa.n_max = p->n_max;
     pa.fb_count = p->d_fb_count; pa.fb_list = p->d_fb_list; pa.status = status;
     e = launch_split_pipe(pa, st);
   } else if (p->warps < 0) {

@@ -84,10 +84,16 @@ constexpr int kSlots = 32;                     // tile slots per CTA in the ring
 // (whole tiles in one chunk up to n = 384: 18.9 -> 18.5 ms); one tour keeps
 // 32 KB (48 KB measured 1.165 -> 1.210 ms at n = 500), and a third stage
 // helped neither.
-__host__ __device__ constexpr uint32_t pipe_stage_bytes(bool batched) {
-  return (batched ? 48u : 32u) * 1024u;
+//
+// A batched plan whose tours are all short (n <= 128: a whole tile is one
+// chunk of 16 KB at most) is bound by the round trip of a stage instead
+// (copy, narrowing, barrier, next copy: with two stages a CTA got a tile
+// every ~2.9 us on 1025 tours of n = 100), so it takes six 16 KB stages.
+constexpr int kMaxNStage = 6;
+constexpr int kShortTour = 128;
+__host__ __device__ constexpr uint32_t pipe_stage_bytes(bool batched, int nstage) {
+  return nstage == 2 ? (batched ? 48u : 32u) * 1024u : 16u * 1024u;
 }
-constexpr int kNStage = 2;                     // stages (copies in flight per CTA)
 // tiles per claimed group: one tour takes them one at a time, so that the
 // CTAs' tile counts differ by one at most and every DP warp of the launch
 // gets within a tile of the same share (groups of 16 left 208 tiles on most
@@ -523,11 +529,13 @@ __device__ __forceinline__ void pipe_tile(int n, int Q, float beta, const unsign
 }
 
 // ------------------------------------------------------------------ kernel
-template <typename QT, typename PT, bool PRED, bool BATCH, bool SOFT>
+template <typename QT, typename PT, bool PRED, bool BATCH, bool SOFT, int NST>
 __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
+  constexpr int kNStage = NST;  // producer stages of this launch
+  static_assert(NST >= 2 && NST <= kMaxNStage, "stage count");
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full_bar[kNStage], empty_bar[kNStage];
-  __shared__ StageMeta smeta[kNStage];
+  __shared__ __align__(8) uint64_t full_bar[kMaxNStage], empty_bar[kMaxNStage];
+  __shared__ StageMeta smeta[kMaxNStage];
   __shared__ uint32_t slot_ready[kSlots], slot_free[kSlots], slot_inf[kSlots];
   __shared__ uint32_t slot_fb[kSlots];  // soft: rows with a demand the staging type cannot hold
   __shared__ uint32_t item_cnt[kSlots], item_need[kSlots];
@@ -539,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   const int Q = a.Q;
   const int64_t S = a.S;
   // shared: stages | DP rings | predecessor stages | (one tour) records | columns
-  constexpr uint32_t kStage = pipe_stage_bytes(BATCH);  // bytes per producer stage
+  constexpr uint32_t kStage = pipe_stage_bytes(BATCH, NST);  // bytes per producer stage
   const uint32_t rings = (smem_u32(smem) + kNStage * kStage + kRingBytes - 1) & ~(kRingBytes - 1);
   const size_t rings_off = rings - smem_u32(smem);  // (the smem size holds kRingBytes of slack)
   uint32_t* ostage = reinterpret_cast<uint32_t*>(smem + rings_off + (size_t)kDp * kRingBytes);
@@ -727,6 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     uint32_t wcol[kWords][PER];          // byte offset in a stage row of each position
     uint32_t wmask[kWords];              // the word's bits of positions below n
     int cached_gen = -1, n = 0, wq = 0, R = 0;
+    int kw0 = kw, roff = 0, rstep = 2;  // this thread's first word, row offset and row step
     int mn_all = 0;
     for (int64_t x = 0;; ++x) {
       if (!mbar_wait_abortable(full_of(x), par_of(x), &abort_flag, a.wait_ns)) {
@@ -742,12 +751,21 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
         wq = (n + PER - 1) / PER;
         R = 32;  // rows per chunk, as the issuer chose them
         while ((uint32_t)R * (uint32_t)n * 4u > kStage) R >>= 1;
+        // short rows (wq <= kHalf / 2): the kHalf threads of a parity form
+        // G = kHalf / wq groups of wq, group g taking rows rpar + 2 g,
+        // rpar + 2 g + 2 G, ..., so that most threads have a word to narrow
+        // (n = 100: 125 of 128 instead of 25); a thread keeps one word's
+        // columns either way
+        const int G = wq <= kHalf / 2 ? kHalf / wq : 1;
+        kw0 = G > 1 ? (kw < G * wq ? kw % wq : wq) : kw;
+        roff = G > 1 ? 2 * (kw / wq) : 0;
+        rstep = 2 * G;
 #pragma unroll
         for (int j = 0; j < kWords; ++j) {
           // a position past n reads the word's first column again (same
           // value: the range test is unchanged) and is masked off after
           // packing
-          const int k = kw + kHalf * j;
+          const int k = kw0 + kHalf * j;
           const uint16_t* cols = cols_of(cached_gen);
           const uint32_t c0 = k < wq ? (uint32_t)cols[PER * k] * 4u : 0u;
           wmask[j] = 0u;
@@ -765,12 +783,13 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
       uint32_t* out = reinterpret_cast<uint32_t*>(qslots + ((int64_t)slot * 32 + mt.rbase) * a.stride);
 #pragma unroll
       for (int j = 0; j < kWords; ++j) {
-        const int k = kw + kHalf * j;
+        const int k = kw0 + kHalf * j;
         if (k >= wq) break;
-        uint32_t rb = sq_b + (uint32_t)(rpar * n) * 4u;  // stage row rpar
-        uint32_t* o = out + (int64_t)rpar * sw + k;
-        int r = rpar;
-        for (; r < rows; r += 2, rb += 8u * (uint32_t)n, o += 2 * sw) {
+        const int r0 = rpar + roff;
+        uint32_t rb = sq_b + (uint32_t)(r0 * n) * 4u;  // stage row r0
+        uint32_t* o = out + (int64_t)r0 * sw + k;
+        int r = r0;
+        for (; r < rows; r += rstep, rb += 4u * (uint32_t)rstep * (uint32_t)n, o += rstep * sw) {
           int v[PER];
 #pragma unroll
           for (int e = 0; e < PER; ++e)
@@ -804,7 +823,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
           }
           *o = word & wmask[j];
         }
-        for (; r < R; r += 2, o += 2 * sw) *o = 0u;  // rows past S
+        for (; r < R; r += rstep, o += rstep * sw) *o = 0u;  // rows past S
       }
       __syncwarp();
       if (lane == 0) {
@@ -913,16 +932,19 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
   }
 }
 
+int pipe_nstage(const PipeArgs& a) { return a.batched && a.n_max <= kShortTour ? kMaxNStage : 2; }
+
 size_t pipe_smem(const PipeArgs& a, bool pred) {
   const int n = a.batched ? kPipeMaxN : a.n1;
-  return (size_t)kNStage * pipe_stage_bytes(a.batched != 0) + (size_t)(kDp + 1) * kRingBytes + (pred ? (size_t)kDp * kOutBytes : 0) +
+  const int ns = pipe_nstage(a);
+  return (size_t)ns * pipe_stage_bytes(a.batched != 0, ns) + (size_t)(kDp + 1) * kRingBytes + (pred ? (size_t)kDp * kOutBytes : 0) +
          (a.batched ? 0 : (size_t)n * sizeof(float2)) +
          (a.batched ? 2 * (size_t)kColsStride : (size_t)n + 8) * sizeof(uint16_t);
 }
 
-template <typename QT, typename PT, bool PRED, bool BATCH, bool SOFT = false>
+template <typename QT, typename PT, bool PRED, bool BATCH, bool SOFT = false, int NST = 2>
 int launch_k(const PipeArgs& a, cudaStream_t st) {
-  auto k = split_pipe_kernel<QT, PT, PRED, BATCH, SOFT>;
+  auto k = split_pipe_kernel<QT, PT, PRED, BATCH, SOFT, NST>;
   const size_t smem = pipe_smem(a, PRED);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
@@ -932,7 +954,9 @@ int launch_k(const PipeArgs& a, cudaStream_t st) {
 
 template <typename QT>
 int launch_q(const PipeArgs& a, cudaStream_t st) {
-  if (a.batched) return launch_k<QT, uint16_t, false, true>(a, st);
+  if (a.batched)
+    return pipe_nstage(a) == kMaxNStage ? launch_k<QT, uint16_t, false, true, false, kMaxNStage>(a, st)
+                                        : launch_k<QT, uint16_t, false, true>(a, st);
   if (a.soft) {  // one tour only
     if (!a.pred) return launch_k<QT, uint16_t, false, false, true>(a, st);
     if (a.pred_dtype == SDP_PRED_U16) return launch_k<QT, uint16_t, true, false, true>(a, st);
