@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     uint32_t wcol[kWords][PER];          // byte offset in a stage row of each position
     uint32_t wmask[kWords];              // the word's bits of positions below n
     int cached_gen = -1, n = 0, wq = 0, R = 0;
-    int kw0 = kw, roff = 0, rstep = 2;  // this thread's first word, row offset and row step
+    int kw0 = kw, rfirst = rpar, rstep = 2;  // this thread's first word, first row and row step
     int mn_all = 0;
     for (int64_t x = 0;; ++x) {
       if (!mbar_wait_abortable(full_of(x), par_of(x), &abort_flag, a.wait_ns)) {
@@ -751,15 +751,23 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
         wq = (n + PER - 1) / PER;
         R = 32;  // rows per chunk, as the issuer chose them
         while ((uint32_t)R * (uint32_t)n * 4u > kStage) R >>= 1;
-        // short rows (wq <= kHalf / 2): the kHalf threads of a parity form
-        // G = kHalf / wq groups of wq, group g taking rows rpar + 2 g,
-        // rpar + 2 g + 2 G, ..., so that most threads have a word to narrow
-        // (n = 100: 125 of 128 instead of 25); a thread keeps one word's
-        // columns either way
-        const int G = wq <= kHalf / 2 ? kHalf / wq : 1;
-        kw0 = G > 1 ? (kw < G * wq ? kw % wq : wq) : kw;
-        roff = G > 1 ? 2 * (kw / wq) : 0;
-        rstep = 2 * G;
+        // rows short enough for three or more groups: the kNarrowThreads
+        // threads form G = kNarrowThreads / wq groups of wq, group g taking
+        // rows g, g + G, ..., so that most threads have a word to narrow
+        // (n = 100: 250 of 256, n = 300: 225 instead of 150); longer rows: a
+        // thread per word position of its parity's rows (n = 500: 250, and
+        // each warp stores 32 words of one row).  A thread keeps one word's
+        // columns either way.
+        if (kNarrowThreads / wq >= 3) {
+          const int G = kNarrowThreads / wq;
+          kw0 = t < G * wq ? t % wq : wq;
+          rfirst = t < G * wq ? t / wq : 0;
+          rstep = G;
+        } else {
+          kw0 = kw;
+          rfirst = rpar;
+          rstep = 2;
+        }
 #pragma unroll
         for (int j = 0; j < kWords; ++j) {
           // a position past n reads the word's first column again (same
@@ -785,7 +793,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
       for (int j = 0; j < kWords; ++j) {
         const int k = kw0 + kHalf * j;
         if (k >= wq) break;
-        const int r0 = rpar + roff;
+        const int r0 = rfirst;
         uint32_t rb = sq_b + (uint32_t)(r0 * n) * 4u;  // stage row r0
         uint32_t* o = out + (int64_t)r0 * sw + k;
         int r = r0;
