@@ -11,7 +11,8 @@
 //
 //   producers (1 issuing + 8 narrowing warps): the issuing warp claims work,
 //     sets up slots and feeds TMA bulk copies (cp.async.bulk, two 32 KB
-//     stages with full / empty mbarriers, L2 evict-first: every demand is read
+//     stages with full / empty mbarriers -- 48 KB in a batched plan, six of
+//     16 KB when its tours are short -- L2 evict-first: every demand is read
 //     once) of R contiguous int32 demand rows into shared memory; the
 //     narrowing warps narrow them to uint8 (Q <= 254) or uint16 (hard
 //     capacity: clamped to [0, Q+1]; soft: kept exactly up to the staging
@@ -722,10 +723,11 @@ __global__ void __launch_bounds__(kThreads, 1) split_pipe_kernel(PipeArgs a) {
     // Chunk x: wait for its stage, narrow + permute its rows into the slot
     // (rows past S become zero demands: their lanes run on them, outputs
     // dropped), count it toward the item (the warp completing the item
-    // publishes it), free the stage.  Thread t owns words k = kw + 128 j of
-    // the rows of parity t / 128, their columns in registers per tour (one
-    // word per thread for rows of up to 512 bytes: the slowest thread sets
-    // the pace of the stage).
+    // publishes it), free the stage.  Thread t owns words k = kw0 + 128 j of
+    // the rows rfirst, rfirst + rstep, ... (the mapping is chosen per tour
+    // below), their columns in registers per tour (one word per thread for
+    // rows of up to 512 bytes: the slowest thread sets the pace of the
+    // stage).
     const int t = (int)threadIdx.x - (kDp + 1) * 32;
     constexpr int kHalf = kNarrowThreads / 2;                       // 128
     constexpr int kWordsMax = kPipeMaxN * (int)sizeof(QT) / 4;      // words per row at most
