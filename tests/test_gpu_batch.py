@@ -184,6 +184,45 @@ def test_batch_every_autotune_shape_bit_identical(Q, qhi):
     plan.close()
 
 
+@pytest.mark.parametrize("Q,qhi,lengths", [
+    (150, 40, [337, 340, 341, 344, 85, 84, 2, 1]),    # uint8 rows: 85 words at n = 340
+    (600, 90, [169, 170, 171, 172, 43, 42, 2, 1]),    # uint16 rows: 85 words at n = 170
+    (150, 40, [128, 127, 100, 64, 33, 32, 17, 5]),    # every tour n <= 128: six 16 KB stages
+])
+def test_batch_pipe_narrowing_boundaries(Q, qhi, lengths):
+    """Tours on both sides of the narrowing's switch from row groups over all
+    its threads (rows of at most 85 words) to one thread per word position,
+    and a plan of short tours only (six producer stages): the pipelined
+    plan's costs are the per-tour PLAIN kernel's bits, its means the same to
+    1e-12, with a ragged last tile (S = 164) and one demand above Q."""
+    S = 164
+    rng = np.random.default_rng(Q + len(lengths) + lengths[0])
+    n = np.array(lengths, np.int32)
+    tours = [(rng.permutation(k) + 1).astype(np.int32) for k in n]
+    coords = [np.concatenate([[[50, 50]], rng.uniform(0, 100, (k, 2))]).astype(np.float32)
+              for k in n]
+    dem = [rng.integers(1, qhi + 1, size=(S, k)).astype(np.int32) for k in n]
+    dem[1][S - 1, n[1] // 2] = Q + 1
+    plan, _ = _plan(n, tours, coords, dem, Q, S)
+    plan.configure(-2, 16, 1)
+    assert plan.info()["warps_per_cta"] == -2
+    api().status()
+    costs, means = plan.run()
+    torch.cuda.synchronize()
+    for b in range(len(n)):
+        p = api().split_eval(torch.from_numpy(tours[b]).cuda(), Q,
+                             torch.from_numpy(dem[b]).cuda(),
+                             coords=torch.from_numpy(coords[b]).cuda(), algo="plain")
+        torch.cuda.synchronize()
+        assert torch.equal(costs[b], p["cost"]), b
+        m, pm = float(means[b]), float(p["mean"])
+        assert (np.isinf(m) and np.isinf(pm)) or abs(m - pm) <= 1e-12 * abs(pm), b
+    st = api().status()
+    assert np.isinf(float(means[1])) and st & api().FLAG_INFEASIBLE
+    assert st & api().FLAG_DEVICE_CHECK == 0
+    plan.close()
+
+
 def test_batch_infeasible_and_fallback():
     """Scenarios with a demand above Q and with zero-cost ties (deque ring
     overflow -> plain fallback) inside a batch."""

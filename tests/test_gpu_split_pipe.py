@@ -98,12 +98,16 @@ def test_pipe_edge_cases(case):
         assert sdp().status() & sdp().FLAG_DEVICE_CHECK == 0
 
 
-@pytest.mark.parametrize("n", [1, 2, 15, 16, 17, 31, 33, 64, 100, 250, 500, 513, 1000, 1024])
+@pytest.mark.parametrize("n", [1, 2, 15, 16, 17, 31, 33, 64, 100, 170, 171, 250, 340, 341,
+                               500, 513, 1000, 1024])
 @pytest.mark.parametrize("Q,hi", [(60, 20), (600, 80)])
 def test_pipe_bit_identical_to_deque_and_plain(n, Q, hi):
     """Every block / tail split of the row, uint8 and uint16 rows, uint16
     predecessor pairs on odd and even n and int32 predecessors give the bits
-    of the other two kernels; S = 257 leaves a ragged last tile."""
+    of the other two kernels; S = 257 leaves a ragged last tile.  n = 170 /
+    171 (uint16) and 340 / 341 (uint8) are the rows of 85 and 86 words on
+    either side of the narrowing's switch from row groups over all its
+    threads to one thread per word position."""
     tour, xy, _, q = _case(100 + n, n, 257, Q, 1, hi)
     args = (_cuda(tour), Q, _cuda(q))
     for preds in ("u16", "i32"):
