@@ -66,7 +66,8 @@ extern "C" {
 #define SDP_FLAG_FALLBACK 8u       /* a scenario took the per-scenario path */
 
 /* Split algorithms */
-#define SDP_ALGO_AUTO 0   /* PIPE where it applies (hard capacity, n <= 1024,
+#define SDP_ALGO_AUTO 0   /* PIPE where it applies (hard or soft capacity,
+                             n <= 1024,
                              Q <= 32767, 16-byte aligned device demands or
                              host demands, warps_per_cta = 0, ring 0 or 16);
                              else DEQUE when a demand row fits 512 bytes
@@ -98,9 +99,11 @@ extern "C" {
                              segments.  Hard or soft capacity; needs
                              1 <= n <= 1024, Q <= 32767 and 16-byte aligned
                              demands; the
-                             workspace grows by about
+                             workspace grows by at most
                              SMs * 32 * 32 * ceil32(n * qb) bytes (qb = 1 for
-                             Q <= 254, else 2): 78 MB at n = 500 on 152 SMs */
+                             Q <= 254, else 2): 78 MB at n = 500 on 152 SMs,
+                             less when a CTA's share of the tiles is below
+                             16 (two slots per tile of its share, 2 to 32) */
 
 /* predecessor dtypes */
 #define SDP_PRED_U16 1    /* uint16, requires n < 65535 */
