@@ -344,8 +344,8 @@ int sdp_split_plan_create(const sdp_split_batch_desc* d, sdp_plan** out);
  * timing, a miss appends the new choice. */
 int sdp_plan_autotune(sdp_plan* p, void* stream, const char* cache_path);
 /* Enqueues one evaluation of the whole batch on `stream`: tour preparation,
- * the persistent kernel, the fallback for flagged scenarios and the per-tour
- * FP64 means.  The first call captures these launches into a CUDA graph;
+ * the persistent kernel, the recomputation of the scenarios it flagged (one
+ * warp per scenario, the plain kernel's bits) and the per-tour FP64 means.  The first call captures these launches into a CUDA graph;
  * later calls replay it (a new launch shape from autotune re-captures). */
 int sdp_plan_run(sdp_plan* p, void* stream);
 /* Device time of the persistent kernel in the most recent sdp_plan_run
