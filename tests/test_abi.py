@@ -116,3 +116,38 @@ def test_product_path_has_no_oracle_import():
             assert "import paper_2602_05179_gb300" not in src, f
             assert "from paper_2602_05179_gb300" not in src, f
             assert "sdp.h" not in src and "StepRec" not in src, f
+
+
+def test_product_path_raises_without_its_library(monkeypatch, tmp_path):
+    """No CPU path: with libsdp.so absent every operator call raises before
+    computing anything."""
+    import torch
+    from paper_2602_05179_gb300 import api
+    monkeypatch.setattr(api, "_LIB_PATH", str(tmp_path / "libsdp.so"))
+    monkeypatch.setattr(api, "_lib", None)
+    tour = torch.arange(1, 6, dtype=torch.int32)
+    q = torch.ones((4, 5), dtype=torch.int32)
+    xy = torch.zeros((6, 2), dtype=torch.float32)
+    with pytest.raises(RuntimeError, match="missing"):
+        api.split_eval(tour, 10, q, coords=xy)
+    with pytest.raises(RuntimeError, match="missing"):
+        api.reinsert_eval(3, 10, 5, 1.0, 2.0, 0.0, torch.ones(3), torch.ones((4, 3),
+                          dtype=torch.int32))
+    with pytest.raises(RuntimeError, match="missing"):
+        api.status()
+
+
+def test_product_path_refuses_host_tensors(lib):
+    """With the library loaded, tensors in ordinary host memory are refused
+    (only device memory, or pinned host demands read by the kernels, is
+    accepted): nothing falls back to a CPU computation."""
+    import torch
+    from paper_2602_05179_gb300 import api
+    tour = torch.arange(1, 6, dtype=torch.int32)
+    q = torch.ones((4, 5), dtype=torch.int32)
+    xy = torch.zeros((6, 2), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        api.split_eval(tour, 10, q, coords=xy)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        api.reinsert_eval(3, 10, 5, 1.0, 2.0, 0.0, torch.ones(3), torch.ones((4, 3),
+                          dtype=torch.int32))
