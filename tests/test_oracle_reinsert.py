@@ -133,6 +133,35 @@ def test_reinsert_forward_equals_backward_on_workload_sample():
     assert abs(r["mean"] - r["value"].mean()) <= 1e-12 * r["mean"]
 
 
+def test_reinsert_ties_prefer_no_delivery_by_brute_force():
+    """Reading R6: with integer costs every action value is exact, so ties
+    between delivering and not delivering are exact.  Along the oracle's
+    path each day's decision must be to deliver exactly when delivering is
+    strictly cheaper than not, both values with every later day optimal
+    found by simulating every continuation."""
+    ties = 0
+    for seed in range(30):
+        rng = np.random.default_rng(2800 + seed)
+        T = int(rng.integers(1, 6))
+        U = int(rng.integers(1, 6))
+        h, p, c = float(rng.integers(0, 2)), float(rng.integers(0, 3)), float(rng.integers(0, 2))
+        fixed = rng.integers(0, 3, size=T).astype(np.float32)
+        cons = rng.integers(0, U + 2, size=T).astype(np.int32)
+        I0 = int(rng.integers(0, U + 1))
+        pol = oracle.reinsert(T, U, I0, h, p, c, fixed, cons[None, :])["policy"][0]
+        I = I0
+        for t in range(T):
+            v = brute.reinsert_action_values(T, U, h, p, c, fixed, cons, t, I)
+            if I == U:
+                expect = 0
+            else:
+                ties += v[0] == v[1]
+                expect = 1 if v[1] < v[0] else 0
+            assert pol[t] == expect, (seed, t, I, v)
+            I = max(0, (U if pol[t] else I) - int(cons[t]))
+    assert ties >= 5
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_reinsert_margin_by_brute_force(seed):
     """The margin at (t, I) -- the relative gap between the two actions,

@@ -180,6 +180,41 @@ def test_split_margin_definition():
                                                           rel=1e-9, abs=1e-15)
 
 
+def test_split_ties_and_infeasible_positions_by_brute_force():
+    """Readings S3 and S4: with travel costs of 0, 1 or 2 every route cost
+    and every sum of them is exact, so ties between predecessors are exact.
+    pred(i) must be the smallest p among the optimal candidates for J(i)
+    that brute force lists (each candidate = the best split of the first p
+    customers plus the route s_{p+1..i}), and -1 at every position that no
+    feasible split reaches (a demand above Q at or before it)."""
+    ties = unreachable = 0
+    for seed in range(30):
+        rng = np.random.default_rng(2700 + seed)
+        n = int(rng.integers(2, 9))
+        Q = int(rng.integers(2, 8))
+        d = rng.integers(0, 3, size=(n + 1, n + 1)).astype(np.float32)
+        np.fill_diagonal(d, 0.0)
+        tour = (rng.permutation(n) + 1).astype(np.int32)
+        q = rng.integers(0, Q + 1, size=n).astype(np.int32)
+        if seed % 3 == 0:
+            q[tour[int(rng.integers(0, n))] - 1] = Q + 1
+        r = oracle.split(tour, Q, q[None, :], dist=d)
+        pred = r["pred"][0]
+        for i in range(1, n + 1):
+            cands = brute.split_candidates(list(tour), list(q), Q,
+                                           lambda a, b: float(d[a, b]), i)
+            if not cands:
+                unreachable += 1
+                assert pred[i - 1] == -1, (seed, i)
+                continue
+            best = min(v for v, _ in cands)
+            opt = [p for v, p in cands if v == best]
+            ties += len(opt) > 1
+            assert pred[i - 1] == min(opt), (seed, i, opt)
+        assert math.isinf(r["cost"][0]) == (seed % 3 == 0)
+    assert ties >= 10 and unreachable >= 10
+
+
 # ---------------------------------------------------------------- gradient
 def test_split_gradient_identities_and_fd():
     """d mean / d dist from backtracked arc usage equals central finite

@@ -144,3 +144,31 @@ def test_soft_split_margin_by_brute_force(seed):
             assert math.isinf(m)
         else:
             assert m == pytest.approx((vals[1] - vals[0]) / abs(vals[0]), rel=1e-9, abs=1e-12), i
+
+
+def test_soft_split_ties_by_brute_force():
+    """Reading S4 for soft capacity: with travel costs of 0, 1 or 2 and an
+    integer penalty every candidate value is exact, so ties are exact; pred(i)
+    must be the smallest p among the optimal candidates for J(i) that brute
+    force lists (every route allowed, beta per unit of load above Q)."""
+    ties = overloaded = 0
+    for seed in range(30):
+        rng = np.random.default_rng(2750 + seed)
+        n = int(rng.integers(2, 9))
+        Q = int(rng.integers(1, 7))
+        beta = float(rng.integers(1, 4))
+        d = rng.integers(0, 3, size=(n + 1, n + 1)).astype(np.float32)
+        np.fill_diagonal(d, 0.0)
+        tour = (rng.permutation(n) + 1).astype(np.int32)
+        q = rng.integers(0, Q + 3, size=n).astype(np.int32)
+        overloaded += int((q > Q).any())
+        r = oracle.split_soft(tour, Q, beta, q[None, :], dist=d)
+        pred = r["pred"][0]
+        for i in range(1, n + 1):
+            cands = brute.split_candidates(list(tour), list(q), Q,
+                                           lambda a, b: float(d[a, b]), i, beta=beta)
+            best = min(v for v, _ in cands)
+            opt = [p for v, p in cands if v == best]
+            ties += len(opt) > 1
+            assert pred[i - 1] == min(opt), (seed, i, opt)
+    assert ties >= 20 and overloaded >= 10
