@@ -1,11 +1,12 @@
 """The oracle's pins catch plausible mistakes.  Each mutant below is a copy of
-oracle/sdp_oracle.c with one mistake planted in it -- a dropped term, a wrong
-sign, an index off by one, a transposed operand, a tie rule or a margin
-taken the other way -- compiled on the CPU into a library of its own.  The
-pin files (tests/test_oracle_*.py) then run, in a child process, against
-that library instead of the real one, and at least one pin must fail.  A
-control copy with no mistake must pass them all.  No mutant reads or writes
-outside its arrays, so each one only computes a wrong answer."""
+oracle/sdp_oracle.c (compiled on the CPU into a library of its own) or of
+oracle/saa.py (executed into the imported module) with one mistake planted
+in it -- a dropped term, a wrong sign, an index off by one, a transposed
+operand, a tie rule or a margin taken the other way.  The pin files
+(tests/test_oracle_*.py) then run, in a child process, against that copy
+instead of the real one, and at least one pin must fail.  A control copy
+with no mistake must pass them all.  No mutant reads or writes outside its
+arrays, so each one only computes a wrong answer."""
 import os
 import shutil
 import subprocess
@@ -13,13 +14,16 @@ import sys
 import tempfile
 from concurrent.futures import ThreadPoolExecutor
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE_C = os.path.join(ROOT, "oracle", "sdp_oracle.c")
+ORACLE_SAA = os.path.join(ROOT, "oracle", "saa.py")
 PIN_FILES = ["tests/test_oracle_split.py", "tests/test_oracle_split_soft.py",
              "tests/test_oracle_split_fleet.py", "tests/test_oracle_reinsert.py",
              "tests/test_oracle_reinsert_routes.py", "tests/test_oracle_saa.py"]
 
-# (name, text in the oracle, replacement, which occurrence of the text)
+# (name, text in oracle/sdp_oracle.c, replacement, which occurrence of the text)
 MUTANTS = [
     # Split (Eq. eqdpA): route cost W, capacity window, arcs, ties, margin
     ("split: return leg dropped", "const double W = cost_ab(c, 0, sp1) + inner + back;",
@@ -79,6 +83,24 @@ MUTANTS = [
     ("routes: policy label", "a = (uint8_t)(r + 1);", "a = (uint8_t)(r + 1 + (r > 0));", 0),
 ]
 
+# the same for oracle/saa.py (the SAA search: SplitMix64, moves, selection)
+SAA_MUTANTS = [
+    ("saa: counter off by one", "z = (seed + (c + 1) * GAMMA) & M64",
+     "z = (seed + c * GAMMA) & M64", 0),
+    ("saa: finaliser shift", "z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64",
+     "z = ((z ^ (z >> 31)) * 0xBF58476D1CE4E5B9) & M64", 0),
+    ("saa: position a from the high word", "a = (z & 0xFFFFFFFF) % n", "a = (z >> 32) % n", 0),
+    ("saa: b skips a strictly", "if b >= a:\n        b += 1", "if b > a:\n        b += 1", 0),
+    ("saa: kind from the wrong byte", "((z >> 32) & 0xFF)", "((z >> 33) & 0xFF)", 0),
+    ("saa: 2-opt one short", "t[a:b + 1] = t[a:b + 1][::-1]", "t[a:b] = t[a:b][::-1]", 0),
+    ("saa: relocate one further", "t.insert(b, x)", "t.insert(b + 1, x)", 0),
+    ("saa: equal score accepted", "take = ms[kbest] < m0", "take = ms[kbest] <= m0", 0),
+    ("saa: last minimum taken", "kbest = int(np.argmin(ms))",
+     "kbest = len(ms) - 1 - int(np.argmin(ms[::-1]))", 0),
+    ("saa: trace of a rejected step", "trace.append(ms[kbest] if take else m0)",
+     "trace.append(ms[kbest])", 0),
+]
+
 
 def _replace_nth(src, old, new, occ):
     at = -1
@@ -88,24 +110,34 @@ def _replace_nth(src, old, new, occ):
     return src[:at] + new + src[at + len(old):]
 
 
-def run_mutant(m):
-    """Compile the oracle with mutant m planted (None: unchanged) and run the
-    pin files against it in a child process: (exit code, last output line)."""
+def run_mutant(m, target=ORACLE_C):
+    """Plant mutant m (None: no change) in a copy of target -- the C oracle,
+    compiled into a library of its own, or the SAA oracle, executed into the
+    imported module -- and run the pin files against it in a child process:
+    (exit code, last output line)."""
     name, old, new, occ = m
-    with open(ORACLE_C) as f:
+    with open(target) as f:
         src = f.read()
     if old is not None:
         src = _replace_nth(src, old, new, occ)
     d = tempfile.mkdtemp(prefix="oracle_mutant_")
     try:
-        c = os.path.join(d, "sdp_oracle.c")
+        c = os.path.join(d, os.path.basename(target))
         with open(c, "w") as f:
             f.write(src)
-        lib = os.path.join(d, "liboracle.so")
-        script = ("import sys, pytest, oracle\n"
-                  f"oracle._SRC = {c!r}\noracle._LIB_PATH = {lib!r}\noracle._lib = None\n"
-                  "sys.exit(pytest.main(['-x', '-q', '-m', 'not gpu', '-p', 'no:cacheprovider', "
-                  f"'-W', 'ignore', *{PIN_FILES!r}]))\n")
+        script = "import sys, pytest, oracle, oracle.saa\n"
+        if target == ORACLE_C:
+            lib = os.path.join(d, "liboracle.so")
+            script += (f"oracle._SRC = {c!r}\noracle._LIB_PATH = {lib!r}\n"
+                       "oracle._lib = None\n")
+        else:
+            # the package re-exports the search's functions: rebind those too
+            script += (f"exec(compile(open({c!r}).read(), oracle.saa.__file__, 'exec'), "
+                       "oracle.saa.__dict__)\n"
+                       "for k in ('apply_move', 'draw_move', 'saa_search', 'splitmix64'):\n"
+                       "    setattr(oracle, k, getattr(oracle.saa, k))\n")
+        script += ("sys.exit(pytest.main(['-x', '-q', '-m', 'not gpu', '-p', 'no:cacheprovider', "
+                   f"'-W', 'ignore', *{PIN_FILES!r}]))\n")
         env = dict(os.environ, OMP_NUM_THREADS="2")
         p = subprocess.run([sys.executable, "-c", script], cwd=ROOT, env=env,
                            capture_output=True, text=True, timeout=900)
@@ -116,14 +148,16 @@ def run_mutant(m):
 
 
 def test_every_planted_mistake_fails_a_pin():
+    jobs = [(m, ORACLE_C) for m in MUTANTS] + [(m, ORACLE_SAA) for m in SAA_MUTANTS]
     with ThreadPoolExecutor(min(8, os.cpu_count() or 1)) as ex:
-        res = list(ex.map(run_mutant, MUTANTS))
-    survived = [(m[0], tail) for m, (rc, tail) in zip(MUTANTS, res) if rc == 0]
-    broken = [(m[0], rc, tail) for m, (rc, tail) in zip(MUTANTS, res) if rc not in (0, 1)]
+        res = list(ex.map(lambda j: run_mutant(*j), jobs))
+    survived = [(j[0][0], tail) for j, (rc, tail) in zip(jobs, res) if rc == 0]
+    broken = [(j[0][0], rc, tail) for j, (rc, tail) in zip(jobs, res) if rc not in (0, 1)]
     assert not broken, broken   # 1 = a pin failed; anything else is a harness error
     assert not survived, survived
 
 
-def test_unplanted_copy_passes_every_pin():
-    rc, tail = run_mutant(("control", None, None, 0))
+@pytest.mark.parametrize("target", [ORACLE_C, ORACLE_SAA])
+def test_unplanted_copy_passes_every_pin(target):
+    rc, tail = run_mutant(("control", None, None, 0), target)
     assert rc == 0, tail

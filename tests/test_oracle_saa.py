@@ -114,3 +114,67 @@ def test_search_ends_in_a_local_optimum():
     assert all(_score(u, Q, q, xy) >= final for u in neighbourhood(list(r["tour"])))
     allbest = min(_score(p, Q, q, xy) for p in itertools.permutations(range(1, 5)))
     assert final >= allbest
+
+
+def test_draws_worked_from_the_published_outputs():
+    """The draw rule worked by hand on the SplitMix64 known-answer outputs of
+    state 1234567 (tests/golden/splitmix64_1234567.json).  Output 0, z =
+    6457827717110365317: low word 4211670149, z >> 40 = 5873360, byte
+    (z >> 32) & 255 = 23.  Output 1, z = 3203168211198807973: 1481904037,
+    2913264, 132.  Output 2, z = 9817491932198370423: 2750577783, 8928956,
+    229.  a = low word mod n; b = (z >> 40) mod (n - 1), plus one when b >= a;
+    kind = byte mod (kinds enabled), in the order 2-opt, relocate, swap;
+    2-opt orders a < b."""
+    s = load("splitmix64_1234567.json")["seed"]
+    assert oracle.draw_move(s, 0, 10) == ("swap", 9, 5)       # 23 mod 3 = 2; b = 5 < a
+    assert oracle.draw_move(s, 0, 7) == ("swap", 1, 3)        # a = 1; b = 2 >= a -> 3
+    assert oracle.draw_move(s, 1, 10) == ("2opt", 0, 7)       # 132 mod 3 = 0; (7, 0) ordered
+    assert oracle.draw_move(s, 1, 7) == ("2opt", 0, 5)        # a = 5, b = 0
+    assert oracle.draw_move(s, 2, 10) == ("relocate", 3, 2)   # 229 mod 3 = 1; b = 2 < a = 3
+    assert oracle.draw_move(s, 2, 7) == ("relocate", 2, 3)    # a = 2; b = 2 >= a -> 3
+    two = ("2opt", "swap")
+    assert oracle.draw_move(s, 0, 10, two) == ("swap", 9, 5)  # 23 mod 2 = 1
+    assert oracle.draw_move(s, 1, 10, two) == ("2opt", 0, 7)  # 132 mod 2 = 0
+    assert oracle.draw_move(s, 2, 10, two) == ("swap", 3, 2)  # 229 mod 2 = 1
+
+
+def _ray_instance(seed, n, S):
+    """Customers on a ray from the depot at integer distances (3, 6, ...):
+    every travel cost is an exact integer, so every score is exact and equal
+    scores are exact ties.  Q holds every scenario's whole demand."""
+    rng = np.random.default_rng(seed)
+    xy = np.zeros((n + 1, 2), np.float32)
+    xy[1:, 0] = 3.0 * (rng.permutation(n) + 1)
+    q = rng.integers(1, 4, size=(S, n)).astype(np.int32)
+    return xy, q, int(q.sum(axis=1).max()), (np.argsort(xy[1:, 0]) + 1).astype(np.int32)
+
+
+def test_search_accepts_strict_improvements_only():
+    """The tour out along the ray scores 2 max x, the least any tour can; many
+    of its neighbours (a suffix reversed, a customer moved to the way back)
+    score exactly that too.  A neighbour replaces the current tour only when
+    strictly better, so none is taken."""
+    xy, q, Q, out = _ray_instance(5, 6, 4)
+    r = oracle.saa_search(out, Q, q, xy, 30, 3, 11)
+    m = r["means"]
+    assert (r["accepted"] == -1).all() and list(r["tour"]) == list(out)
+    assert (m[:, 1:] >= m[:, :1]).all()
+    assert (m[:, 1:] == m[:, :1]).sum() >= 3          # exact ties with the current tour
+    assert np.array_equal(r["trace"], m[:, 0])
+
+
+def test_search_takes_the_first_of_equal_best_neighbours():
+    """From a zigzag tour along the ray several neighbours often reach the
+    same best score (one move drawn twice, or two moves giving tours of equal
+    cost); the accepted neighbour must be the first of them."""
+    xy, q, Q, out = _ray_instance(6, 6, 4)
+    zig = out[[0, 5, 1, 4, 2, 3]]
+    r = oracle.saa_search(zig, Q, q, xy, 40, 4, 12)
+    tied_and_taken = 0
+    for t in range(4):
+        m0, ms = r["means"][t][0], list(r["means"][t][1:])
+        best = min(ms)
+        first = ms.index(best)
+        assert r["accepted"][t] == (first if best < m0 else -1), t
+        tied_and_taken += best < m0 and ms.count(best) > 1
+    assert tied_and_taken >= 1
