@@ -460,7 +460,10 @@ int check_ws(void* ws, size_t have, size_t need) {
   return SDP_OK;
 }
 
-// Runs the DEQUE kernel (+ plain fallback) or the PLAIN kernel over all S.
+// Runs the chosen DP kernel over all S, then recomputes the scenarios it
+// flagged (one warp each where split_rescue.cu applies: hard capacity, no
+// route histogram; else the plain kernel over the flagged list), or runs the
+// PLAIN kernel over all S.
 int run_split_core(const sdp_split_args* a, const SplitWs& w, uint32_t* status,
                    unsigned long long* hist, cudaStream_t st) {
   int algo = resolve_algo(a);

@@ -6,9 +6,10 @@
 // tours by decreasing n_b), the concatenated tour records, the per-tour D(n)
 // in FP64, the work-queue counter, the fallback list and its scratch.  One
 // run = [tour prep for every tour (also resets the counter) -> persistent
-// DEQUE kernel over (tour, 32-scenario tile) items -> plain fallback for
-// flagged scenarios -> per-tour FP64 means], captured once in a CUDA graph
-// and replayed.  The persistent kernel is the pipelined one
+// kernel over (tour, 32-scenario tile) items -> recomputation of the
+// scenarios it flagged (one warp each, split_rescue.cu, where the longest
+// tour fits its shared memory; else the plain per-scenario kernel) ->
+// per-tour FP64 means], captured once in a CUDA graph and replayed.  The persistent kernel is the pipelined one
 // (split_pipe_kernel: producer warps narrow each tile's rows into tour order
 // in an L2-resident slot ring, 23 DP warps per SM) when the demand offsets
 // allow bulk copies and every tour has n <= 1024, else the streaming one
@@ -373,7 +374,7 @@ int sdp_plan_info(const sdp_plan* p, int32_t* warps_per_cta, int32_t* ring, int3
 namespace sdp {
 // min_ring: the smallest deque ring timed.  Plans whose tours change between
 // runs (the SAA search) take 16: a ring sized on the tours it was timed on can
-// overflow on later ones, and overflowed scenarios go to the plain fallback.
+// overflow on later ones, and every overflowed scenario is recomputed.
 int plan_autotune(sdp_plan* p, void* stream, const char* cache_path, int min_ring) {
   if (!p) return pfail(SDP_ERR_INVALID_ARG, "plan is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
