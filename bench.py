@@ -599,9 +599,10 @@ def op_routes(c, out):
 
 
 def op_adjoint(c, out):
-    """Split adjoint n=300, S=10^5: the fused forward + on-chip backtrack
-    against the plain kernel's forward with stored predecessors + their
-    backtrack."""
+    """Split adjoint n=300, S=10^5: the fused forward + on-chip backtrack,
+    one step = a CUDA graph replay of the whole adjoint (the kernel's own
+    time from an eager call through the profile hook), against the plain
+    kernel's forward with stored predecessors + their backtrack."""
     import torch
     ad = c.wl.ADJOINT_C5
     tour, xy, distm = c.wl.split_tour(ad)
@@ -612,8 +613,12 @@ def op_adjoint(c, out):
     arcs = int(tot)
     g1 = torch.ones((), dtype=torch.float32, device=c.dev)
     fn = lambda: c.api.split_backward(t, ad.Q, q, dm, g1, want_hist=True)
-    ms, kms = _timed(fn, c.steps or 20)
+    eager_ms, kms = _timed(fn, c.steps or 20)
+    graphed = c.api.GraphedSplitBackward(t, ad.Q, q, dm, g1, want_hist=True)
+    ms, _ = _timed(graphed.run, c.steps or 20, events=False)
     g, hist = fn()
+    torch.cuda.synchronize()
+    graph_same = bool(torch.equal(graphed.grad, g) and torch.equal(graphed.hist, hist))
     byts = ad.S * ad.n * 4
 
     def plain():
@@ -624,6 +629,9 @@ def op_adjoint(c, out):
     gp, hp = plain()
     line = {"value": arcs / (ms / 1e3), "unit": "arcs/s (forward+backtrack)",
             "ms_per_step": ms, "kernel_ms": kms, "kernel": "split_tmem_adj_kernel",
+            "launch": "CUDA graph replay of the step (hist reset, tour prep, DP kernel, "
+                      "recompute of flagged scenarios, gradient assembly)",
+            "eager_ms_per_step": eager_ms, "graph_bits_equal_eager": graph_same,
             "roofline": c.hbm_roof(byts, kms),
             "alu_frac": 2 * arcs / (kms / 1e3) / c.p_alu,
             "vs_plain": {"path": "plain forward with int32 predecessors + backtrack kernel",

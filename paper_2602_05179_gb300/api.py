@@ -392,6 +392,39 @@ def split_backward(tour, Q, demands, dist, grad_mean, *, pred=None, pred_dtype=N
     return grad, hist
 
 
+class GraphedSplitBackward:
+    """split_backward (fused forward + backtrack) captured once in a CUDA
+    graph and replayed: the hist reset, tour preparation, DP kernel, the
+    recomputation of flagged scenarios and the gradient assembly go to the
+    device as one launch per step, without the per-call host work.
+
+    The graph reads tour, demands, dist and grad_mean where they were at
+    capture, so refill those tensors in place between replays (same shapes);
+    run() returns the same grad (and hist) tensors every time, overwritten
+    by each replay.  One warm-up call on a side stream sets up the library's
+    per-device state before the capture."""
+
+    def __init__(self, tour, Q, demands, dist, grad_mean, *, want_hist=False):
+        _load()
+        gm = grad_mean.reshape(()).to(device=tour.device, dtype=torch.float32)
+        self._keep = (tour, demands, dist, gm)
+        args = (tour, Q, demands, dist, gm)
+        side = torch.cuda.Stream(device=tour.device)
+        side.wait_stream(torch.cuda.current_stream(tour.device))
+        with torch.cuda.stream(side):
+            split_backward(*args, want_hist=want_hist)
+        torch.cuda.current_stream(tour.device).wait_stream(side)
+        torch.cuda.synchronize(tour.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            self.grad, self.hist = split_backward(*args, want_hist=want_hist)
+
+    def run(self):
+        """Replays the step on the current stream; returns (grad, hist)."""
+        self.graph.replay()
+        return self.grad, self.hist
+
+
 class SplitMeanCost(torch.autograd.Function):
     """mean_s J_s(n) as a differentiable function of the travel-cost matrix.
 

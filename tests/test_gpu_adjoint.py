@@ -318,3 +318,32 @@ def test_adjoint_equals_central_differences_of_the_oracle_mean():
         assert g[a, b] == pytest.approx(fd, rel=1e-6, abs=1e-7), (a, b)
         checked += 1
     assert checked >= 0.9 * len(entries)
+
+
+@pytest.mark.parametrize("n,S", [(60, 3000), (300, 20000)])
+def test_graphed_backward_replays_the_eager_bits(n, S):
+    """GraphedSplitBackward (the fused adjoint step captured in a CUDA graph):
+    every replay gives the eager call's gradient and route counts bit for
+    bit; after the demands are refilled in place a replay gives the eager
+    result for the new demands; and the gradient scales exactly with
+    grad_mean (a factor of 4 is a power of two)."""
+    tour, dist, q1 = _case(40 + n, n, S, 100, 9.0)
+    _, _, q2 = _case(41 + n, n, S, 100, 9.0)
+    t, d, q = _cuda(tour), _cuda(dist), _cuda(q1).clone()
+    gm = torch.tensor(0.5, dtype=torch.float32, device="cuda")
+    g = sdp().GraphedSplitBackward(t, 100, q, d, gm, want_hist=True)
+    eg, eh = sdp().split_backward(t, 100, q, d, gm, want_hist=True)
+    for _ in range(3):
+        gg, gh = g.run()
+        torch.cuda.synchronize()
+        assert torch.equal(gg, eg) and torch.equal(gh, eh)
+    q.copy_(_cuda(q2))
+    eg2, eh2 = sdp().split_backward(t, 100, q, d, gm, want_hist=True)
+    gg, gh = g.run()
+    torch.cuda.synchronize()
+    assert torch.equal(gg, eg2) and torch.equal(gh, eh2) and not torch.equal(eh2, eh)
+    gm.fill_(2.0)
+    gg, _ = g.run()
+    torch.cuda.synchronize()
+    assert torch.equal(gg, eg2 * 4)
+    assert sdp().status() & sdp().FLAG_DEVICE_CHECK == 0
