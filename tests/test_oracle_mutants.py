@@ -81,6 +81,37 @@ MUTANTS = [
      "if (cap[(size_t)t * K + r] <= q) continue;", 0),
     ("routes: ties to the last route", "if (dv < best) {", "if (dv <= best) {", 0),
     ("routes: policy label", "a = (uint8_t)(r + 1);", "a = (uint8_t)(r + 1 + (r > 0));", 0),
+    ("routes: margin halved", "(den > 0 ? (second - best) / den : 0.0)",
+     "(den > 0 ? (second - best) / (2 * den) : 0.0)", 0),
+    ("routes: end state from I", "const int64_t x1 = (int64_t)U - dt;",
+     "const int64_t x1 = (int64_t)I - dt;", 0),
+    ("routes: backtrack state", "const int64_t x = (a ? U : I) - d[t];",
+     "const int64_t x = (a ? U - 1 : I) - d[t];", 0),
+    # the sample means, the fleet margin along the path, the last layer
+    ("split: mean over S - 1", "*mean_out = S > 0 ? sum / (double)S : 0.0;",
+     "*mean_out = S > 1 ? sum / (double)(S - 1) : 0.0;", 0),
+    ("fleet: mean over S - 1", "*mean_out = S > 0 ? sum / (double)S : 0.0;",
+     "*mean_out = S > 1 ? sum / (double)(S - 1) : 0.0;", 1),
+    ("soft: mean over S - 1", "*mean_out = S > 0 ? sum / (double)S : 0.0;",
+     "*mean_out = S > 1 ? sum / (double)(S - 1) : 0.0;", 2),
+    ("reinsert: mean over S - 1", "*mean_out = S > 0 ? sum / (double)S : 0.0;",
+     "*mean_out = S > 1 ? sum / (double)(S - 1) : 0.0;", 3),
+    ("fleet: path margin ignored", "mg = fmin(mg, M[k * w + i]);", "mg = mg;", 0),
+    ("fleet: last layer ignored", "for (int k = 1; k <= K; ++k) {\n    const double v",
+     "for (int k = 1; k < K; ++k) {\n    const double v", 0),
+    # the forward recursion, the terminal and table costs, the C_0 table, arcs
+    ("forward: last action overwrites", "if (c < *a) *a = c;", "*a = c;", 0),
+    ("reinsert: value0 of day 1", "for (int I = 0; I < W; ++I) value0[I] = C[I];",
+     "for (int I = 0; I < W; ++I) value0[I] = C[(T > 1 ? W : 0) + I];", 0),
+    ("reinsert: terminal cost 1", "for (int I = 0; I < W; ++I) C[(size_t)T * W + I] = 0.0;",
+     "for (int I = 0; I < W; ++I) C[(size_t)T * W + I] = 1.0;", 0),
+    ("reinsert: table end cost shifted",
+     "if (m->H) return m->H[x > 0 ? (x > m->U ? m->U : x) : 0];",
+     "if (m->H) return m->H[x > 1 ? (x > m->U ? m->U : x - 1) : 0];", 0),
+    ("split: arcs miss p = 0",
+     "++narcs;\n      if (p < i - 1) inner += cost_ab(c, sp1, tour[p + 1]);\n      if (isinf",
+     "narcs += p > 0;\n      if (p < i - 1) inner += cost_ab(c, sp1, tour[p + 1]);\n      if (isinf",
+     0),
 ]
 
 # the same for oracle/saa.py (the SAA search: SplitMix64, moves, selection)

@@ -120,3 +120,45 @@ def test_fleet_monotone_in_K_and_routes_consistent():
             assert r[-1] + 1 == o["nroutes"][s]
             loads = np.bincount(r, weights=q[s][tour - 1])
             assert (loads <= Q).all()
+
+
+def test_fleet_margin_is_positive_exactly_when_the_optimum_is_unique():
+    """The margin is the tightest relative gap over the choices that make up
+    the optimal split (the number of routes, then each route's start along
+    the backtrack), so it certifies uniqueness.  With travel costs of 0, 1 or
+    2 every sum is exact: margin > 0 if and only if brute force finds exactly
+    one optimal split into at most K routes (+inf where none fits)."""
+    unique = multiple = 0
+    for seed in range(40):
+        rng = np.random.default_rng(2900 + seed)
+        n = int(rng.integers(2, 8))
+        Q = int(rng.integers(2, 9))
+        K = int(rng.integers(1, n + 1))
+        d = rng.integers(0, 3, size=(n + 1, n + 1)).astype(np.float32)
+        np.fill_diagonal(d, 0.0)
+        tour = (rng.permutation(n) + 1).astype(np.int32)
+        q = rng.integers(0, Q + 1, size=(4, n)).astype(np.int32)
+        o = oracle.split_fleet(tour, Q, K, q, dist=d, want_margin=True)
+        for s in range(4):
+            best, parts = split_brute(tour.tolist(), q[s].tolist(), Q,
+                                      lambda a, b: float(d[a, b]), max_routes=K)
+            if math.isinf(best):
+                assert math.isinf(o["margin"][s])
+                continue
+            assert (o["margin"][s] > 0) == (len(parts) == 1), (seed, s, parts)
+            unique += len(parts) == 1
+            multiple += len(parts) > 1
+    assert unique >= 10 and multiple >= 10
+
+
+@pytest.mark.parametrize("K", [2, 9])
+def test_fleet_mean_is_the_sample_average(K):
+    """The mean is the average of the per-scenario costs over all S (the SAA
+    mean), +inf as soon as one scenario has no split into K routes."""
+    tour, xy, q = _inst(7, 9, 50, 30, 12)
+    o = oracle.split_fleet(tour, 30, K, q, coords=xy)
+    c = o["cost"]
+    if np.isinf(c).any():
+        assert K == 2 and math.isinf(o["mean"])
+    else:
+        assert o["mean"] == pytest.approx(math.fsum(c) / len(c), rel=1e-14)

@@ -172,3 +172,14 @@ def test_soft_split_ties_by_brute_force():
             ties += len(opt) > 1
             assert pred[i - 1] == min(opt), (seed, i, opt)
     assert ties >= 20 and overloaded >= 10
+
+
+def test_soft_split_mean_is_the_sample_average():
+    """The mean is the average of the per-scenario costs over all S (the SAA
+    mean); with soft capacity every scenario is finite."""
+    rng = np.random.default_rng(2950)
+    tour, xy, _, _ = _instance(rng, 20, 10, False)
+    q = rng.integers(0, 25, size=(64, 20)).astype(np.int32)
+    r = oracle.split_soft(tour, 30, 7.0, q, coords=xy)
+    assert np.isfinite(r["cost"]).all()
+    assert r["mean"] == pytest.approx(math.fsum(r["cost"]) / len(r["cost"]), rel=1e-14)
