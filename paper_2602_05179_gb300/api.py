@@ -399,7 +399,9 @@ class GraphedSplitBackward:
     device as one launch per step, without the per-call host work.
 
     The graph reads tour, demands, dist and grad_mean where they were at
-    capture, so refill those tensors in place between replays (same shapes);
+    capture, so refill those tensors in place between replays (same shapes;
+    grad_mean is read in place when it is a CUDA fp32 scalar, else a copy
+    taken at construction is used);
     run() returns the same grad (and hist) tensors every time, overwritten
     by each replay.  One warm-up call on a side stream sets up the library's
     per-device state before the capture."""
