@@ -192,3 +192,26 @@ def test_every_planted_mistake_fails_a_pin():
 def test_unplanted_copy_passes_every_pin(target):
     rc, tail = run_mutant(("control", None, None, 0), target)
     assert rc == 0, tail
+
+
+def test_oracle_has_no_undefined_behaviour_on_the_pins(tmp_path):
+    """The C oracle built with UndefinedBehaviorSanitizer, stopping at the
+    first finding (signed overflow, shifts out of range, array indexes out of
+    bounds, misaligned loads), passes every pin."""
+    src = tmp_path / "sdp_oracle.c"
+    shutil.copy(ORACLE_C, src)
+    lib = tmp_path / "liboracle.so"
+    cc = subprocess.run(["gcc", "-std=c11", "-O1", "-fopenmp", "-ffp-contract=off",
+                         "-fno-fast-math", "-fPIC", "-shared", "-fsanitize=undefined",
+                         "-fno-sanitize-recover=all", str(src), "-o", str(lib), "-lm"],
+                        capture_output=True, text=True)
+    if cc.returncode != 0:
+        pytest.skip("no UndefinedBehaviorSanitizer runtime: " + cc.stderr[-200:])
+    script = ("import os, sys, pytest, oracle\n"
+              f"oracle._SRC = {str(src)!r}\noracle._LIB_PATH = {str(lib)!r}\noracle._lib = None\n"
+              f"os.utime({str(lib)!r})\n"
+              "sys.exit(pytest.main(['-x', '-q', '-m', 'not gpu', '-p', 'no:cacheprovider', "
+              f"'-W', 'ignore', *{PIN_FILES!r}]))\n")
+    p = subprocess.run([sys.executable, "-c", script], cwd=ROOT, capture_output=True,
+                       text=True, timeout=900, env=dict(os.environ, OMP_NUM_THREADS="2"))
+    assert p.returncode == 0, (p.stdout[-1500:], p.stderr[-1500:])
