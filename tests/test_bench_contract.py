@@ -159,3 +159,24 @@ def test_kernel_rev_ignores_comments_and_blank_lines(tmp_path, monkeypatch):
     assert "kCheckEvery = 2;" in src
     (d / "split_pipe.cu").write_text(src.replace("kCheckEvery = 2;", "kCheckEvery = 4;"))
     assert bench.kernel_rev("pipe") != h0
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """Launched as the N > 1 runs are (torchrun, one process per rank, the
+    rendezvous on 127.0.0.1): rank 0 alone runs the oracle and prints the one
+    JSON line; the other rank exits 0 without output."""
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    p = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                        "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                        "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
