@@ -2,10 +2,15 @@
 // (Sec. 2 "Instantiation B", Eq. eqdp2; Algorithm "SolveBatchDP"), all T
 // stages fused in one launch, then the backtrack from I0.
 //
-// Two kernels.  reinsert_kernel (the default) runs one scenario per warp;
-// reinsert_lane_kernel (below, SDP_REINSERT_LANE) one scenario per lane.
+// Three kernels.  reinsert_kernel runs one scenario per warp (the two
+// actions), reinsert_routes_kernel one scenario per warp with up to K route
+// options, and reinsert_lane_kernel (below) one scenario per lane, for the
+// two actions or up to 8 route options.  SDP_REINSERT_AUTO takes the lane
+// kernel wherever it applies (U <= 255, T <= 4096, at least 4 warps' worth of
+// its shared memory per SM; not with a table end cost and route options);
+// SDP_REINSERT_WARP forces the warp kernels.
 //
-// Mapping.  One warp per scenario; lane l owns the inventory states
+// Mapping of the warp kernels.  One warp per scenario; lane l owns the inventory states
 // I = l + 32k, k < KC, so the consumption of the day is warp-uniform and the
 // stage loop has no divergence.  With
 //     G_{t+1}(j) = e(j) + C_{t+1}(max(0, j))      (e: end-of-day cost)
