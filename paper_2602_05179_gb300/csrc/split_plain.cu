@@ -7,7 +7,9 @@
 // in the K(i) = J(i) - D(i) form (see StepRec).  The K(p) history of each
 // scenario lives in a global scratch array interleaved by thread slot so that
 // a warp's accesses coalesce.  The same kernel, fed a list of scenario ids,
-// recomputes the few scenarios the deque kernel cannot hold on chip.
+// recomputes the scenarios a deque kernel flagged where the warp kernel of
+// split_rescue.cu does not apply: soft capacity, the adjoint's route counts,
+// and rows too long for that kernel's shared memory.
 #include <math_constants.h>
 
 #include "sdp_internal.cuh"
