@@ -215,3 +215,33 @@ def test_oracle_has_no_undefined_behaviour_on_the_pins(tmp_path):
     p = subprocess.run([sys.executable, "-c", script], cwd=ROOT, capture_output=True,
                        text=True, timeout=900, env=dict(os.environ, OMP_NUM_THREADS="2"))
     assert p.returncode == 0, (p.stdout[-1500:], p.stderr[-1500:])
+
+
+def test_oracle_has_no_memory_errors_on_the_pins(tmp_path):
+    """The C oracle built with AddressSanitizer (out-of-bounds and
+    use-after-free accesses, reported and fatal) passes every pin.  The
+    sanitizer's runtime has to be loaded first, so the child Python starts
+    with it preloaded."""
+    asan = subprocess.run(["gcc", "-print-file-name=libasan.so"], capture_output=True,
+                          text=True).stdout.strip()
+    if not asan or not os.path.isabs(asan) or not os.path.exists(asan):
+        pytest.skip("no AddressSanitizer runtime")
+    src = tmp_path / "sdp_oracle.c"
+    shutil.copy(ORACLE_C, src)
+    lib = tmp_path / "liboracle.so"
+    cc = subprocess.run(["gcc", "-std=c11", "-O1", "-g", "-fopenmp", "-ffp-contract=off",
+                         "-fno-fast-math", "-fPIC", "-shared", "-fsanitize=address",
+                         "-fno-omit-frame-pointer", str(src), "-o", str(lib), "-lm"],
+                        capture_output=True, text=True)
+    if cc.returncode != 0:
+        pytest.skip("AddressSanitizer build failed: " + cc.stderr[-200:])
+    script = ("import os, sys, pytest, oracle\n"
+              f"oracle._SRC = {str(src)!r}\noracle._LIB_PATH = {str(lib)!r}\noracle._lib = None\n"
+              f"os.utime({str(lib)!r})\n"
+              "sys.exit(pytest.main(['-x', '-q', '-m', 'not gpu', '-p', 'no:cacheprovider', "
+              f"'-W', 'ignore', *{PIN_FILES!r}]))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="2", LD_PRELOAD=asan,
+               ASAN_OPTIONS="detect_leaks=0:verify_asan_link_order=0:abort_on_error=1")
+    p = subprocess.run([sys.executable, "-c", script], cwd=ROOT, capture_output=True,
+                       text=True, timeout=900, env=env)
+    assert p.returncode == 0, (p.stdout[-1500:], p.stderr[-1500:])
