@@ -144,3 +144,49 @@ def test_reinsert_eval_rejections(lib, kw, code, words):
 
 def test_reinsert_eval_null_args(lib):
     _expect(lib, lib.sdp_reinsert_eval(None, None), INVALID, "args is NULL")
+
+
+def _desc(**kw):
+    from paper_2602_05179_gb300 import api
+    d = api.BatchDesc()
+    d.B, d.Q, d.S = 2, 30, 4
+    d.n_host = d.tour_off_host = d.coord_off_host = d.dem_off_host = HOST
+    d.tours = d.coords = d.demands = d.costs_out = HOST
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("kw,code,words", [
+    (dict(B=0), INVALID, "B < 1"),
+    (dict(Q=0), UNSUPPORTED, "1 <= Q <= 32767"),
+    (dict(Q=40000), UNSUPPORTED, "1 <= Q <= 32767"),
+    (dict(S=0), INVALID, "S < 1"),
+    (dict(B=1 << 30, S=1 << 62), UNSUPPORTED, "B*S too large"),
+    (dict(dem_off_host=None), INVALID, "host offset arrays"),
+    (dict(costs_out=None), INVALID, "costs_out must be set"),
+])
+def test_plan_create_rejections(lib, kw, code, words):
+    lib.sdp_split_plan_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    h = ctypes.c_void_p(12345)
+    _expect(lib, lib.sdp_split_plan_create(ctypes.byref(_desc(**kw)), ctypes.byref(h)),
+            code, words)
+    assert not h.value  # no plan handed out
+
+
+def test_plan_calls_on_a_null_plan(lib):
+    P = ctypes.c_void_p
+    lib.sdp_split_plan_create.argtypes = [P, P]
+    _expect(lib, lib.sdp_split_plan_create(None, None), INVALID, "NULL")
+    for name, args in (("sdp_plan_run", (None, None)),
+                       ("sdp_plan_info", (None, None, None, None, None)),
+                       ("sdp_plan_configure", (None, -2, 16, 1)),
+                       ("sdp_plan_kernel_ms", (None, None)),
+                       ("sdp_plan_scenarios_per_lane", (None, None)),
+                       ("sdp_plan_count_arcs", (None, None, None)),
+                       ("sdp_plan_autotune", (None, None, None))):
+        f = getattr(lib, name)
+        f.argtypes = [P if a is None else ctypes.c_int32 for a in args]
+        assert f(*args) == INVALID, name
+    lib.sdp_plan_destroy.argtypes = [P]
+    lib.sdp_plan_destroy(None)  # a no-op
