@@ -190,3 +190,18 @@ def test_plan_calls_on_a_null_plan(lib):
         assert f(*args) == INVALID, name
     lib.sdp_plan_destroy.argtypes = [P]
     lib.sdp_plan_destroy(None)  # a no-op
+
+
+def test_count_arcs_and_profile_hook_rejections(lib):
+    P = ctypes.c_void_p
+    lib.sdp_split_count_arcs.argtypes = [P, P, P, P]
+    _expect(lib, lib.sdp_split_count_arcs(None, None, None, None), INVALID, "args is NULL")
+    a = _split(S=0, n=5)
+    _expect(lib, lib.sdp_split_count_arcs(ctypes.byref(a), HOST, None, None), INVALID,
+            "arcs_out must be a device pointer")
+    _expect(lib, lib.sdp_split_count_arcs(ctypes.byref(a), None, HOST, None), INVALID,
+            "total_out must be a device pointer")
+    lib.sdp_set_profile_events.argtypes = [P, P]
+    _expect(lib, lib.sdp_set_profile_events(HOST, None), INVALID, "both events or neither")
+    _expect(lib, lib.sdp_set_profile_events(None, HOST), INVALID, "both events or neither")
+    assert lib.sdp_set_profile_events(None, None) == 0
