@@ -117,3 +117,110 @@ def test_short_rows_keep_most_threads_busy():
         else:
             got = 2 * min(wq, HALF)
         assert got == busy, n
+
+
+# --------------------------------------------------------------- predecessors
+def test_pred_stage_model_follows_the_kernel_source():
+    src = open(SRC).read()
+    for line in ("static constexpr int W = 32 / (int)sizeof(PT);",
+                 "const int sw = ((lane >> 2) & 3) << 1;",
+                 "st[lane * 8 + ((pos >> 1) ^ sw)] = __byte_perm(pend, p, 0x5410);",
+                 "st[lane * 8 + (pos ^ sw)] = p;",
+                 "if (sizeof(PT) == 2 && (cnt & 1)) st[lane * 8 + ((cnt >> 1) ^ (((lane >> 2) & 3) << 1))] = pend;",
+                 "if (wide && cnt == W) {",
+                 "const int k2 = lane & 3;",
+                 "const int r = 8 * m + (lane >> 2);",
+                 "const int sz = ((r >> 2) & 3) << 1;",
+                 "const uint2 v = *reinterpret_cast<const uint2*>(st + r * 8 + (2 * k2 ^ sz));",
+                 "PT* dst = tile + (int64_t)r * n + (i0 - 1) + 2 * k2 * PER;",
+                 "const int k = lane & 7;",
+                 "const int r = 4 * m + (lane >> 3);",
+                 "const uint32_t v = st[r * 8 + (k ^ ((m & 3) << 1))];",
+                 "if (r < rows && k * PER < cnt) {",
+                 "} else if (pairs && k * 2 + 1 < cnt) {",
+                 "if (k * 2 + 1 < cnt) dst[1] = (PT)(v >> 16);",
+                 "ps.pairs = sizeof(PT) == 4 || ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(a.pred) & 3) == 0);",
+                 "ps.wide = (n % (8 / (int)sizeof(PT))) == 0 && (reinterpret_cast<uintptr_t>(a.pred) & 7) == 0;",
+                 "if (u % W == W - 1) ps.flush(i - W + 1, W);",
+                 "if (u % W == W - 1 || i == n) ps.flush(i - u % W, u % W + 1);"):
+        assert line in src, line
+
+
+def _pred_flush(size, cnt, rows, pairs, wide, n, i0, s0, base):
+    """Stores of one flush: [(byte address, nbytes, [(row, position, value)])].
+    Lane l's predecessor of position i0 + e is the code 1000 * l + e."""
+    W, PER = 32 // size, 4 // size
+    st = [[None] * 8 for _ in range(32)]
+    for lane in range(32):
+        sw = ((lane >> 2) & 3) << 1
+        pend = None
+        for pos in range(cnt):
+            p = (lane, pos)
+            if size == 2:
+                if pos % 2 == 0:
+                    pend = p
+                else:
+                    st[lane][(pos >> 1) ^ sw] = (pend, p)
+            else:
+                st[lane][pos ^ sw] = (p,)
+        if size == 2 and cnt % 2:
+            st[lane][(cnt >> 1) ^ sw] = (pend, None)
+    stores = []
+
+    def addr(r, col):
+        return base + ((s0 + r) * n + (i0 - 1) + col) * size
+
+    if wide and cnt == W:
+        for lane in range(32):
+            k2 = lane & 3
+            for m in range(4):
+                r = 8 * m + (lane >> 2)
+                sz = ((r >> 2) & 3) << 1
+                w = (2 * k2) ^ sz
+                assert w % 2 == 0
+                v = st[r][w] + st[r][w + 1]
+                if r < rows:
+                    stores.append((addr(r, 2 * k2 * PER), 8, [(r, 2 * k2 * PER + e, x)
+                                                              for e, x in enumerate(v)]))
+        return stores
+    for lane in range(32):
+        k = lane & 7
+        for m in range(8):
+            r = 4 * m + (lane >> 3)
+            v = st[r][k ^ ((m & 3) << 1)]
+            if r < rows and k * PER < cnt:
+                col = k * PER
+                if size == 4 or (pairs and k * 2 + 1 < cnt):
+                    stores.append((addr(r, col), 4, [(r, col + e, x) for e, x in enumerate(v)]))
+                else:
+                    stores.append((addr(r, col), 2, [(r, col, v[0])]))
+                    if k * 2 + 1 < cnt:
+                        stores.append((addr(r, col + 1), 2, [(r, col + 1, v[1])]))
+    return stores
+
+
+@pytest.mark.parametrize("size", [2, 4])
+def test_pred_stage_writes_each_position_once(size):
+    """Every flush the kernel makes (a full block of W positions, or the last
+    cnt at the end of the tour; W = 16 uint16 or 8 int32 predecessors)
+    writes each (row, position) below (rows, cnt) once, with its own value,
+    and each 4- or 8-byte store on its own alignment whenever the launch
+    chose pairs / wide for that n and base address."""
+    W = 32 // size
+    for n in (W, 2 * W, 3 * W + 5, 100, 101, 500, 513):
+        for base in (0, 2, 4, 8, 16):
+            if base % size:
+                continue
+            pairs = size == 4 or (n % 2 == 0 and base % 4 == 0)
+            wide = n % (8 // size) == 0 and base % 8 == 0
+            for i0 in range(1, n + 1, W):
+                cnt = min(W, n - i0 + 1)
+                for rows in (1, 17, 32):
+                    got = {}
+                    for a, nb, elems in _pred_flush(size, cnt, rows, pairs, wide, n, i0, 64, base):
+                        assert a % nb == 0, (n, base, i0, nb)
+                        for r, pos, val in elems:
+                            assert (r, pos) not in got
+                            got[(r, pos)] = val
+                    assert set(got) == {(r, p) for r in range(rows) for p in range(cnt)}
+                    assert all(val == (r, p) for (r, p), val in got.items())
