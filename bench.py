@@ -889,6 +889,26 @@ def op_saa(c, out):
     out[f"saa_n{spec.n}_S1e4_B{c.wl.SAA_B}"] = line
 
 
+def issue_roof(tj, S, kern_ms, sms, sm_mhz):
+    """The DP kernel against its instruction-issue bound: the warp
+    instructions of one launch (the stored capture's smsp__inst_executed.sum,
+    scaled from the captured scenario count to S) over the kernel time,
+    against SMs x 4 schedulers x the maximum SM clock (one warp instruction
+    per scheduler per cycle).  None without a matching capture."""
+    inst = (tj or {}).get("smsp_inst_executed_captured")
+    cap = (tj or {}).get("captured_scenarios")
+    if not inst or not cap or not kern_ms or kern_ms <= 0 or not sms or not sm_mhz:
+        return None
+    per_launch = float(inst) * float(S) / float(cap)
+    peak = float(sms) * 4.0 * float(sm_mhz) * 1e6
+    achieved = per_launch / (kern_ms / 1e3)
+    return {"bound": "issue", "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak,
+            "inst_per_launch": per_launch,
+            "source": "smsp__inst_executed.sum of the stored capture, scaled by scenarios",
+            "peak_source": f"{sms} SMs x 4 schedulers x sm_max_mhz"}
+
+
 def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plain, e2e,
            flags, clocks, t_wall0, t_wall1, dist, ops=None, errors=None):
     import torch
@@ -899,6 +919,7 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
     alg_bytes = S * n * 4 + S * 4 + S * n * pbytes  # demands in, fp32 cost + preds out
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     traffic = None
+    tj_now = None  # the stored capture, when it describes the kernel being timed
     tp = os.path.join(ROOT, "profiles", "split_pipe_traffic.json" if args.algo == "pipe"
                       else "split_deque_traffic.json")
     if os.path.exists(tp):
@@ -906,6 +927,7 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
             tj = json.load(f)
         if tj.get("kernel_rev") == kernel_rev(args.algo):
             traffic = tj.get("dram_bytes_per_launch")
+            tj_now = tj
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
             "kernel": {"pipe": "split_pipe_kernel", "deque": "split_tmem_kernel",
@@ -931,6 +953,7 @@ def report(args, spec, S, world, value, scen_s, ms_step, kern_ms, arcs_all, plai
         "roofline": roof,
         "alu_roofline": {"ops_per_arc": 2, "peak_ops_per_s": p_alu,
                          "frac": 2 * arcs_all / world / (kern_ms / 1e3) / p_alu},
+        "issue_roofline": issue_roof(tj_now, S, kern_ms, sms, peaks.get("sm_max_mhz", 2070.0)),
         "vs_plain": plain,
         "errors": errors,
         "e2e": e2e,

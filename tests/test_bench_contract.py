@@ -180,3 +180,62 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_issue_roofline_arithmetic():
+    """The headline's instruction-issue fraction: the stored capture's warp
+    instructions scaled to the launch, over the kernel time, against SMs x 4
+    schedulers x the clock; with the recorded capture and the measured 1.1533
+    ms kernel it is the 68% the design notes state."""
+    with open(os.path.join(ROOT, "profiles", "split_pipe_traffic.json")) as f:
+        tj = json.load(f)
+    r = bench.issue_roof(tj, 1_000_000, 1.1533, 152, 2070.0)
+    per = tj["smsp_inst_executed_captured"] * 1e6 / tj["captured_scenarios"]
+    assert r["inst_per_launch"] == pytest.approx(per, rel=1e-12)
+    assert r["peak"] == pytest.approx(152 * 4 * 2070e6, rel=1e-12)
+    assert r["frac"] == pytest.approx(per / 1.1533e-3 / (152 * 4 * 2070e6), rel=1e-12)
+    assert 0.67 < r["frac"] < 0.70 and r["bound"] == "issue"
+    assert bench.issue_roof(None, 10, 1.0, 152, 2070.0) is None
+    assert bench.issue_roof({"captured_scenarios": 5}, 10, 1.0, 152, 2070.0) is None
+    assert bench.issue_roof(tj, 10, 0.0, 152, 2070.0) is None
+
+
+def test_report_builds_the_contract_line(monkeypatch, capsys):
+    """The GPU arm's report on the host, with the device queries stubbed: the
+    one JSON line carries the contract's keys, the HBM roofline of the
+    measured kernel time with the stored traffic, and the issue fraction."""
+    import argparse
+
+    import torch
+    from paper_2602_05179_gb300 import workloads as wl
+
+    class Props:
+        multi_processor_count = 152
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: Props())
+    args = argparse.Namespace(preds="u16", algo="pipe", steps=20, warmup=3,
+                              no_cpu_baseline=True)
+    spec = wl.SPLIT_C2
+    S = spec.S
+    rc = bench.report(args, spec, S, 1, 5.26e12, 8.45e8, 1.183, 1.1533, 6.22e9,
+                      {"ms_per_step": 136.2}, {"value": 6.4e11}, 0, bench.ClockSampler(0),
+                      0.0, 1.0, None, ops=None, errors={"sample": 2000})
+    assert rc == 0
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "roofline", "e2e", "gpu_launches", "clocks", "errors", "vs_plain"):
+        assert k in d, k
+    assert d["metric"] == bench.METRIC and d["config"]["workload"] == bench.WORKLOAD
+    assert d["gpu_launches"] == 5 * 20 and d["n_gpus"] == 1
+    peaks, _ = bench.measured_peaks()
+    alg = S * spec.n * 4 + S * 4 + S * spec.n * 2
+    assert d["roofline"]["algorithmic_bytes_per_launch"] == alg
+    assert d["roofline"]["frac"] == pytest.approx(alg / 1.1533e-3 / 1e9 / peaks["hbm_gbs"])
+    with open(os.path.join(ROOT, "profiles", "split_pipe_traffic.json")) as f:
+        tj = json.load(f)
+    if tj["kernel_rev"] == bench.kernel_rev("pipe"):
+        assert d["roofline"]["traffic"] == pytest.approx(tj["dram_bytes_per_launch"])
+        assert 0.6 < d["issue_roofline"]["frac"] < 0.8
+    else:
+        assert d["roofline"]["traffic"] is None and d["issue_roofline"] is None
