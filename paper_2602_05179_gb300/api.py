@@ -29,6 +29,8 @@ P = ctypes.c_void_p
 
 
 class SplitArgs(ctypes.Structure):
+    """Mirror of sdp_split_args (the Split of Eq. eqdpA); the library checks
+    its size against this layout when it loads."""
     _fields_ = [("n", ctypes.c_int32), ("Q", ctypes.c_int32), ("S", ctypes.c_int64),
                 ("tour", P), ("coords", P), ("dist", P), ("demands", P),
                 ("cost_out", P), ("pred_out", P), ("pred_dtype", ctypes.c_int32),
@@ -39,6 +41,8 @@ class SplitArgs(ctypes.Structure):
 
 
 class ReinsertArgs(ctypes.Structure):
+    """Mirror of sdp_reinsert_args (the reinsertion DP of Eq. eqdp2 /
+    Algorithm SolveBatchDP); size-checked like SplitArgs."""
     _fields_ = [("T", ctypes.c_int32), ("U", ctypes.c_int32), ("I0", ctypes.c_int32),
                 ("algo", ctypes.c_int32), ("h", ctypes.c_float), ("p", ctypes.c_float),
                 ("unit_cost", ctypes.c_float), ("S", ctypes.c_int64), ("fixed", P),
@@ -49,6 +53,8 @@ class ReinsertArgs(ctypes.Structure):
 
 
 class BatchDesc(ctypes.Structure):
+    """Mirror of sdp_split_batch_desc (a batched Split plan's tours, offsets
+    and outputs)."""
     _fields_ = [("B", ctypes.c_int32), ("Q", ctypes.c_int32), ("S", ctypes.c_int64),
                 ("n_host", P), ("tour_off_host", P), ("tours", P), ("coord_off_host", P),
                 ("coords", P), ("dem_off_host", P), ("demands", P), ("costs_out", P),
@@ -56,18 +62,24 @@ class BatchDesc(ctypes.Structure):
 
 
 class SaaSearchDesc(ctypes.Structure):
+    """Mirror of sdp_saa_search_desc (the SAA candidate search's instance,
+    neighbourhood size, move kinds and seed)."""
     _fields_ = [("n", ctypes.c_int32), ("coords", P), ("Q", ctypes.c_int32),
                 ("S", ctypes.c_int64), ("demands", P), ("B", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("moves", ctypes.c_int32), ("tour0", P)]
 
 
 class SdpError(RuntimeError):
+    """A negative status from the library: .code is the SDP_ERR_* value, the
+    message is sdp_last_error() of the failing call."""
+
     def __init__(self, code: int, msg: str):
         super().__init__(f"libsdp error {code}: {msg}")
         self.code = code
 
 
 def lib_path() -> str:
+    """Path of the in-tree libsdp.so this module loads."""
     return _LIB_PATH
 
 
@@ -245,8 +257,9 @@ def adaptive_batches(run, S, batch=None, *, bytes_per_scenario=0, device=None, m
 
 def reinsert_eval_batched(T, U, I0, h, p, unit_cost, fixed, consumption, *, batch=None,
                           min_batch=32, **kw):
-    """reinsert_eval over consumption [S, T] in adaptive batches
-    (adaptive_batches): value [S], policy [S, T] (if asked), FP64 mean over
+    """reinsert_eval (Algorithm SolveBatchDP) over consumption [S, T] in
+    adaptive batches (adaptive_batches: the halving on out-of-memory of
+    Algorithm gpu-dp): value [S], policy [S, T] (if asked), FP64 mean over
     all S, and the batch sizes used."""
     S = int(consumption.shape[0])
     per = 4 * T + 4 + T + 4 * (U + 1)  # inputs and outputs of one scenario, roughly
@@ -329,7 +342,8 @@ def split_eval(tour, Q, demands, *, coords=None, dist=None, preds=None, algo="au
 def split_fleet_eval(tour, Q, demands, max_routes, *, coords=None, dist=None, routes=True,
                      algo="auto", mean=True, stream=None):
     """Fleet-limited Split: at most max_routes routes per scenario (hard
-    capacity).  Arguments as split_eval; algo "auto" or "plain".  Returns
+    capacity; the extensive model's fleet-size constraint, Appendix A, on
+    the recursion of Eq. eqdpA).  Arguments as split_eval; algo "auto" or "plain".  Returns
     dict(cost fp32 [S] (+inf where no split fits), nroutes int32 [S],
     route uint8 [S, n] (route of each position, 255 when infeasible) or None,
     mean fp64 0-d tensor or None)."""
@@ -353,8 +367,8 @@ def split_fleet_eval(tour, Q, demands, max_routes, *, coords=None, dist=None, ro
 
 def split_count_arcs(tour, Q, demands, *, coords=None, dist=None, per_scenario=True,
                      stream=None):
-    """Capacity-feasible arcs (p, i) per scenario (int64 [S]) and their total
-    (uint64 stored in an int64 0-d tensor)."""
+    """Capacity-feasible arcs (p, i) of Eq. eqdpA per scenario (int64 [S])
+    and their total (uint64 stored in an int64 0-d tensor)."""
     _load()
     dev = tour.device
     S = int(demands.shape[0])
@@ -371,7 +385,8 @@ def split_count_arcs(tour, Q, demands, *, coords=None, dist=None, per_scenario=T
 def split_backward(tour, Q, demands, dist, grad_mean, *, pred=None, pred_dtype=None,
                    algo="auto", want_hist=False, warps=0, ring=0, stream=None):
     """d mean / d dist (fp32 [n+1, n+1]) as scenario-averaged arc-usage counts
-    times grad_mean (device fp32 scalar).  pred: the forward's predecessors,
+    times grad_mean (device fp32 scalar): the route cost W of Sec. 2 is a sum
+    of travel costs, so the optimal split's cost is piecewise linear in them.  pred: the forward's predecessors,
     or None to recompute them in the fused forward + backtrack kernel
     (warps / ring: the DEQUE launch shape, as in split_eval; 0 = default)."""
     _load()
@@ -428,7 +443,8 @@ class GraphedSplitBackward:
 
 
 class SplitMeanCost(torch.autograd.Function):
-    """mean_s J_s(n) as a differentiable function of the travel-cost matrix.
+    """mean_s J_s(n) (the SAA objective of Sec. 2) as a differentiable
+    function of the travel-cost matrix.
 
     forward(dist [n+1, n+1] fp32 CUDA, tour, demands, Q, keep_pred=False)
     returns the FP64 scenario mean (0-d); backward returns
@@ -498,7 +514,8 @@ def reinsert_eval(T, U, I0, h, p, unit_cost, fixed, consumption, *, table=None,
 
 
 class SplitPlan:
-    """Batched Split over B giant tours of uneven length, S scenarios each:
+    """Batched Split over B giant tours of uneven length, S scenarios each
+    (the candidate evaluations that Tables cand_cvrp / gpu_dsirp count):
     one persistent launch (work queue over (tour, 32-scenario tile) items,
     longest tours first) replayed from a CUDA graph.
 
@@ -593,7 +610,9 @@ MOVES = {"2opt": 1, "relocate": 2, "swap": 4}
 
 
 class SaaSearch:
-    """SAA local search over giant tours: every iteration scores the current
+    """SAA local search over giant tours (the candidate loop of Sec. "Decision
+    Quality under Fixed Time Budgets", with local-search moves in place of the
+    paper's genetic algorithm): every iteration scores the current
     tour and B neighbours (2-opt / relocate / swap moves drawn from a
     SplitMix64 stream) by their Split mean over the same scenario set, in one
     batched-plan replay, and keeps the best neighbour if it is strictly
