@@ -310,9 +310,10 @@ int sdp_split_backward(const sdp_split_args* fwd, const void* pred,
                        int64_t* route_hist_out, void* stream);
 
 /* -------------------------------------------------------- batched Split */
-/* B giant tours of uneven length, S scenarios each, run as one persistent
- * launch (work queue over (tour, 32-scenario tile) items, longest tours
- * first) captured in a CUDA graph.  Offsets are HOST arrays read at plan
+/* The Split of Eq. eqdpA for B giant tours of uneven length, S scenarios
+ * each (the candidate evaluations Tables cand_cvrp / gpu_dsirp count), run
+ * as one persistent launch (work queue over (tour, 32-scenario tile) items,
+ * longest tours first) captured in a CUDA graph.  Offsets are HOST arrays read at plan
  * creation; the device arrays must stay valid while the plan is used. */
 typedef struct sdp_split_batch_desc {
   int32_t B;                    /* tours, B >= 1 */
