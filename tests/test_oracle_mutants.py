@@ -112,6 +112,37 @@ MUTANTS = [
      "++narcs;\n      if (p < i - 1) inner += cost_ab(c, sp1, tour[p + 1]);\n      if (isinf",
      "narcs += p > 0;\n      if (p < i - 1) inner += cost_ab(c, sp1, tour[p + 1]);\n      if (isinf",
      0),
+    ("soft: arcs miss p = 0",
+     "      ++narcs;\n      if (p < i - 1) inner += cost_ab(c, sp1, tour[p + 1]);\n      const double W",
+     "      narcs += p > 0;\n      if (p < i - 1) inner += cost_ab(c, sp1, tour[p + 1]);\n"
+     "      const double W", 0),
+    # single-candidate margins, the explicit matrix's last predecessor, distances
+    ("matrix: last predecessor left out",
+     "for (int p = 0; p < i; ++p) col[p] = A_out[(size_t)p * m + i];",
+     "for (int p = 0; p < i; ++p) col[p] = p == i - 1 ? INFINITY : A_out[(size_t)p * m + i];", 0),
+    ("split: single-candidate margin 0",
+     "if (bestp < 0 || isinf(second)) margin[i - 1] = INFINITY;",
+     "if (bestp < 0 || isinf(second)) margin[i - 1] = 0.0;", 0),
+    ("soft: single-candidate margin 0",
+     "if (bestp < 0 || isinf(second)) margin[i - 1] = INFINITY;",
+     "if (bestp < 0 || isinf(second)) margin[i - 1] = 0.0;", 1),
+    ("reinsert: margin at I = U is 0", "double mg = INFINITY;", "double mg = 0.0;", 1),
+    ("euclid: squared distance", "return sqrt(dx * dx + dy * dy);", "return dx * dx + dy * dy;", 0),
+    # fleet routes and margin, gradient scale, route counts, value0, route backtrack
+    ("fleet: first customer of a route unlabelled", "for (int m = p; m < i; ++m) route[m] = k - 1;",
+     "for (int m = p + 1; m < i; ++m) route[m] = k - 1;", 0),
+    ("fleet: margin of the layer choice ignored",
+     "double mg = (bestk == 0 || isinf(second)) ? INFINITY : (second - best) / fmax(fabs(best), 1e-300);",
+     "double mg = INFINITY;", 0),
+    ("gradient: over S + 1",
+     "for (size_t e = 0; e < (size_t)m * m; ++e) grad_out[e] /= (double)S;",
+     "for (size_t e = 0; e < (size_t)m * m; ++e) grad_out[e] /= (double)(S + 1);", 0),
+    ("route counts: skipped not counted", "if (!ok) { ++skip; continue; }",
+     "if (!ok) { continue; }", 0),
+    ("reinsert: value0 skipped for I = U", "for (int I = 0; I < W; ++I) value0[I] = C[I];",
+     "for (int I = 0; I < W - 1; ++I) value0[I] = C[I];", 0),
+    ("routes: backtrack refills on route 1 only", "const int64_t x = (a ? U : I) - d[t];",
+     "const int64_t x = (a > 1 ? U : I) - d[t];", 0),
 ]
 
 # the same for oracle/saa.py (the SAA search: SplitMix64, moves, selection)

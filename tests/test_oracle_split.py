@@ -215,6 +215,33 @@ def test_split_ties_and_infeasible_positions_by_brute_force():
     assert ties >= 10 and unreachable >= 10
 
 
+def test_route_counts_skip_infeasible_scenarios():
+    """A scenario with no feasible split (a demand above Q: predecessors -1
+    from there on) contributes no route and is counted as skipped; the counts
+    are those of the feasible scenarios alone, and their total is the number
+    of routes found by walking each feasible scenario's predecessors back."""
+    rng = np.random.default_rng(41)
+    n, Q, S = 25, 30, 40
+    tour, xy, _, _ = _rand_instance(rng, n, Q, 10, False)
+    q = rng.integers(1, 11, size=(S, n)).astype(np.int32)
+    bad = [3, 17, 18, 39]
+    for s in bad:
+        q[s, int(rng.integers(0, n))] = Q + 1
+    r = oracle.split(tour, Q, q, coords=xy)
+    start, end, skipped = oracle.split_route_counts(r["pred"])
+    assert skipped == len(bad)
+    keep = np.setdiff1d(np.arange(S), bad)
+    s2, e2, k2 = oracle.split_route_counts(r["pred"][keep])
+    assert k2 == 0 and np.array_equal(start, s2) and np.array_equal(end, e2)
+    routes = 0
+    for s in keep:
+        i = n
+        while i > 0:
+            i = int(r["pred"][s][i - 1])
+            routes += 1
+    assert start.sum() == end.sum() == routes
+
+
 # ---------------------------------------------------------------- gradient
 def test_split_gradient_identities_and_fd():
     """d mean / d dist from backtracked arc usage equals central finite
